@@ -1,0 +1,309 @@
+"""Seeded synthetic inputs shared by the CUDA path, the CPU oracle, the tests and the bench.
+
+This module holds no arithmetic of the method (no network, determinant or Hamiltonian
+action). It only describes a problem (lattice, Hamiltonian constants, network shape) and
+draws its inputs:
+
+* occupation configurations, uniformly random among the valid ones
+  (local states of Sec. II.B "Embedding Layer": 0 = empty, 1 = up, 2 = down, 3 = up+down);
+* a flat float64 parameter vector, every entry i.i.d. N(0, scale^2) in a fixed tensor order;
+* the plane-wave reference orbitals M0 (an input added to the orbital projection, not a
+  learnable parameter), built from the closed-form eigenvectors of the hopping matrix;
+* connected-move proposals for chain tests and benches.
+
+Parameter layout (flat, float64, in this order; the C header documents the same order):
+  embed   [N][4][h]   (per-site tables E_i, Sec. II.B) or [4][h] when shared
+  for each layer l:  kernel [k_l][k_l][h][h] (ky, kx, c_in, c_out), bias [h]
+  proj_w  [h][2*Ne]   columns [0,Ne) build rows (i, up), [Ne, 2Ne) rows (i, down)
+  proj_b  [2*Ne]
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence
+
+import numpy as np
+
+MODEL_HUBBARD = 0
+MODEL_TJ = 1
+ACT_TANH = 0
+ACT_SILU = 1
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+MOVE_NONE = -1
+MOVE_HOP = 0
+MOVE_EXCHANGE = 1
+
+
+@dataclasses.dataclass
+class Problem:
+    """Lattice + Hamiltonian + network shape. Plain data; see the module docstring."""
+
+    Lx: int
+    Ly: int
+    pbc_x: int = 1
+    pbc_y: int = 1
+    n_up: int = 1
+    n_dn: int = 1
+    model: int = MODEL_HUBBARD
+    t: float = 1.0
+    tp: float = 0.0
+    U: float = 8.0
+    J: float = 0.0
+    n_layers: int = 2
+    h: int = 8
+    ksize: Sequence[int] = (3, 1)
+    residual: Sequence[int] = (1, 0)
+    act: int = ACT_TANH
+    per_site_embed: int = 1
+    precision: int = PREC_FP64
+    refresh_every: int = 64
+    drift_tol: float = 1e-4
+
+    @property
+    def N(self) -> int:
+        return self.Lx * self.Ly
+
+    @property
+    def Ne(self) -> int:
+        return self.n_up + self.n_dn
+
+    def as_dict(self) -> dict:
+        d = dataclasses.asdict(self)
+        d["ksize"] = list(self.ksize)
+        d["residual"] = list(self.residual)
+        return d
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+
+def scale_layout(L: int, ksize_first: int = 3, conv_residual: int = 1):
+    """Per-layer kernel sizes / residual flags for the SCALE layer layout of Sec. II.B:
+    one k x k convolution with a residual (Eq. conv) followed by L-1 site-wise layers
+    without residual (Eq. MLP)."""
+    ks = [ksize_first] + [1] * (L - 1)
+    rs = [conv_residual] + [0] * (L - 1)
+    return ks, rs
+
+
+def param_shapes(pb: Problem) -> List[tuple]:
+    """(name, shape) of every parameter tensor in flat-vector order."""
+    N, h, Ne = pb.N, pb.h, pb.Ne
+    shapes = [("embed", (N, 4, h) if pb.per_site_embed else (4, h))]
+    for l in range(pb.n_layers):
+        k = int(pb.ksize[l])
+        shapes.append((f"kernel{l}", (k, k, h, h)))
+        shapes.append((f"bias{l}", (h,)))
+    shapes.append(("proj_w", (h, 2 * Ne)))
+    shapes.append(("proj_b", (2 * Ne,)))
+    return shapes
+
+
+def param_count(pb: Problem) -> int:
+    return int(sum(int(np.prod(s)) for _, s in param_shapes(pb)))
+
+
+def param_offsets(pb: Problem) -> dict:
+    off, out = 0, {}
+    for name, s in param_shapes(pb):
+        n = int(np.prod(s))
+        out[name] = (off, s)
+        off += n
+    return out
+
+
+def random_params(pb: Problem, seed: int, scale: float = 0.05) -> np.ndarray:
+    """Every learnable entry i.i.d. N(0, scale^2) from PCG64(seed), tensors in layout order."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0.0, scale, size=int(np.prod(s))) for _, s in param_shapes(pb)]
+    return np.concatenate(parts).astype(np.float64)
+
+
+def random_configs(pb: Problem, B: int, seed: int) -> np.ndarray:
+    """B uniformly random configurations with exactly n_up / n_dn electrons.
+
+    Hubbard: up and down sites drawn independently without replacement.
+    t-J: n_up + n_dn distinct sites, a uniformly random n_up-subset of them is up
+    (no double occupancy, the Gutzwiller-projected space of Eq. ham-tj)."""
+    rng = np.random.default_rng(seed)
+    N = pb.N
+    occ = np.zeros((B, N), dtype=np.int8)
+    for b in range(B):
+        if pb.model == MODEL_TJ:
+            sites = rng.choice(N, pb.n_up + pb.n_dn, replace=False)
+            perm = rng.permutation(pb.n_up + pb.n_dn)
+            up = sites[perm[: pb.n_up]]
+            dn = sites[perm[pb.n_up:]]
+        else:
+            up = rng.choice(N, pb.n_up, replace=False)
+            dn = rng.choice(N, pb.n_dn, replace=False)
+        occ[b, up] |= 1
+        occ[b, dn] |= 2
+    return occ
+
+
+def _chain_modes(L: int, periodic: int):
+    """Real one-dimensional modes of a chain of L sites (nearest-neighbour adjacency):
+    returns (list of (cos-of-wavevector, label tuple), mode matrix [L][n_modes])."""
+    x = np.arange(L)
+    modes, labels = [], []
+    if periodic:
+        for m in range(L):
+            mm = (L - m) % L
+            if mm < m:
+                continue  # pair {m, L-m} represented once
+            k = 2.0 * math.pi * m / L
+            if mm == m:  # k == -k (m = 0 or m = L/2)
+                modes.append(np.cos(k * x) / math.sqrt(L))
+                labels.append((math.cos(k), m, 0))
+            else:
+                modes.append(np.cos(k * x) * math.sqrt(2.0 / L))
+                labels.append((math.cos(k), m, 0))
+                modes.append(np.sin(k * x) * math.sqrt(2.0 / L))
+                labels.append((math.cos(k), m, 1))
+    else:
+        for m in range(1, L + 1):
+            q = math.pi * m / (L + 1)
+            modes.append(np.sin(q * (x + 1)) * math.sqrt(2.0 / (L + 1)))
+            labels.append((math.cos(q), m, 0))
+    return labels, np.stack(modes, axis=1)
+
+
+def plane_wave_orbitals(pb: Problem):
+    """Single-particle eigenvectors of the hopping matrix of Eq. H_h (NN amplitude -t,
+    NNN amplitude -t'), as real products of chain modes, sorted by energy.
+
+    Energy of the product mode (a, b): -2t(ca + cb) - 4t' ca cb, with ca, cb the
+    cosines of the two chain wave-vectors. Returns (energies [N], vectors [N][N]),
+    site index i = y*Lx + x. Ties are ordered by the mode labels (cos before sin)."""
+    lx, mx = _chain_modes(pb.Lx, pb.pbc_x)
+    ly, my = _chain_modes(pb.Ly, pb.pbc_y)
+    entries = []
+    for a, (ca, ma, sa) in enumerate(lx):
+        for b, (cb, mb, sb) in enumerate(ly):
+            e = -2.0 * pb.t * (ca + cb) - 4.0 * pb.tp * ca * cb
+            entries.append((round(e, 12), ma, mb, sa, sb, a, b, e))
+    entries.sort(key=lambda r: r[:5])
+    N = pb.N
+    vecs = np.zeros((N, N))
+    eps = np.zeros(N)
+    for col, r in enumerate(entries):
+        a, b = r[5], r[6]
+        # site (x, y) -> y*Lx + x
+        vecs[:, col] = np.outer(my[:, b], mx[:, a]).reshape(-1)
+        eps[col] = r[7]
+    return eps, vecs
+
+
+def plane_wave_M0(pb: Problem) -> np.ndarray:
+    """Reference orbital matrix M0 [2N][Ne]: block diagonal, rows (up, i) hold the n_up
+    lowest plane waves in columns [0, n_up), rows (down, i) the n_dn lowest in
+    columns [n_up, Ne). Orbital row index o = sigma*N + i."""
+    _, vecs = plane_wave_orbitals(pb)
+    N, Ne = pb.N, pb.Ne
+    M0 = np.zeros((2 * N, Ne))
+    M0[:N, : pb.n_up] = vecs[:, : pb.n_up]
+    M0[N:, pb.n_up:] = vecs[:, : pb.n_dn]
+    return M0
+
+
+def random_hop_moves(pb: Problem, occ: np.ndarray, seed: int) -> np.ndarray:
+    """One proposed nearest-neighbour move per sample, int32 [B][4] = (kind, src, dst, spin).
+
+    Hop: an electron of spin `spin` on `src` moves to the neighbour `dst` where that
+    spin-orbital is empty (t-J: `dst` fully empty). kind = MOVE_NONE when the drawn
+    site has no allowed move. Only used to drive chain benches and tests."""
+    rng = np.random.default_rng(seed)
+    B, N = occ.shape
+    out = np.full((B, 4), MOVE_NONE, dtype=np.int32)
+    for b in range(B):
+        for _ in range(64):
+            src = int(rng.integers(N))
+            spin = int(rng.integers(2))
+            if not (occ[b, src] >> spin) & 1:
+                continue
+            x, y = src % pb.Lx, src // pb.Lx
+            d = int(rng.integers(4))
+            dx, dy = [(1, 0), (-1, 0), (0, 1), (0, -1)][d]
+            xx, yy = x + dx, y + dy
+            if not (0 <= xx < pb.Lx):
+                if not pb.pbc_x:
+                    continue
+                xx %= pb.Lx
+            if not (0 <= yy < pb.Ly):
+                if not pb.pbc_y:
+                    continue
+                yy %= pb.Ly
+            dst = yy * pb.Lx + xx
+            if (occ[b, dst] >> spin) & 1:
+                continue
+            if pb.model == MODEL_TJ and occ[b, dst] != 0:
+                continue
+            out[b] = (MOVE_HOP, src, dst, spin)
+            break
+    return out
+
+
+def apply_moves(occ: np.ndarray, moves: np.ndarray) -> np.ndarray:
+    """Occupations after the given moves (bookkeeping only; no amplitudes)."""
+    out = occ.copy()
+    for b in range(occ.shape[0]):
+        kind, src, dst, spin = (int(v) for v in moves[b])
+        if kind == MOVE_HOP:
+            out[b, src] &= ~(1 << spin)
+            out[b, dst] |= 1 << spin
+        elif kind == MOVE_EXCHANGE:
+            out[b, src], out[b, dst] = out[b, dst], out[b, src]
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# Named workloads: the lattices, dopings and network shapes the method is exercised on.
+# Seeds: parameters 1234 + index, configurations 5678 + index.
+# ---------------------------------------------------------------------------------------
+
+def workload(name: str) -> Problem:
+    if name == "hubbard4x4":  # 4x4 torus, 7+7, 2 layers, 8 channels, FP64
+        ks, rs = scale_layout(2)
+        return Problem(4, 4, 1, 1, 7, 7, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 2, 8, ks, rs,
+                       ACT_TANH, 1, PREC_FP64, 64, 1e-10)
+    if name == "hubbard8x8":  # 8x8 torus, 1/8 doping 28+28, 4 layers, 16 channels
+        ks, rs = scale_layout(4)
+        return Problem(8, 8, 1, 1, 28, 28, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 4, 16, ks, rs,
+                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+    if name == "hubbard16x16":  # 16x16 torus, 112+112, 6 layers, 32 channels, mixed
+        ks, rs = scale_layout(6)
+        return Problem(16, 16, 1, 1, 112, 112, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 6, 32, ks, rs,
+                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+    if name == "cylinder16x4":  # periodic along 16, open along 4, t'=-0.2, 12 residual 3x3
+        return Problem(16, 4, 1, 0, 28, 28, MODEL_HUBBARD, 1.0, -0.2, 8.0, 0.0, 12, 32,
+                       [3] * 12, [1] * 12, ACT_TANH, 1, PREC_FP64, 64, 1e-10)
+    if name == "tj8x8":
+        ks, rs = scale_layout(4)
+        return Problem(8, 8, 1, 1, 28, 28, MODEL_TJ, 1.0, 0.0, 0.0, 0.4, 4, 16, ks, rs,
+                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+    if name == "tj16x16":
+        ks, rs = scale_layout(6)
+        return Problem(16, 16, 1, 1, 112, 112, MODEL_TJ, 1.0, 0.0, 0.0, 0.4, 6, 32, ks, rs,
+                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+    if name == "hubbard32x32":
+        ks, rs = scale_layout(4)
+        return Problem(32, 32, 1, 1, 448, 448, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 4, 16, ks, rs,
+                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+    if name == "tj32x32":
+        ks, rs = scale_layout(4)
+        return Problem(32, 32, 1, 1, 448, 448, MODEL_TJ, 1.0, 0.0, 0.0, 0.4, 4, 16, ks, rs,
+                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+    raise KeyError(name)
+
+
+WORKLOAD_INDEX = {"hubbard4x4": 0, "hubbard8x8": 1, "hubbard16x16": 2, "cylinder16x4": 3,
+                  "tj8x8": 4, "tj16x16": 4, "hubbard32x32": 4, "tj32x32": 4}
+
+
+def workload_seeds(name: str):
+    i = WORKLOAD_INDEX[name]
+    return 1234 + i, 5678 + i
