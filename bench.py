@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the SCALE local-energy hot path on GB300.
+
+One step = one chain step over B resident walkers of the 16x16 Hubbard workload
+(U = 8, 112+112 electrons, 6 layers of 32 channels, mixed precision):
+  * low-rank local energies of every walker (device-side enumeration of the connected
+    configurations, incremental receptive-field update, rank-r determinants);
+  * one Woodbury commit per walker (a proposed nearest-neighbour hop, drawn on the host
+    beforehand with a seeded generator and uploaded once);
+  * the FP64 re-factorisation of the walkers whose commit counter reaches 64 (counters are
+    staggered, so 1/64 of the batch per step).
+value = local energies per second (walkers x steps / device time), max over ranks.
+
+Also reported (rank 0): the cold path (load = forward + FP64 inverse + projector, then
+E_loc), the full-recompute path on a subset of the same walkers (same GPU, same precision
+mode), per-sample gradients, the roofline of the dominant kernel, GPU clocks during the
+timed region, and the FP64 CPU oracle timed on the host cores on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl scale|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2604_25775_gb300 import inputs as I  # noqa: E402
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+FP64_PEAK_TFLOPS = 1.196  # DFMA loop measured on this machine's GB300 (profiles/peaks_fp32_fp64.txt)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="scale", choices=["scale", "reference"])
+    ap.add_argument("--workload", default="hubbard16x16")
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--full-samples", type=int, default=128)
+    ap.add_argument("--cpu-samples", type=int, default=48)
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def move_schedule(pb, occ, n_steps, seed):
+    """Valid nearest-neighbour hop proposals for n_steps consecutive commits (host, seeded)."""
+    cur = occ
+    out = []
+    for k in range(n_steps):
+        mv = I.random_hop_moves(pb, cur, seed + k)
+        out.append(mv)
+        cur = I.apply_moves(cur, mv)
+    return np.stack(out)
+
+
+def lowrank_flops_per_sample(pb, occ, n=32):
+    """Algorithmic FLOPs of one low-rank E_loc per walker, counted from the configurations:
+    per connected move, |S| sites x (L-1) site-wise layers x 2h^2, the moved electron's
+    G row (2 r Ne + 2 r h), the Delta H . P block (2 r^2 h) and the r x r LU (2/3 r^3);
+    r = electrons on the affected sites after the move, S = union of the 3x3 stencils."""
+    N, h, L, Ne = pb.N, pb.h, pb.n_layers, pb.Ne
+    r0 = (pb.ksize[0] - 1) // 2
+    tot = 0.0
+    for b in range(min(n, occ.shape[0])):
+        x = occ[b]
+        for i in range(N):
+            for (dx, dy) in ((1, 0), (0, 1)):
+                xx, yy = (i % pb.Lx + dx) % pb.Lx, (i // pb.Lx + dy) % pb.Ly
+                j = yy * pb.Lx + xx
+                for s in (0, 1):
+                    a, c = (x[i] >> s) & 1, (x[j] >> s) & 1
+                    if a == c:
+                        continue
+                    src, dst = (i, j) if a else (j, i)
+                    S = set()
+                    for t in (src, dst):
+                        for ey in range(-r0, r0 + 1):
+                            for ex in range(-r0, r0 + 1):
+                                S.add(((t // pb.Lx + ey) % pb.Ly) * pb.Lx + (t % pb.Lx + ex) % pb.Lx)
+                    y = x.copy()
+                    y[src] &= ~(1 << s)
+                    y[dst] |= 1 << s
+                    r = sum(((y[q] & 1) + ((y[q] >> 1) & 1)) for q in S)
+                    tot += len(S) * (L - 1) * 2 * h * h + 2 * r * Ne + 2 * r * h + 2 * r * r * h + 2 * r ** 3 / 3
+    return tot / min(n, occ.shape[0])
+
+
+def run_reference(args, world, rank):
+    """The oracle (FP64 CPU, full recompute), as it stands, on the host cores: each step a
+    bounded sample of walkers of the same workload."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    pb = I.workload(args.workload)
+    pseed, cseed = I.workload_seeds(args.workload)
+    params = I.random_params(pb, pseed)
+    M0 = I.plane_wave_M0(pb)
+    m = O.Model(pb, params, M0)
+    per_step = max(1, O.num_threads() // 2)
+    occ = I.random_configs(pb, per_step * (args.steps + args.warmup), cseed)
+    for k in range(args.warmup):
+        m.local_energy(occ[k * per_step:(k + 1) * per_step])
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        m.local_energy(occ[k * per_step:(k + 1) * per_step])
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": "local energies/s (16x16 Hubbard, FP64 CPU oracle, full recompute)",
+            "value": value, "unit": "E_loc/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "per_step_walkers": per_step},
+            "cpu_baseline": {"value": value, "unit": "E_loc/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{per_step} walkers per step x {args.steps} steps"},
+            "e2e": {"value": value, "unit": "E_loc/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, world, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2604_25775_gb300 import binding as Bd
+    Bd.load_library(build=True)
+
+    pb = I.workload(args.workload)
+    pseed, cseed = I.workload_seeds(args.workload)
+    B, K, W = args.batch, args.steps, args.warmup
+    params = I.random_params(pb, pseed)
+    M0 = I.plane_wave_M0(pb)
+    occ = I.random_configs(pb, B, cseed + 1000 * rank)
+    stream = torch.cuda.Stream()
+    ctx = Bd.make_context(pb, params, M0, B, stream=stream)
+    moves = move_schedule(pb, occ, K + W, 777 + 1000 * rank)
+    moves_d = torch.from_numpy(moves).cuda()
+    occ_d = torch.from_numpy(occ).cuda()
+    eloc = torch.empty(B, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        ctx.scale_load(occ_d)
+    stream.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for k in range(W):
+        ctx.scale_local_energy(eloc)
+        ctx.scale_commit(moves_d[k])
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            ctx.scale_local_energy(eloc)
+            ev[k][1].record(stream)
+            ctx.scale_commit(moves_d[W + k])
+            ev[k][2].record(stream)
+        t_end.record(stream)
+        barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    eloc_ms = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
+    commit_ms = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * B * K / (t_max / 1e3)
+    assert torch.isfinite(eloc).float().mean().item() > 0.99
+
+    # end-to-end through the public API: proposals from pinned host memory, E_loc back
+    E2E_STEPS = min(K, 10)
+    mv_host = torch.from_numpy(move_schedule(pb, ctx.get_occ().cpu().numpy(), E2E_STEPS, 999 + rank)).pin_memory()
+    e_host = torch.empty((E2E_STEPS, B), dtype=torch.float64).pin_memory()
+    mv_dev = torch.empty((B, 4), dtype=torch.int32, device="cuda")
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    with torch.cuda.stream(stream):
+        for k in range(E2E_STEPS):
+            mv_dev.copy_(mv_host[k], non_blocking=True)
+            ctx.scale_local_energy(eloc)
+            ctx.scale_commit(mv_dev)
+            e_host[k].copy_(eloc, non_blocking=True)
+    t1.record(stream)
+    barrier()
+    e2e_ms = t0.elapsed_time(t1)
+    e2e_val = world * B * E2E_STEPS / (e2e_ms / 1e3)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * B * E2E_STEPS / (float(t.item()) / 1e3)
+
+    line = {
+        "metric": "local energies/s, low-rank (cached network + rank-r determinant) chain step, 16x16 Hubbard",
+        "value": value, "unit": "E_loc/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (rank-r, network) + f64 (LU refresh, accumulation)", "data": "synthetic",
+        "config": {"workload": "hubbard16x16: 16x16 torus, U=8, 112+112, SCALE 1 conv 3x3 + 5 site-wise, h=32",
+                   "walkers": B, "precision": "mixed", "refresh_every": pb.refresh_every,
+                   "step": "E_loc (low-rank) + 1 Woodbury commit per walker + staggered FP64 refresh",
+                   "l2": "inputs larger than L2 (cached inverses 1.6 GB)", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_val, "unit": "E_loc/s", "h2d_bytes_per_step": B * 4 * 4,
+                "d2h_bytes_per_step": B * 8},
+        "stage_ms": {"eloc_lowrank": eloc_ms, "commit_and_refresh": commit_ms},
+        "clocks": clk.summary(),
+    }
+    stats = ctx.scale_get_stats()
+    line["stats"] = {k: stats[k] for k in ("n_commits", "n_refresh", "n_drift_refresh", "drift_max")}
+
+    if rank == 0 and not args.no_extras:
+        flops = lowrank_flops_per_sample(pb, occ)
+        achieved = flops * B / (eloc_ms / 1e3) / 1e12
+        line["roofline"] = {"kernel": "k_eloc (low-rank E_loc)", "bound": "alu", "achieved": achieved,
+                            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                            "traffic": None, "flops_per_walker": flops,
+                            "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived)"}
+        # cold path: load (forward, FP64 Gauss-Jordan inverse, projector) + E_loc
+        ctx2 = Bd.make_context(pb, params, M0, B)
+        ctx2.scale_load(occ_d)
+        ctx2.scale_local_energy(eloc)
+        torch.cuda.synchronize()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx2.scale_load(occ_d)
+        mid = torch.cuda.Event(enable_timing=True)
+        mid.record()
+        ctx2.scale_local_energy(eloc)
+        b2.record()
+        torch.cuda.synchronize()
+        load_ms, cold_eloc_ms = a.elapsed_time(mid), mid.elapsed_time(b2)
+        line["cold"] = {"load_ms": load_ms, "eloc_ms": cold_eloc_ms,
+                        "eloc_per_s": B / ((load_ms + cold_eloc_ms) / 1e3)}
+        # full-recompute path on a subset of the same walkers
+        nf = args.full_samples
+        ctxf = Bd.make_context(pb, params, M0, nf)
+        ctxf.scale_load(occ_d[:nf].contiguous())
+        ef = torch.empty(nf, dtype=torch.float64, device="cuda")
+        el = torch.empty(nf, dtype=torch.float64, device="cuda")
+        ctxf.scale_local_energy(ef, Bd.PATH_FULL)
+        torch.cuda.synchronize()
+        a.record()
+        ctxf.scale_local_energy(ef, Bd.PATH_FULL)
+        b2.record()
+        torch.cuda.synchronize()
+        full_ms = a.elapsed_time(b2)
+        ctxf.scale_local_energy(el, Bd.PATH_LOWRANK)
+        torch.cuda.synchronize()
+        agree = float(((ef - el).abs() / ef.abs().clamp(min=1.0)).max().item())
+        full_rate = nf / (full_ms / 1e3)
+        lowrank_rate = B / (eloc_ms / 1e3)
+        line["full_recompute"] = {"walkers": nf, "ms": full_ms, "eloc_per_s": full_rate,
+                                  "lowrank_eloc_per_s": lowrank_rate, "speedup_lowrank_vs_full": lowrank_rate / full_rate,
+                                  "max_rel_diff_vs_lowrank": agree}
+        ctxf.close()
+        ctx2.close()
+        # per-sample gradients on a subset
+        ng = 1024
+        ctxg = Bd.make_context(pb, params, M0, ng)
+        ctxg.scale_load(occ_d[:ng].contiguous())
+        g = torch.empty((ng, ctxg.P), dtype=torch.float64, device="cuda")
+        ctxg.scale_grad_logpsi(g)
+        torch.cuda.synchronize()
+        a.record()
+        ctxg.scale_grad_logpsi(g)
+        b2.record()
+        torch.cuda.synchronize()
+        line["grad"] = {"walkers": ng, "ms": a.elapsed_time(b2), "params": ctxg.P}
+        del g
+        ctxg.close()
+        # CPU oracle baseline on a bounded sample
+        from oracle import oracle as O
+        m = O.Model(pb, params, M0)
+        n_cpu = args.cpu_samples
+        t0c = time.perf_counter()
+        m.local_energy(occ[:n_cpu])
+        dt = time.perf_counter() - t0c
+        line["cpu_baseline"] = {"value": n_cpu / dt, "unit": "E_loc/s", "cores": O.num_threads(), "kind": "oracle",
+                                "sample": f"{n_cpu} walkers of the same workload, FP64 full recompute"}
+    line["gpu_launches"] = K * (2 + 6 + 6)  # per step: k_eloc, k_commit, mark, 6 forward/refresh kernels
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

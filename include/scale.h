@@ -1,0 +1,203 @@
+/*
+ * scale.h -- C ABI of the GB300 (sm_103a) SCALE local-energy library.
+ *
+ * The library evaluates, for a batch of lattice-fermion configurations n, the amplitude
+ * psi(n) = det Phi(n) of the SCALE convolutional-backflow ansatz (arXiv 2604.25775,
+ * Sec. II.B), amplitude ratios psi(n')/psi(n), local energies
+ *   E_loc(n) = sum_n' <n|H|n'> psi(n')/psi(n)            (Sec. II.A)
+ * for the Hubbard and t-J Hamiltonians (Eq. H_h, Eq. ham-tj), and per-sample gradients
+ * d log|psi| / d theta. Ratios use the cached-network + Sherman-Morrison-Woodbury local
+ * update of Sec. II.C (Eq. neighbor, Eq. SMW): every connected configuration costs a
+ * rank-r determinant det(I_r + V^T Phi^-1 U) against a cached per-sample Phi^-1.
+ *
+ * Conventions used by every entry point
+ *   - Site i = y*Lx + x. Local state n_i in {0 empty, 1 up, 2 down, 3 up+down}, int8.
+ *   - Orbital (row of the orbital matrix M) o = s*N + i, s = 0 up, 1 down.
+ *   - psi(n) = det of the rows of M of the occupied orbitals in ascending order; log|psi|
+ *     and sign are reported in that convention (a global sign of psi is irrelevant to
+ *     E_loc and to log-derivatives, this one makes results comparable across codes).
+ *   - Parameters: one flat float64 vector, tensors in this order:
+ *       embed  [N][4][h] (per_site_embed = 1, tables E_i of Sec. II.B) or [4][h]
+ *       for each layer l: kernel [k_l][k_l][h][h] (ky, kx, c_in, c_out), bias [h]
+ *         layer l: H(l+1)_i = residual_l * H(l)_i
+ *                             + act(bias_l + sum_{|dx|,|dy|<=(k_l-1)/2} H(l)_{i+(dx,dy)} K_l[dy][dx])
+ *         (Eq. conv for k_l > 1, Eq. MLP for k_l = 1; offsets wrap on periodic axes and
+ *          read zeros past open edges)
+ *       proj_w [h][2*Ne], proj_b [2*Ne]: M[(s,i)][k] = M0[(s,i)][k] + proj_b[s*Ne+k]
+ *                                             + sum_c H(L)_i[c] proj_w[c][s*Ne+k]
+ *     M0 [2N][Ne] float64 is an input (reference orbitals, e.g. plane waves), not a
+ *     parameter.
+ *   - Moves (connected configurations) are int32 quadruples (kind, src, dst, spin):
+ *       kind 0 (hop): the spin-`spin` electron on site src moves to site dst;
+ *       kind 1 (exchange, t-J): the single spins on src and dst swap;
+ *       kind -1: no move (ratio 1, commit is a no-op).
+ *
+ * Memory, streams, errors
+ *   - Pointer arguments are DEVICE pointers unless the name ends in _host. The caller owns
+ *     every pointer it passes; the context owns its cache (features, Phi^-1, projector,
+ *     slot maps), allocated once at scale_create within the HBM budget.
+ *   - Every call is asynchronous on the stream given at creation, except the stated
+ *     host-reading calls (scale_get_stats, scale_footprint_bytes). A context is not
+ *     re-entrant: one host thread at a time.
+ *   - Call-level failures return a scale_status; scale_last_error(ctx) gives the text.
+ *     Per-sample problems (wrong particle numbers, double occupancy under the t-J
+ *     projection, a singular Phi) never fail the call: the sample's status word is set,
+ *     log|psi| = -inf, sign = 0, E_loc = NaN, gradient = NaN.
+ */
+#ifndef SCALE_H
+#define SCALE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SCALE_OK = 0,
+  SCALE_EINVAL = 1,       /* bad argument or descriptor */
+  SCALE_ENOMEM = 2,       /* device allocation failed */
+  SCALE_EBUDGET = 3,      /* request does not fit the HBM budget */
+  SCALE_ECUDA = 4,        /* a CUDA call failed (text in scale_last_error) */
+  SCALE_ETIMEOUT = 5,     /* a bounded wait ran out */
+  SCALE_EUNSUPPORTED = 6  /* valid but not supported by this build (see text) */
+} scale_status;
+
+enum { SCALE_MODEL_HUBBARD = 0, SCALE_MODEL_TJ = 1 };
+enum { SCALE_ACT_TANH = 0, SCALE_ACT_SILU = 1 };
+enum { SCALE_PREC_FP64 = 0, SCALE_PREC_MIXED = 1 };
+enum { SCALE_PATH_LOWRANK = 0, SCALE_PATH_FULL = 1 };
+
+/* per-sample status bits */
+enum {
+  SCALE_SAMPLE_OK = 0,
+  SCALE_SAMPLE_BAD_COUNT = 1,   /* particle numbers differ from n_up / n_dn */
+  SCALE_SAMPLE_DOUBLE_OCC = 2,  /* double occupancy in the Gutzwiller-projected t-J space */
+  SCALE_SAMPLE_SINGULAR = 4,    /* Phi singular (exact zero pivot) */
+  SCALE_SAMPLE_DRIFT = 8        /* drift check fired since the last refresh */
+};
+
+#define SCALE_MAX_LAYERS 32
+
+/* Lattice and Hamiltonian (Eq. H_h, Eq. ham-tj). Periodic extents must be >= 3. */
+typedef struct {
+  int32_t Lx, Ly;
+  int32_t pbc_x, pbc_y;   /* 1 periodic, 0 open */
+  int32_t n_up, n_dn;
+  int32_t model;          /* SCALE_MODEL_* */
+  double t, tp, U, J;     /* NN hopping, NNN hopping, on-site U (Hubbard), J (t-J) */
+} scale_system;
+
+/* Network shape and numerics. */
+typedef struct {
+  int32_t n_layers;       /* L >= 1 */
+  int32_t h;              /* channels of every layer, 1..64 */
+  int32_t act;            /* SCALE_ACT_* */
+  int32_t per_site_embed; /* 1: tables E_i per site (Sec. II.B); 0: one shared table */
+  int32_t precision;      /* SCALE_PREC_FP64: everything FP64.
+                             SCALE_PREC_MIXED: network on BF16 tensor cores with FP32
+                             accumulation, rank-r algebra and cached Phi^-1 in FP32,
+                             LU / log|det| / drift check in FP64 */
+  int32_t refresh_every;  /* FP64 re-factorisation of Phi every this many commits (>= 1);
+                             counters start staggered at load (sample b at b mod
+                             refresh_every) so refreshes spread evenly over calls */
+  double drift_tol;       /* drift check threshold: max |Phi' Phi'^-1 - I| on the changed
+                             rows after a commit; above it the sample is refreshed early */
+  int32_t ksize[SCALE_MAX_LAYERS];    /* odd kernel size per layer, 1 = site-wise */
+  int32_t residual[SCALE_MAX_LAYERS]; /* 1: add the layer input (Eq. conv residual) */
+} scale_arch;
+
+typedef struct {
+  int64_t n_eloc;          /* local energies produced (low-rank path) */
+  int64_t n_eloc_full;     /* local energies produced (full-recompute path) */
+  int64_t n_commits;       /* accepted moves applied */
+  int64_t n_refresh;       /* samples re-factorised in FP64 */
+  int64_t n_drift_refresh; /* of which forced by the drift check */
+  double drift_max;        /* largest drift residual seen */
+  int32_t batch;           /* samples currently loaded */
+  int32_t max_moves;       /* capacity of connected configurations per sample */
+} scale_stats;
+
+typedef struct scale_ctx scale_ctx;
+
+/* Number of float64 entries of the flat parameter vector for this shape. Returns -1 for
+ * an invalid descriptor. Host-only, no GPU work. */
+int64_t scale_param_count(const scale_system *sys, const scale_arch *arch);
+
+/* Device bytes a context with this shape and batch capacity allocates (cache + scratch).
+ * Host-only. Returns 0 for an invalid descriptor. */
+size_t scale_footprint_bytes(const scale_system *sys, const scale_arch *arch, int32_t max_batch);
+
+/* Create a context for up to max_batch samples on the current CUDA device.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream), used by every later call.
+ * hbm_budget_bytes: 0 = no limit; otherwise SCALE_EBUDGET when the footprint exceeds it.
+ * Validates the descriptors (SCALE_EINVAL) and allocates the cache (SCALE_ENOMEM). */
+scale_status scale_create(const scale_system *sys, const scale_arch *arch, int32_t max_batch,
+                          size_t hbm_budget_bytes, void *cuda_stream, scale_ctx **out);
+
+/* Copy the parameters (params: scale_param_count float64 entries) and the reference
+ * orbitals (M0: [2N][Ne] float64) into the context and build the derived tables
+ * (precision copies, the layer-0 conv-of-embedding table). Invalidates loaded samples. */
+scale_status scale_set_params(scale_ctx *ctx, const double *params, const double *M0);
+
+/* Load B <= max_batch configurations occ[B][N] (int8) and build their cache: network
+ * forward, Phi, FP64 Gauss-Jordan inverse with partial pivoting and log|det| (Sec. II.C,
+ * "single LU"), projector P_s = W_s Phi^-1. sample_status[B] (int32, may be NULL)
+ * receives SCALE_SAMPLE_* bits. */
+scale_status scale_load(scale_ctx *ctx, const int8_t *occ, int32_t B, int32_t *sample_status);
+
+/* log|psi| [B] (float64) and sign [B] (int32, 0 for a zero amplitude) of the loaded
+ * samples, ascending-orbital convention. Either pointer may be NULL. */
+scale_status scale_log_psi(scale_ctx *ctx, double *logabs, int32_t *sign);
+
+/* Current configurations occ[B][N] (int8) of the loaded samples (changed by commits). */
+scale_status scale_get_occ(scale_ctx *ctx, int8_t *occ);
+
+/* Ratios psi(n')/psi(n) (ascending convention) for M moves per sample:
+ * moves [B][M][4] int32, ratio [B][M] float64. Low-rank update (Eq. neighbor + Eq. SMW).
+ * A move that leaves the model's space (occupied target, double occupancy in t-J) gives
+ * ratio 0. Requires the SCALE layer layout (k_l = 1 for l >= 1), else SCALE_EUNSUPPORTED. */
+scale_status scale_ratios(scale_ctx *ctx, const int32_t *moves, int32_t M, double *ratio);
+
+/* E_loc [B] (float64) of the loaded samples.
+ * path SCALE_PATH_LOWRANK: connected configurations enumerated on the device, each ratio a
+ *   rank-r determinant against the cached Phi^-1 after an incremental receptive-field
+ *   update of the network (needs k_l = 1 for l >= 1).
+ * path SCALE_PATH_FULL: every psi(n') by a full network forward and a fresh LU in the
+ *   precision of the mode (FP64 mode: FP64; mixed: FP32) -- the comparison path of
+ *   Sec. III.A, any layer layout. */
+scale_status scale_local_energy(scale_ctx *ctx, int32_t path, double *eloc);
+
+/* Apply one accepted move per sample (moves [B][4] int32, kind -1 = reject): Woodbury
+ * update of Phi^-1 (Eq. SMW, second line), rank-r update of the projector, incremental
+ * update of the cached features, occupations and slot maps, running log|det|. Samples
+ * whose commit counter reaches refresh_every, or whose drift check fired, are
+ * re-factorised in FP64 within the same call. Moves must be allowed (the library checks
+ * and skips a move whose source is empty or whose target is occupied). */
+scale_status scale_commit(scale_ctx *ctx, const int32_t *moves);
+
+/* Re-factorise in FP64 every loaded sample (force_all = 1) or only the ones flagged by
+ * the drift check or the commit counter (force_all = 0). */
+scale_status scale_refresh(scale_ctx *ctx, int32_t force_all);
+
+/* Per-sample gradients d log|psi| / d theta, grad [B][P] float64 (flat parameter
+ * layout): d log|det Phi| / d Phi = Phi^-T, back through the projection, every layer and
+ * the embedding (hand-written backward). recompute = 1 keeps only every ceil(sqrt(L))-th
+ * layer input and recomputes the rest (for deep stacks that exceed the scratch). */
+scale_status scale_grad_logpsi(scale_ctx *ctx, double *grad, int32_t recompute);
+
+/* Counters since creation (host struct). Synchronises the context's stream. */
+scale_status scale_get_stats(scale_ctx *ctx, scale_stats *out_host);
+
+/* Text of the last error of this context ("" if none); valid until the next call. */
+const char *scale_last_error(scale_ctx *ctx);
+
+/* Free the context and its device memory (synchronises its stream). NULL is a no-op. */
+void scale_destroy(scale_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCALE_H */

@@ -1,0 +1,418 @@
+// api.cu -- the C ABI of include/scale.h: descriptor validation, context allocation
+// (one cudaMalloc per buffer at creation), parameter upload and the call sequences.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "scale_internal.cuh"
+
+using namespace scale;
+
+namespace {
+
+#define SCALE_TRY(ctx, expr)                                                              \
+  do {                                                                                    \
+    cudaError_t _e = (expr);                                                              \
+    if (_e != cudaSuccess) {                                                              \
+      (ctx)->err = std::string("CUDA error in ") + #expr + ": " + cudaGetErrorString(_e); \
+      return SCALE_ECUDA;                                                                 \
+    }                                                                                     \
+  } while (0)
+
+bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
+  char buf[256];
+  auto fail = [&](const char* m) {
+    *why = m;
+    return false;
+  };
+  if (!s || !a) return fail("null descriptor");
+  if (s->Lx < 1 || s->Ly < 1 || s->Lx > 128 || s->Ly > 128) return fail("lattice extents must be in [1, 128]");
+  if ((s->pbc_x && s->Lx < 3) || (s->pbc_y && s->Ly < 3)) return fail("periodic extents must be >= 3");
+  const int N = s->Lx * s->Ly;
+  if (N > 4096) return fail("at most 4096 sites");
+  if (s->n_up < 0 || s->n_dn < 0 || s->n_up > N || s->n_dn > N || s->n_up + s->n_dn < 1)
+    return fail("particle numbers out of range");
+  if (s->model != SCALE_MODEL_HUBBARD && s->model != SCALE_MODEL_TJ) return fail("unknown model");
+  if (s->model == SCALE_MODEL_TJ && s->n_up + s->n_dn > N) return fail("t-J: more electrons than sites");
+  if (a->n_layers < 1 || a->n_layers > SCALE_MAX_LAYERS) return fail("n_layers must be in [1, 32]");
+  if (a->h < 1 || a->h > kMaxH) return fail("h must be in [1, 64]");
+  if (a->act != SCALE_ACT_TANH && a->act != SCALE_ACT_SILU) return fail("unknown activation");
+  if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED) return fail("unknown precision");
+  if (a->refresh_every < 1) return fail("refresh_every must be >= 1");
+  for (int l = 0; l < a->n_layers; ++l) {
+    const int k = a->ksize[l];
+    if (k < 1 || k > 7 || (k % 2) == 0) {
+      snprintf(buf, sizeof buf, "layer %d: kernel size must be odd in [1, 7]", l);
+      *why = buf;
+      return false;
+    }
+    if (a->residual[l] != 0 && a->residual[l] != 1) return fail("residual flags must be 0 or 1");
+  }
+  return true;
+}
+
+int64_t param_count(const scale_system* s, const scale_arch* a) {
+  const int64_t N = (int64_t)s->Lx * s->Ly, h = a->h, Ne = s->n_up + s->n_dn;
+  int64_t n = (a->per_site_embed ? N : 1) * 4 * h;
+  for (int l = 0; l < a->n_layers; ++l) n += (int64_t)a->ksize[l] * a->ksize[l] * h * h + h;
+  return n + h * 2 * Ne + 2 * Ne;
+}
+
+// Bonds of Eq. H_h: NN (i, i+x), (i, i+y); NNN (i, i+x+y), (i, i+x-y); open edges dropped.
+std::vector<int32_t> make_bonds(const Lattice& lat, int* nb_nn, int* nb_nnn) {
+  std::vector<int32_t> out;
+  const int offs[4][2] = {{1, 0}, {0, 1}, {1, 1}, {1, -1}};
+  *nb_nn = *nb_nnn = 0;
+  for (int kind = 0; kind < 2; ++kind) {
+    if (kind == 1 && lat.tp == 0.0) break;
+    for (int i = 0; i < lat.N; ++i)
+      for (int d = 0; d < 2; ++d) {
+        const int j = site_off(lat, i, offs[2 * kind + d][0], offs[2 * kind + d][1]);
+        if (j < 0) continue;
+        out.push_back(i);
+        out.push_back(j);
+        ++(kind == 0 ? *nb_nn : *nb_nnn);
+      }
+  }
+  return out;
+}
+
+struct Sizes {
+  size_t T, total;
+  int cap;
+};
+
+Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
+  Sizes z{};
+  const size_t N = (size_t)s->Lx * s->Ly, Ne = s->n_up + s->n_dn, h = a->h;
+  z.T = a->precision == SCALE_PREC_FP64 ? 8 : 4;
+  const size_t T = z.T;
+  const size_t nb_nn = 2 * N, nb_nnn = s->tp != 0.0 ? 2 * N : 0;  // upper bounds
+  z.cap = (int)(2 * (nb_nn + nb_nnn) + (s->model == SCALE_MODEL_TJ ? nb_nn : 0));
+  const size_t P = (size_t)param_count(s, a);
+  const size_t k0 = a->ksize[0];
+  size_t t = 0;
+  t += P * 8 + (T == 4 ? P * 4 : 0);
+  t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0);
+  t += (a->per_site_embed ? N : 1) * 4 * k0 * k0 * h * T;
+  t += (nb_nn + nb_nnn) * 2 * 4;
+  t += (size_t)B * (N + Ne * 4 + 2 * N * 4);
+  t += (size_t)B * N * h * T * 4;          // z0, HL, act_a, act_b
+  t += (size_t)B * Ne * Ne * T;            // Binv
+  t += (size_t)B * 2 * Ne * h * T;         // Pt
+  t += (size_t)B * (8 + 4 + 4 + 4 + 8 + 4 + 4 + 8 + 4 + 8);
+  t += (size_t)B * Ne * Ne * 8;            // Phi64
+  t += (size_t)B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T;  // commit scratch
+  t += (size_t)B * (N + 4 + 8 + 4);        // full-path chunk
+  t += (size_t)B * z.cap * (8 + 8 + 16);   // full-path coefficients, terms, moves
+  t += (size_t)(B + 1) * 8 + 64;
+  z.total = t;
+  return z;
+}
+
+template <typename TD, typename TS>
+__global__ void k_convert(const TS* __restrict__ in, TD* __restrict__ out, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+    out[q] = (TD)in[q];
+}
+
+template <typename P>
+cudaError_t alloc(scale_ctx* c, P** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e == cudaSuccess) c->allocated += bytes;
+  return e;
+}
+
+void free_all(scale_ctx* c) {
+  void* ptrs[] = {c->params64, c->params32, c->M0_64, c->M0_32, c->KE, c->bonds, c->occ, c->orb_of_slot,
+                  c->slot_of_orb, c->z0, c->HL, c->Binv, c->Pt, c->logabs, c->sign_slot, c->status,
+                  c->commits, c->drift, c->Phi64, c->act_a, c->act_b, c->list, c->list_count, c->stat_dev,
+                  c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_terms, c->full_moves,
+                  c->commit_scratch, c->la_tmp, c->sg_tmp, c->full_la, c->full_sg, c->full_diag,
+                  c->full_offsets, c->grad_scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+scale_status check_loaded(scale_ctx* c) {
+  if (!c) return SCALE_EINVAL;
+  if (!c->params_set) {
+    c->err = "parameters not set (scale_set_params)";
+    return SCALE_EINVAL;
+  }
+  if (c->B <= 0) {
+    c->err = "no samples loaded (scale_load)";
+    return SCALE_EINVAL;
+  }
+  return SCALE_OK;
+}
+
+scale_status require_lowrank(scale_ctx* c) {
+  if (!c->lowrank_ok) {
+    c->err = "low-rank path needs the SCALE layer layout: layer 0 with kernel size 1 or 3 and "
+             "site-wise layers (kernel size 1) after it; use the full-recompute path";
+    return SCALE_EUNSUPPORTED;
+  }
+  return SCALE_OK;
+}
+
+}  // namespace
+
+namespace scale {
+
+// FP64 re-factorisation of the samples selected by the commit counter / drift flag (or
+// all of them): network forward, ascending slot maps, Phi, Gauss-Jordan inverse, projector.
+cudaError_t refresh_samples(scale_ctx* c, bool force_all) {
+  cudaError_t e;
+  if ((e = launch_mark_refresh(c, force_all)) != cudaSuccess) return e;
+  if ((e = launch_forward(c, c->occ, c->B, c->list, true, c->Phi64)) != cudaSuccess) return e;
+  if ((e = launch_slots_list(c, c->list, c->B)) != cudaSuccess) return e;
+  if ((e = launch_gj(c, c->Phi64, c->Ne, c->B, c->list, true, c->fp64, c->Binv, c->logabs, c->sign_slot,
+                     c->status)) != cudaSuccess)
+    return e;
+  return launch_projector(c, c->B, c->list);
+}
+
+}  // namespace scale
+
+extern "C" {
+
+int64_t scale_param_count(const scale_system* sys, const scale_arch* arch) {
+  std::string why;
+  if (!validate(sys, arch, &why)) return -1;
+  return param_count(sys, arch);
+}
+
+size_t scale_footprint_bytes(const scale_system* sys, const scale_arch* arch, int32_t max_batch) {
+  std::string why;
+  if (!validate(sys, arch, &why) || max_batch < 1) return 0;
+  return sizes_of(sys, arch, max_batch).total;
+}
+
+scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32_t max_batch,
+                          size_t hbm_budget_bytes, void* cuda_stream, scale_ctx** out) {
+  if (!out) return SCALE_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (!validate(sys, arch, &why) || max_batch < 1 || max_batch > 65535) return SCALE_EINVAL;
+  const Sizes sz = sizes_of(sys, arch, max_batch);
+  if (hbm_budget_bytes && sz.total > hbm_budget_bytes) return SCALE_EBUDGET;
+  scale_ctx* c = new scale_ctx();
+  c->sys = *sys;
+  c->arch = *arch;
+  c->N = sys->Lx * sys->Ly;
+  c->Ne = sys->n_up + sys->n_dn;
+  c->h = arch->h;
+  c->L = arch->n_layers;
+  c->k0 = arch->ksize[0];
+  c->r0 = (c->k0 - 1) / 2;
+  c->fp64 = arch->precision == SCALE_PREC_FP64;
+  c->P = param_count(sys, arch);
+  c->B_max = max_batch;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->budget = hbm_budget_bytes;
+  c->lat = Lattice{sys->Lx, sys->Ly, sys->pbc_x, sys->pbc_y, c->N, sys->n_up, sys->n_dn, c->Ne, sys->model,
+                   sys->t, sys->tp, sys->U, sys->J};
+  c->lowrank_ok = c->k0 <= 3;
+  for (int l = 1; l < c->L; ++l) c->lowrank_ok = c->lowrank_ok && arch->ksize[l] == 1;
+  std::vector<int32_t> bonds = make_bonds(c->lat, &c->nb_nn, &c->nb_nnn);
+  c->max_moves = 2 * (c->nb_nn + c->nb_nnn) + (sys->model == SCALE_MODEL_TJ ? c->nb_nn : 0);
+  c->full_chunk = max_batch;
+  const size_t B = max_batch, N = c->N, Ne = c->Ne, h = c->h, T = c->fp64 ? 8 : 4;
+  const size_t Ns = arch->per_site_embed ? N : 1;
+  const size_t cap = std::max(1, c->max_moves);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t bytes) {
+    if (e == cudaSuccess) e = alloc(c, p, bytes);
+  };
+  A(&c->params64, c->P * 8);
+  if (!c->fp64) A(&c->params32, c->P * 4);
+  A(&c->M0_64, 2 * N * Ne * 8);
+  if (!c->fp64) A(&c->M0_32, 2 * N * Ne * 4);
+  A((char**)&c->KE, Ns * 4 * c->k0 * c->k0 * h * T);
+  A(&c->bonds, std::max<size_t>(bonds.size(), 2) * 4);
+  A(&c->occ, B * N);
+  A(&c->orb_of_slot, B * Ne * 4);
+  A(&c->slot_of_orb, B * 2 * N * 4);
+  A((char**)&c->z0, B * N * h * T);
+  A((char**)&c->HL, B * N * h * T);
+  A((char**)&c->Binv, B * Ne * Ne * T);
+  A((char**)&c->Pt, B * 2 * Ne * h * T);
+  A(&c->logabs, B * 8);
+  A(&c->sign_slot, B * 4);
+  A(&c->status, B * 4);
+  A(&c->commits, B * 4);
+  A(&c->drift, B * 8);
+  A(&c->Phi64, B * Ne * Ne * 8);
+  A((char**)&c->act_a, B * N * h * T);
+  A((char**)&c->act_b, B * N * h * T);
+  A(&c->list, B * 4);
+  A(&c->list_count, 16);
+  A(&c->stat_dev, 4 * 8);
+  A(&c->move_count, B * 4);
+  A((char**)&c->commit_scratch, B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T);
+  A(&c->la_tmp, B * 8);
+  A(&c->sg_tmp, B * 4);
+  A(&c->full_occ, B * N);
+  A(&c->full_owner, B * 4);
+  A(&c->full_la, B * 8);
+  A(&c->full_sg, B * 4);
+  A(&c->full_diag, B * 8);
+  A(&c->full_offsets, (B + 1) * 8);
+  A(&c->full_coeff, B * cap * 8);
+  A(&c->full_terms, B * cap * 8);
+  A(&c->full_moves, B * cap * 16);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return SCALE_ENOMEM;
+  }
+  if (!bonds.empty())
+    e = cudaMemcpyAsync(c->bonds, bonds.data(), bonds.size() * 4, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stat_dev, 0, 32, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->drift, 0, B * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->commits, 0, B * 4, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return SCALE_ECUDA;
+  }
+  c->stats.max_moves = c->max_moves;
+  *out = c;
+  return SCALE_OK;
+}
+
+scale_status scale_set_params(scale_ctx* c, const double* params, const double* M0) {
+  if (!c || !params || !M0) return SCALE_EINVAL;
+  const size_t N = c->N, Ne = c->Ne;
+  SCALE_TRY(c, cudaMemcpyAsync(c->params64, params, c->P * 8, cudaMemcpyDeviceToDevice, c->stream));
+  SCALE_TRY(c, cudaMemcpyAsync(c->M0_64, M0, 2 * N * Ne * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (!c->fp64) {
+    k_convert<float, double><<<1024, 256, 0, c->stream>>>(c->params64, c->params32, (size_t)c->P);
+    k_convert<float, double><<<1024, 256, 0, c->stream>>>(c->M0_64, c->M0_32, 2 * N * Ne);
+    SCALE_TRY(c, cudaGetLastError());
+  }
+  SCALE_TRY(c, launch_build_ke(c));
+  c->params_set = true;
+  c->B = 0;
+  return SCALE_OK;
+}
+
+scale_status scale_load(scale_ctx* c, const int8_t* occ, int32_t B, int32_t* sample_status) {
+  if (!c || !occ || B < 1) return SCALE_EINVAL;
+  if (!c->params_set) {
+    c->err = "parameters not set (scale_set_params)";
+    return SCALE_EINVAL;
+  }
+  if (B > c->B_max) {
+    c->err = "batch larger than max_batch";
+    return SCALE_EINVAL;
+  }
+  c->B = B;
+  SCALE_TRY(c, cudaMemcpyAsync(c->occ, occ, (size_t)B * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  SCALE_TRY(c, cudaMemsetAsync(c->drift, 0, (size_t)B * 8, c->stream));
+  SCALE_TRY(c, launch_slots(c, c->occ, B));
+  SCALE_TRY(c, launch_forward(c, c->occ, B, nullptr, true, c->Phi64));
+  SCALE_TRY(c, launch_gj(c, c->Phi64, c->Ne, B, nullptr, true, c->fp64, c->Binv, c->logabs, c->sign_slot, c->status));
+  SCALE_TRY(c, launch_projector(c, B, nullptr));
+  if (sample_status)
+    SCALE_TRY(c, cudaMemcpyAsync(sample_status, c->status, (size_t)B * 4, cudaMemcpyDeviceToDevice, c->stream));
+  c->stats.batch = B;
+  return SCALE_OK;
+}
+
+scale_status scale_log_psi(scale_ctx* c, double* logabs, int32_t* sign) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  SCALE_TRY(c, launch_logpsi_out(c, logabs, sign));
+  return SCALE_OK;
+}
+
+scale_status scale_get_occ(scale_ctx* c, int8_t* occ) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  if (!occ) return SCALE_EINVAL;
+  SCALE_TRY(c, cudaMemcpyAsync(occ, c->occ, (size_t)c->B * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  return SCALE_OK;
+}
+
+scale_status scale_ratios(scale_ctx* c, const int32_t* moves, int32_t M, double* ratio) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  if (!moves || !ratio || M < 1) return SCALE_EINVAL;
+  if ((s = require_lowrank(c)) != SCALE_OK) return s;
+  SCALE_TRY(c, launch_ratios(c, moves, M, ratio));
+  return SCALE_OK;
+}
+
+scale_status scale_local_energy(scale_ctx* c, int32_t path, double* eloc) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  if (!eloc) return SCALE_EINVAL;
+  if (path == SCALE_PATH_LOWRANK) {
+    if ((s = require_lowrank(c)) != SCALE_OK) return s;
+    SCALE_TRY(c, launch_eloc_lowrank(c, eloc));
+    c->stats.n_eloc += c->B;
+  } else if (path == SCALE_PATH_FULL) {
+    SCALE_TRY(c, launch_eloc_full(c, eloc));
+    c->stats.n_eloc_full += c->B;
+  } else {
+    return SCALE_EINVAL;
+  }
+  return SCALE_OK;
+}
+
+scale_status scale_commit(scale_ctx* c, const int32_t* moves) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  if (!moves) return SCALE_EINVAL;
+  if ((s = require_lowrank(c)) != SCALE_OK) return s;
+  SCALE_TRY(c, launch_commit(c, moves));
+  SCALE_TRY(c, refresh_samples(c, false));
+  return SCALE_OK;
+}
+
+scale_status scale_refresh(scale_ctx* c, int32_t force_all) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  SCALE_TRY(c, refresh_samples(c, force_all != 0));
+  return SCALE_OK;
+}
+
+scale_status scale_grad_logpsi(scale_ctx* c, double* grad, int32_t recompute) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  if (!grad) return SCALE_EINVAL;
+  SCALE_TRY(c, launch_grad(c, grad, recompute));
+  return SCALE_OK;
+}
+
+scale_status scale_get_stats(scale_ctx* c, scale_stats* out) {
+  if (!c || !out) return SCALE_EINVAL;
+  double host[4];
+  SCALE_TRY(c, cudaMemcpyAsync(host, c->stat_dev, sizeof host, cudaMemcpyDeviceToHost, c->stream));
+  SCALE_TRY(c, cudaStreamSynchronize(c->stream));
+  *out = c->stats;
+  out->drift_max = host[0];
+  int32_t cnt[6];
+  std::memcpy(cnt, &host[1], sizeof cnt);
+  out->n_commits = cnt[0];
+  out->n_refresh = cnt[1];
+  out->n_drift_refresh = cnt[2];
+  return SCALE_OK;
+}
+
+const char* scale_last_error(scale_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void scale_destroy(scale_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

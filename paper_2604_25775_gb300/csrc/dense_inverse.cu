@@ -1,0 +1,251 @@
+// dense_inverse.cu -- batched Gauss-Jordan elimination with partial pivoting.
+//
+// One CTA per matrix. It returns log|det|, the sign and (inverse mode) the inverse in the
+// library's dual-row layout Binv[c][k] = (A^-1)[k][c]; "det-only" mode restricts the
+// elimination to the rows not yet pivoted and the columns to the right, which is LU with
+// partial pivoting (n^3/3 multiply-adds) -- both are the "single LU decomposition" of
+// Sec. II.C giving the determinant and the inverse together.
+//
+// Blocking. Pivots are taken W columns at a time. The W-column panel is swept in shared
+// memory; the W elementary row operations of the block combine into T = I + U P^T, where
+// the columns of U are the swept panel columns minus the unit vectors of the pivot rows
+// and P selects the pivot rows. Every other column then takes one rank-W update
+//     A[i][c] += sum_j U[i][j] A_old[p_j][c]
+// so each matrix element is read and written once per W pivots. The matrix stays in
+// global memory (L2-resident while the CTAs in flight fit), the work is the FMA pipe of
+// the working type; on sm_103a FP64 this kernel is DFMA-bound.
+//
+// Pivot choice: largest |value| among unpivoted rows, ties to the lowest row index.
+// Pivoting is implicit (no row swaps); the pivot row of column k is p[k] and the final
+// storage holds A^-1[k][p[j]] at (p[k], j).
+#include <algorithm>
+
+#include "scale_internal.cuh"
+
+namespace scale {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename TW>
+struct ArgMax {
+  TW v;
+  int i;
+};
+
+template <typename TW>
+__device__ __forceinline__ void argmax_merge(TW& v, int& i, TW v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+
+// TW: working precision; TOUT: inverse output precision.
+template <typename TW, typename TOUT, bool kInverse, int W>
+__global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, const int32_t* __restrict__ list,
+                                                 TOUT* __restrict__ binv, double* __restrict__ logabs_out,
+                                                 int32_t* __restrict__ sign_out, int32_t* __restrict__ status) {
+  extern __shared__ unsigned char smem_raw[];
+  TW* panel = reinterpret_cast<TW*>(smem_raw);   // [n][W]
+  TW* prow = panel + (size_t)n * W;              // [W][n]
+  TW* colk = prow + (size_t)W * n;               // [n]
+  TW* rowp = colk + n;                           // [W]
+  int* piv = reinterpret_cast<int*>(rowp + W);   // [n] pivot row of column k
+  int* qinv = piv + n;                           // [n] column whose pivot row is r
+  unsigned char* used = reinterpret_cast<unsigned char*>(qinv + n);  // [n]
+  __shared__ TW red_v[kThreads / 32];
+  __shared__ int red_i[kThreads / 32];
+  __shared__ int s_p;
+  __shared__ int s_singular;
+
+  const int b = list ? list[blockIdx.x] : blockIdx.x;
+  if (b < 0) return;
+  TW* A = mats + (size_t)b * n * n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int i = tid; i < n; i += kThreads) used[i] = 0;
+  if (tid == 0) s_singular = 0;
+  double logdet = 0.0;  // kept by thread 0
+  int sgn = 1;
+  __syncthreads();
+
+  for (int K0 = 0; K0 < n; K0 += W) {
+    const int w = min(W, n - K0);
+    // panel <- columns [K0, K0+w)
+    for (int q = tid; q < n * w; q += kThreads) {
+      const int i = q / w, j = q - i * w;
+      panel[i * W + j] = A[(size_t)i * n + K0 + j];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < w; ++jj) {
+      const int k = K0 + jj;
+      // pivot search over unpivoted rows
+      TW bv = TW(-1);
+      int bi = n;
+      for (int i = tid; i < n; i += kThreads) {
+        if (used[i]) continue;
+        const TW v = fabs(panel[i * W + jj]);
+        argmax_merge(bv, bi, v, i);
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const TW v2 = __shfl_down_sync(0xffffffffu, bv, off);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
+        argmax_merge(bv, bi, v2, i2);
+      }
+      if (lane == 0) {
+        red_v[warp] = bv;
+        red_i[warp] = bi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        TW v = red_v[0];
+        int i = red_i[0];
+        for (int q = 1; q < kThreads / 32; ++q) argmax_merge(v, i, red_v[q], red_i[q]);
+        if (!(v > TW(0)) || i >= n) {
+          s_singular = 1;
+          i = 0;
+        }
+        s_p = i;
+      }
+      __syncthreads();
+      if (s_singular) break;
+      const int p = s_p;
+      const TW pv = panel[p * W + jj];
+      const TW inv = TW(1) / pv;
+      // snapshot the pivot row (panel part) and column jj before updating
+      for (int j = tid; j < w; j += kThreads) rowp[j] = (j == jj) ? inv : panel[p * W + j] * inv;
+      for (int i = tid; i < n; i += kThreads) colk[i] = panel[i * W + jj];
+      if (tid == 0) {
+        piv[k] = p;
+        used[p] = 1;
+        logdet += log(fabs((double)pv));
+        if (pv < TW(0)) sgn = -sgn;
+      }
+      __syncthreads();
+      for (int q = tid; q < n * w; q += kThreads) {
+        const int i = q / w, j = q - i * w;
+        if (i == p) {
+          panel[i * W + j] = rowp[j];
+        } else if (kInverse || !used[i]) {
+          const TW f = colk[i];
+          const TW base = (j == jj) ? TW(0) : panel[i * W + j];
+          panel[i * W + j] = base - f * rowp[j];
+        }
+      }
+      __syncthreads();
+    }
+    if (s_singular) break;
+    // old pivot rows of the block (all columns outside the panel)
+    for (int q = tid; q < w * n; q += kThreads) {
+      const int j = q / n, c = q - j * n;
+      prow[j * n + c] = A[(size_t)piv[K0 + j] * n + c];
+    }
+    __syncthreads();
+    // rank-w update of the columns outside the panel
+    const int c_lo = kInverse ? 0 : K0 + w;
+    const int ncols = n - c_lo;
+    for (int q = tid; q < n * ncols; q += kThreads) {
+      const int i = q / ncols, c = c_lo + (q - i * ncols);
+      if (c >= K0 && c < K0 + w) continue;
+      if (!kInverse && used[i]) continue;
+      TW acc = A[(size_t)i * n + c];
+#pragma unroll 4
+      for (int j = 0; j < w; ++j) {
+        const TW u = panel[i * W + j] - ((piv[K0 + j] == i) ? TW(1) : TW(0));
+        acc += u * prow[j * n + c];
+      }
+      A[(size_t)i * n + c] = acc;
+    }
+    // write the swept panel back
+    for (int q = tid; q < n * w; q += kThreads) {
+      const int i = q / w, j = q - i * w;
+      A[(size_t)i * n + K0 + j] = panel[i * W + j];
+    }
+    __syncthreads();
+  }
+
+  if (tid == 0) {
+    int st = 0;
+    double la = logdet;
+    int sg = sgn;
+    if (s_singular) {
+      st = SCALE_SAMPLE_SINGULAR;
+      la = -INFINITY;
+      sg = 0;
+    } else {
+      // sign of the permutation k -> piv[k]
+      for (int k = 0; k < n; ++k) qinv[k] = 0;
+      int parity = 0;
+      for (int k = 0; k < n; ++k) {
+        if (qinv[k]) continue;
+        int j = k, len = 0;
+        while (!qinv[j]) {
+          qinv[j] = 1;
+          j = piv[j];
+          ++len;
+        }
+        parity += len - 1;
+      }
+      if (parity & 1) sg = -sg;
+    }
+    if (logabs_out) logabs_out[b] = la;
+    if (sign_out) sign_out[b] = sg;
+    if (status && st) status[b] |= st;
+  }
+  if (!kInverse) return;
+  __syncthreads();
+  if (s_singular) {
+    if (binv)
+      for (int q = tid; q < n * n; q += kThreads) binv[(size_t)b * n * n + q] = TOUT(0);
+    return;
+  }
+  for (int k = tid; k < n; k += kThreads) qinv[piv[k]] = k;
+  __syncthreads();
+  // Binv[s][cf] = A^-1[cf][s] = A_final[piv[cf]][qinv[s]]
+  for (int q = tid; q < n * n; q += kThreads) {
+    const int s = q / n, cf = q - s * n;
+    binv[(size_t)b * n * n + q] = (TOUT)A[(size_t)piv[cf] * n + qinv[s]];
+  }
+}
+
+template <typename TW, typename TOUT, bool kInverse, int W>
+cudaError_t run_gj(cudaStream_t st, TW* mats, int n, int B, const int32_t* list, TOUT* binv, double* la,
+                   int32_t* sg, int32_t* status) {
+  const size_t smem = sizeof(TW) * ((size_t)2 * n * W + n + W) + sizeof(int) * 2 * n + n + 16;
+  auto kern = k_gj<TW, TOUT, kInverse, W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<B, kThreads, smem, st>>>(mats, n, list, binv, la, sg, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// FP64 inverse (out_fp64: Binv in double, else float) or determinant only, for B matrices
+// [B][n][n] stored in Phi (overwritten).
+cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32_t* list, bool inverse,
+                      bool out_fp64, void* Binv, double* logabs, int32_t* sign, int32_t* status) {
+  double* A = const_cast<double*>(Phi);
+  if (B <= 0) return cudaSuccess;
+  if (inverse) {
+    if (out_fp64) {
+      if (n > 448) return run_gj<double, double, true, 8>(c->stream, A, n, B, list, (double*)Binv, logabs, sign, status);
+      return run_gj<double, double, true, 16>(c->stream, A, n, B, list, (double*)Binv, logabs, sign, status);
+    }
+    if (n > 448) return run_gj<double, float, true, 8>(c->stream, A, n, B, list, (float*)Binv, logabs, sign, status);
+    return run_gj<double, float, true, 16>(c->stream, A, n, B, list, (float*)Binv, logabs, sign, status);
+  }
+  if (n > 448) return run_gj<double, double, false, 8>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
+  return run_gj<double, double, false, 16>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
+}
+
+// Determinant only, FP32 working precision (full-recompute path in mixed mode).
+cudaError_t launch_det_f32(scale_ctx* c, float* mats, int n, int B, double* logabs, int32_t* sign) {
+  if (B <= 0) return cudaSuccess;
+  if (n > 448) return run_gj<float, float, false, 8>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
+  return run_gj<float, float, false, 16>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
+}
+
+}  // namespace scale

@@ -1,0 +1,305 @@
+// forward.cu -- network forward (Sec. II.B), slot bookkeeping, Slater-matrix build,
+// layer-0 conv-of-embedding table and the log|psi| output convention.
+#include <algorithm>
+
+#include "scale_internal.cuh"
+
+namespace scale {
+
+namespace {
+
+// One network layer for every (sample, site, channel):
+//   out_i[c] = res * in_i[c] + act(b[c] + sum_{offsets d} sum_c' in_{i+d}[c'] K[d][c'][c])
+// Layer 0 reads its input from the embedding tables E_i[n_i] (Sec. II.B). Offsets wrap on
+// periodic axes and read zeros past open edges (Eq. conv, "same boundary conditions as
+// the Hamiltonian").
+template <typename T>
+__global__ void k_layer(Lattice lat, Net<T> net, int l, const int8_t* __restrict__ occ,
+                        const int32_t* __restrict__ list, const T* __restrict__ in, T* __restrict__ out,
+                        T* __restrict__ zout, int B) {
+  const int h = net.h, N = lat.N;
+  const int row = blockIdx.y;  // position in the launch
+  const int b = list ? list[row] : row;
+  if (b < 0) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * h) return;
+  const int i = idx / h, c = idx - i * h;
+  const int k = net.ksize[l], r = (k - 1) / 2;
+  const T* K = net.kernel[l];
+  T z = net.bias[l][c];
+  const int8_t* ob = occ + (size_t)b * N;
+  const T* ib = in ? in + (size_t)b * N * h : nullptr;
+  for (int ky = 0; ky < k; ++ky)
+    for (int kx = 0; kx < k; ++kx) {
+      const int j = site_off(lat, i, kx - r, ky - r);
+      if (j < 0) continue;
+      const T* w = K + (size_t)(ky * k + kx) * h * h + c;
+      const T* x = (l == 0) ? net.embed + ((size_t)(net.per_site ? j * 4 : 0) + (ob[j] & 3)) * h
+                            : ib + (size_t)j * h;
+#pragma unroll 8
+      for (int ci = 0; ci < h; ++ci) z += x[ci] * w[(size_t)ci * h];
+    }
+  T self = T(0);
+  if (net.resid[l]) {
+    self = (l == 0) ? net.embed[((size_t)(net.per_site ? i * 4 : 0) + (ob[i] & 3)) * h + c]
+                    : ib[(size_t)i * h + c];
+  }
+  out[(size_t)b * N * h + idx] = self + act_fn<T>(net.act, z);
+  if (zout) zout[(size_t)b * N * h + idx] = z;
+}
+
+// Block-wide exclusive scan of 0/1 flags over 2N orbitals; writes the ascending list of
+// occupied orbitals. Returns the count (valid in every thread).
+__device__ int occupied_list(const int8_t* ob, int N, int* list_out, int* s_tmp) {
+  // s_tmp: at least blockDim.x ints
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int per = (2 * N + nt - 1) / nt;
+  const int o0 = tid * per;
+  int cnt = 0;
+  for (int o = o0; o < min(o0 + per, 2 * N); ++o) {
+    const int s = o / N, i = o - s * N;
+    cnt += (ob[i] >> s) & 1;
+  }
+  s_tmp[tid] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int t = 0; t < nt; ++t) {
+      const int v = s_tmp[t];
+      s_tmp[t] = acc;
+      acc += v;
+    }
+    s_tmp[nt] = acc;
+  }
+  __syncthreads();
+  int pos = s_tmp[tid];
+  for (int o = o0; o < min(o0 + per, 2 * N); ++o) {
+    const int s = o / N, i = o - s * N;
+    if ((ob[i] >> s) & 1) list_out[pos++] = o;
+  }
+  __syncthreads();
+  return s_tmp[nt];
+}
+
+// Slot maps (ascending orbital order), particle-number and projection checks.
+// commits: at load (stagger > 0) sample b's counter starts at b mod stagger so that about
+// B / refresh_every samples re-factorise per commit call instead of the whole batch at
+// once; after a refresh it restarts at 0.
+__global__ void k_slots(Lattice lat, const int8_t* __restrict__ occ, const int32_t* __restrict__ list,
+                        int32_t* __restrict__ orb_of_slot, int32_t* __restrict__ slot_of_orb,
+                        int32_t* __restrict__ status, int32_t* __restrict__ commits, int stagger) {
+  extern __shared__ int sm[];
+  const int b = list ? list[blockIdx.x] : blockIdx.x;
+  if (b < 0) return;
+  const int N = lat.N, Ne = lat.Ne;
+  int* olist = sm;               // [2N]
+  int* tmp = sm + 2 * N;         // [blockDim + 1]
+  __shared__ int s_up, s_dn, s_dbl;
+  if (threadIdx.x == 0) { s_up = 0; s_dn = 0; s_dbl = 0; }
+  __syncthreads();
+  const int8_t* ob = occ + (size_t)b * N;
+  int up = 0, dn = 0, dbl = 0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    up += ob[i] & 1;
+    dn += (ob[i] >> 1) & 1;
+    dbl += ob[i] == 3;
+    if (ob[i] < 0 || ob[i] > 3) up += 1 << 20;  // invalid local state
+  }
+  atomicAdd(&s_up, up);
+  atomicAdd(&s_dn, dn);
+  atomicAdd(&s_dbl, dbl);
+  const int n = occupied_list(ob, N, olist, tmp);
+  int st = 0;
+  if (s_up != lat.n_up || s_dn != lat.n_dn) st |= SCALE_SAMPLE_BAD_COUNT;
+  if (lat.model == SCALE_MODEL_TJ && s_dbl > 0) st |= SCALE_SAMPLE_DOUBLE_OCC;
+  for (int o = threadIdx.x; o < 2 * N; o += blockDim.x) slot_of_orb[(size_t)b * 2 * N + o] = -1;
+  __syncthreads();
+  if (st == 0) {
+    for (int a = threadIdx.x; a < n && a < Ne; a += blockDim.x) {
+      orb_of_slot[(size_t)b * Ne + a] = olist[a];
+      slot_of_orb[(size_t)b * 2 * N + olist[a]] = a;
+    }
+  } else {
+    for (int a = threadIdx.x; a < Ne; a += blockDim.x) orb_of_slot[(size_t)b * Ne + a] = -1;
+  }
+  if (threadIdx.x == 0) {
+    status[b] = st;
+    if (commits) commits[b] = stagger > 0 ? b % stagger : 0;
+  }
+}
+
+// Slater matrix in ascending orbital order (Sec. II.B "Orbital Projection"):
+//   Phi[a][k] = M0[o_a][k] + proj_b[s*Ne+k] + sum_c H(L)_i[c] proj_w[c][s*Ne+k],
+// o_a = s*N + i the a-th occupied orbital. Computed in T, stored as TO.
+template <typename T, typename TO>
+__global__ void k_phi(Lattice lat, Net<T> net, const int8_t* __restrict__ occ, const int32_t* __restrict__ list,
+                      const T* __restrict__ HL, TO* __restrict__ phi) {
+  extern __shared__ int sm[];
+  const int b = list ? list[blockIdx.x] : blockIdx.x;
+  if (b < 0) return;
+  const int N = lat.N, Ne = lat.Ne, h = net.h;
+  int* olist = sm;
+  int* tmp = sm + 2 * N;
+  const int n = occupied_list(occ + (size_t)b * N, N, olist, tmp);
+  TO* P = phi + (size_t)b * Ne * Ne;
+  if (n != Ne) {  // invalid sample: leave a zero matrix (singular)
+    for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = TO(0);
+    return;
+  }
+  const T* Hb = HL + (size_t)b * N * h;
+  for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) {
+    const int a = q / Ne, k = q - a * Ne;
+    const int o = olist[a], s = o / N, i = o - s * N;
+    T v = net.M0[(size_t)o * Ne + k] + net.proj_b[s * Ne + k];
+    const T* w = net.proj_w + s * Ne + k;
+    const T* x = Hb + (size_t)i * h;
+    for (int c = 0; c < h; ++c) v += x[c] * w[(size_t)c * 2 * Ne];
+    P[q] = (TO)v;
+  }
+}
+
+// KE[t][n][d][c] = sum_c' E_t[n][c'] K_0[d][c'][c]: layer-0 response to the embedding of
+// state n on site t, for every stencil offset d.
+template <typename T>
+__global__ void k_build_ke(Net<T> net, int Ns, T* __restrict__ KE) {
+  const int h = net.h, k = net.ksize[0], kk = k * k;
+  const size_t total = (size_t)Ns * 4 * kk * h;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int c = q % h;
+    const int d = (q / h) % kk;
+    const size_t tn = q / ((size_t)h * kk);  // t*4 + n
+    const T* e = net.embed + tn * h;
+    const T* w = net.kernel[0] + (size_t)d * h * h + c;
+    T acc = T(0);
+    for (int ci = 0; ci < h; ++ci) acc += e[ci] * w[(size_t)ci * h];
+    KE[q] = acc;
+  }
+}
+
+// log|psi| and sign in the ascending convention: sign = sign_slot * parity of the slot
+// permutation orb_of_slot (inversions counted directly).
+__global__ void k_logpsi_out(int Ne, const int32_t* __restrict__ orb_of_slot, const double* __restrict__ la_slot,
+                             const int32_t* __restrict__ sg_slot, const int32_t* __restrict__ status,
+                             double* __restrict__ logabs, int32_t* __restrict__ sign) {
+  const int b = blockIdx.x;
+  const int32_t* os = orb_of_slot + (size_t)b * Ne;
+  int inv = 0;
+  for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) {
+    const int a = q / Ne, c = q - a * Ne;
+    inv += (a < c) && (os[a] > os[c]);
+  }
+  __shared__ int s_inv;
+  if (threadIdx.x == 0) s_inv = 0;
+  __syncthreads();
+  atomicAdd(&s_inv, inv);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool bad = status[b] & (SCALE_SAMPLE_BAD_COUNT | SCALE_SAMPLE_DOUBLE_OCC | SCALE_SAMPLE_SINGULAR);
+    const int sg = bad ? 0 : sg_slot[b] * ((s_inv & 1) ? -1 : 1);
+    if (logabs) logabs[b] = bad ? -INFINITY : la_slot[b];
+    if (sign) sign[b] = sg;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+Net<T> make_net(scale_ctx* c) {
+  Net<T> n{};
+  n.h = c->h;
+  n.L = c->L;
+  n.act = c->arch.act;
+  n.per_site = c->arch.per_site_embed;
+  const T* base = c->fp64 ? (const T*)c->params64 : (const T*)c->params32;
+  int64_t p = 0;
+  n.embed = base + p;
+  p += (int64_t)(c->arch.per_site_embed ? c->N : 1) * 4 * c->h;
+  for (int l = 0; l < c->L; ++l) {
+    n.ksize[l] = c->arch.ksize[l];
+    n.resid[l] = c->arch.residual[l];
+    n.kernel[l] = base + p;
+    p += (int64_t)n.ksize[l] * n.ksize[l] * c->h * c->h;
+    n.bias[l] = base + p;
+    p += c->h;
+  }
+  n.proj_w = base + p;
+  p += (int64_t)c->h * 2 * c->Ne;
+  n.proj_b = base + p;
+  n.M0 = c->fp64 ? (const T*)c->M0_64 : (const T*)c->M0_32;
+  n.KE = (const T*)c->KE;
+  return n;
+}
+
+template Net<double> make_net<double>(scale_ctx*);
+template Net<float> make_net<float>(scale_ctx*);
+
+namespace {
+template <typename T>
+cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, bool keep_cache,
+                      double* phi_out, void* phi_f32) {
+  const Net<T> net = make_net<T>(c);
+  const int N = c->N, h = c->h;
+  dim3 grid((N * h + 127) / 128, B);
+  T* bufs[2] = {(T*)c->act_a, (T*)c->act_b};
+  const T* in = nullptr;
+  for (int l = 0; l < c->L; ++l) {
+    T* out = (l == c->L - 1 && keep_cache) ? (T*)c->HL : bufs[l & 1];
+    T* zo = (l == 0 && keep_cache) ? (T*)c->z0 : nullptr;
+    k_layer<T><<<grid, 128, 0, c->stream>>>(c->lat, net, l, occ, list, in, out, zo, B);
+    in = out;
+  }
+  const size_t smem = sizeof(int) * (2 * N + 257);
+  if (phi_out)
+    k_phi<T, double><<<B, 256, smem, c->stream>>>(c->lat, net, occ, list, in, phi_out);
+  if (phi_f32)
+    k_phi<T, float><<<B, 256, smem, c->stream>>>(c->lat, net, occ, list, in, (float*)phi_f32);
+  return cudaGetLastError();
+}
+}  // namespace
+
+// Forward every listed sample of occ; keep_cache writes z0 / HL of the context.
+cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, bool keep_cache,
+                           double* phi_out) {
+  if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, nullptr);
+  return forward_t<float>(c, occ, B, list, keep_cache, phi_out, nullptr);
+}
+
+// Forward for the full-recompute path: Slater matrices of B configurations into phi
+// (double in FP64 mode, float in mixed mode); features go to the scratch buffers.
+cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, void* phi) {
+  if (c->fp64) return forward_t<double>(c, occ, B, nullptr, false, (double*)phi, nullptr);
+  return forward_t<float>(c, occ, B, nullptr, false, nullptr, phi);
+}
+
+cudaError_t launch_slots(scale_ctx* c, const int8_t* occ, int B) {
+  const size_t smem = sizeof(int) * (2 * c->N + 257);
+  k_slots<<<B, 256, smem, c->stream>>>(c->lat, occ, nullptr, c->orb_of_slot, c->slot_of_orb, c->status,
+                                        c->commits, c->arch.refresh_every);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slots_list(scale_ctx* c, const int32_t* list, int B) {
+  const size_t smem = sizeof(int) * (2 * c->N + 257);
+  k_slots<<<B, 256, smem, c->stream>>>(c->lat, c->occ, list, c->orb_of_slot, c->slot_of_orb, c->status,
+                                        c->commits, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_ke(scale_ctx* c) {
+  const int Ns = c->arch.per_site_embed ? c->N : 1;
+  const size_t total = (size_t)Ns * 4 * c->k0 * c->k0 * c->h;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  if (c->fp64)
+    k_build_ke<double><<<blocks, 256, 0, c->stream>>>(make_net<double>(c), Ns, (double*)c->KE);
+  else
+    k_build_ke<float><<<blocks, 256, 0, c->stream>>>(make_net<float>(c), Ns, (float*)c->KE);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logpsi_out(scale_ctx* c, double* logabs, int32_t* sign) {
+  k_logpsi_out<<<c->B, 256, 0, c->stream>>>(c->Ne, c->orb_of_slot, c->logabs, c->sign_slot, c->status,
+                                             logabs, sign);
+  return cudaGetLastError();
+}
+
+}  // namespace scale

@@ -1,0 +1,369 @@
+// lowrank.cu -- local energies and amplitude ratios by the cached-network + rank-r
+// determinant update of Sec. II.C, and the projector P_s = W_s Phi^-1 it relies on.
+//
+// One CTA per sample. Connected configurations are enumerated on the device in a fixed
+// order (NN bonds, then NNN bonds, each with spin up then down; then t-J exchanges on NN
+// bonds), compacted chunk by chunk, and handed to the warps (one move per warp at a time,
+// move.cuh). Per-move contributions are summed in enumeration order, so E_loc does not
+// depend on scheduling.
+//
+// Matrix elements in slot order (a moved electron keeps its determinant row):
+//   hop     -t (NN) / -t' (NNN) times det R   (its Jordan-Wigner sign and the row
+//           permutation sign of the ascending convention cancel),
+//   exchange (J/2)(S+_i S-_j + h.c.) = -(J/2) (c+_{i up} c_{j up})(c+_{j dn} c_{i dn}):
+//           -J/2 times det R.
+// Diagonal: Hubbard U * (doubly occupied sites); t-J J sum_<ij> Sz_i Sz_j.
+#include <algorithm>
+
+#include "move.cuh"
+
+namespace scale {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kChunk = 256;
+
+struct MoveDesc {
+  int kind, src, dst, spin;
+};
+
+struct LowrankArgs {
+  Lattice lat;
+  int k0;
+  const int8_t* occ;
+  const int32_t* slot_of_orb;
+  const void* z0;
+  const void* HL;
+  const void* Binv;
+  const void* Pt;
+  const int32_t* bonds;
+  int nb_nn, nb_nnn;
+  const int32_t* status;
+  double* out;           // eloc [B] or ratio [B][M]
+  int32_t* move_count;   // [B] (eloc only)
+  const int32_t* moves;  // explicit moves [B][M][4] (ratios only)
+  int M;
+};
+
+// Candidate id -> move (kind -1 when not allowed in the current configuration).
+__device__ __forceinline__ MoveDesc candidate(const LowrankArgs& a, const int8_t* occ, int id, double* coeff) {
+  MoveDesc m{-1, 0, 0, 0};
+  const int nb = a.nb_nn + a.nb_nnn;
+  if (id < 2 * nb) {
+    const int q = id >> 1, s = id & 1;
+    const int i = a.bonds[2 * q], j = a.bonds[2 * q + 1];
+    const int oi = occ[i], oj = occ[j];
+    const bool hi = (oi >> s) & 1, hj = (oj >> s) & 1;
+    if (hi == hj) return m;
+    const int src = hi ? i : j, dst = hi ? j : i;
+    if (a.lat.model == SCALE_MODEL_TJ && occ[dst] != 0) return m;
+    m.kind = 0;
+    m.src = src;
+    m.dst = dst;
+    m.spin = s;
+    *coeff = (q < a.nb_nn) ? -a.lat.t : -a.lat.tp;
+    return m;
+  }
+  const int q = id - 2 * nb;
+  const int i = a.bonds[2 * q], j = a.bonds[2 * q + 1];
+  const int oi = occ[i], oj = occ[j];
+  if ((oi == 1 && oj == 2) || (oi == 2 && oj == 1)) {
+    m.kind = 1;
+    m.src = i;
+    m.dst = j;
+    m.spin = 0;
+    *coeff = -0.5 * a.lat.J;
+  }
+  return m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.lat.N, Ne = a.lat.Ne, h = net.h;
+  MoveScratch<T>* ms_all = reinterpret_cast<MoveScratch<T>*>(smem);
+  MoveDesc* moves = reinterpret_cast<MoveDesc*>(ms_all + kWarps);
+  double* contrib = reinterpret_cast<double*>(moves + kChunk);
+  double* coeffs = contrib + kChunk;
+  int32_t* slot_s = reinterpret_cast<int32_t*>(coeffs + kChunk);
+  int8_t* occ_s = reinterpret_cast<int8_t*>(slot_s + 2 * N);
+  __shared__ int warp_cnt[kWarps];
+  __shared__ double s_diag;
+
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int st = a.status[b];
+  if (st & (SCALE_SAMPLE_BAD_COUNT | SCALE_SAMPLE_DOUBLE_OCC | SCALE_SAMPLE_SINGULAR)) {
+    if (tid == 0) {
+      a.out[b] = CUDART_NAN;
+      if (a.move_count) a.move_count[b] = 0;
+    }
+    return;
+  }
+  for (int i = tid; i < N; i += blockDim.x) occ_s[i] = a.occ[(size_t)b * N + i];
+  for (int o = tid; o < 2 * N; o += blockDim.x) slot_s[o] = a.slot_of_orb[(size_t)b * 2 * N + o];
+  __syncthreads();
+  if (tid == 0) {
+    double d = 0.0;
+    if (a.lat.model == SCALE_MODEL_HUBBARD) {
+      int nd = 0;
+      for (int i = 0; i < N; ++i) nd += occ_s[i] == 3;
+      d = a.lat.U * nd;
+    } else {
+      for (int q = 0; q < a.nb_nn; ++q) {
+        const int i = a.bonds[2 * q], j = a.bonds[2 * q + 1];
+        const double szi = 0.5 * ((occ_s[i] & 1) - ((occ_s[i] >> 1) & 1));
+        const double szj = 0.5 * ((occ_s[j] & 1) - ((occ_s[j] >> 1) & 1));
+        d += a.lat.J * szi * szj;
+      }
+    }
+    s_diag = d;
+  }
+  SampleView<T> sv;
+  sv.occ = occ_s;
+  sv.slot_of_orb = slot_s;
+  sv.z0 = (const T*)a.z0 + (size_t)b * N * h;
+  sv.HL = (const T*)a.HL + (size_t)b * N * h;
+  sv.Binv = (const T*)a.Binv + (size_t)b * Ne * Ne;
+  sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
+  MoveScratch<T>& ms = ms_all[warp];
+
+  const int nb = a.nb_nn + a.nb_nnn;
+  const int ncand = 2 * nb + ((a.lat.model == SCALE_MODEL_TJ && a.lat.J != 0.0) ? a.nb_nn : 0);
+  double total = 0.0;  // thread 0
+  int nmoves = 0;
+  for (int cs = 0; cs < ncand; cs += kChunk) {
+    const int id = cs + tid;
+    double cf = 0.0;
+    MoveDesc m{-1, 0, 0, 0};
+    if (id < ncand) m = candidate(a, occ_s, id, &cf);
+    const bool valid = m.kind >= 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) warp_cnt[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, nm = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      if (w < warp) off += warp_cnt[w];
+      nm += warp_cnt[w];
+    }
+    if (valid) {
+      const int pos = off + __popc(bal & ((1u << lane) - 1u));
+      moves[pos] = m;
+      coeffs[pos] = cf;
+    }
+    __syncthreads();
+    for (int mi = warp; mi < nm; mi += kWarps) {
+      if (lane == 0) {
+        ms.kind = moves[mi].kind;
+        ms.src = moves[mi].src;
+        ms.dst = moves[mi].dst;
+        ms.spin = moves[mi].spin;
+      }
+      __syncwarp();
+      move_features<T>(a.lat, net, a.k0, sv, ms);
+      const int r = move_matrix<T>(a.lat, net, sv, ms);
+      const T det = (r < 0) ? T(CUDART_NAN) : warp_det<T>(ms, r);
+      if (lane == 0) contrib[mi] = coeffs[mi] * (double)det;
+      __syncwarp();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 0; q < nm; ++q) total += contrib[q];
+      nmoves += nm;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    a.out[b] = s_diag + total;
+    if (a.move_count) a.move_count[b] = nmoves;
+  }
+}
+
+// psi(n')/psi(n) in the ascending convention for M explicit moves per sample.
+template <typename T>
+__global__ void __launch_bounds__(kWarps * 32) k_ratios(LowrankArgs a, Net<T> net) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.lat.N, Ne = a.lat.Ne, h = net.h;
+  MoveScratch<T>* ms_all = reinterpret_cast<MoveScratch<T>*>(smem);
+  int32_t* slot_s = reinterpret_cast<int32_t*>(ms_all + kWarps);
+  int8_t* occ_s = reinterpret_cast<int8_t*>(slot_s + 2 * N);
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int st = a.status[b];
+  const bool bad = st & (SCALE_SAMPLE_BAD_COUNT | SCALE_SAMPLE_DOUBLE_OCC | SCALE_SAMPLE_SINGULAR);
+  if (bad) {
+    for (int m = tid; m < a.M; m += blockDim.x) a.out[(size_t)b * a.M + m] = CUDART_NAN;
+    return;
+  }
+  for (int i = tid; i < N; i += blockDim.x) occ_s[i] = a.occ[(size_t)b * N + i];
+  for (int o = tid; o < 2 * N; o += blockDim.x) slot_s[o] = a.slot_of_orb[(size_t)b * 2 * N + o];
+  __syncthreads();
+  SampleView<T> sv;
+  sv.occ = occ_s;
+  sv.slot_of_orb = slot_s;
+  sv.z0 = (const T*)a.z0 + (size_t)b * N * h;
+  sv.HL = (const T*)a.HL + (size_t)b * N * h;
+  sv.Binv = (const T*)a.Binv + (size_t)b * Ne * Ne;
+  sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
+  MoveScratch<T>& ms = ms_all[warp];
+  for (int mi = warp; mi < a.M; mi += kWarps) {
+    const int32_t* mv = a.moves + ((size_t)b * a.M + mi) * 4;
+    const int kind = mv[0], src = mv[1], dst = mv[2], spin = mv[3];
+    double out;
+    if (kind < 0) {
+      out = 1.0;
+    } else if (!move_allowed(a.lat, kind, src, dst, spin, occ_s)) {
+      out = 0.0;
+    } else {
+      if (lane == 0) {
+        ms.kind = kind;
+        ms.src = src;
+        ms.dst = dst;
+        ms.spin = spin;
+      }
+      __syncwarp();
+      move_features<T>(a.lat, net, a.k0, sv, ms);
+      const int r = move_matrix<T>(a.lat, net, sv, ms);
+      const T det = (r < 0) ? T(CUDART_NAN) : warp_det<T>(ms, r);
+      int par;
+      if (kind == 0) {
+        par = between_parity(occ_s, N, spin * N + src, spin * N + dst);
+      } else {
+        // exchange: the up electron and the down electron each hop between src and dst
+        par = between_parity(occ_s, N, src, dst) ^ between_parity(occ_s, N, N + src, N + dst);
+      }
+      out = (par ? -1.0 : 1.0) * (double)det;
+    }
+    if (lane == 0) a.out[(size_t)b * a.M + mi] = out;
+    __syncwarp();
+  }
+}
+
+// Pt[s][c][:] = W_s Binv[c], i.e. the GEMM Pt[s] = Binv (Ne x Ne) * W_s^T (Ne x h),
+// W_s^T[k][cc] = proj_w[cc][s*Ne + k]. 32 rows per CTA, K tiles of 32.
+template <typename T>
+__global__ void __launch_bounds__(256) k_project(int Ne, int h, const T* __restrict__ proj_w,
+                                                 const T* __restrict__ Binv, T* __restrict__ Pt,
+                                                 const int32_t* __restrict__ list) {
+  __shared__ T Bs[32][33];
+  __shared__ T Ws[32][2 * kMaxH + 1];
+  const int b = list ? list[blockIdx.y] : blockIdx.y;
+  if (b < 0) return;
+  const int c0 = blockIdx.x * 32;
+  const int tid = threadIdx.x;
+  const int row = tid >> 3, grp = tid & 7;
+  const int ncol = 2 * h;
+  T acc[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = T(0);
+  const T* Bb = Binv + (size_t)b * Ne * Ne;
+  for (int k0 = 0; k0 < Ne; k0 += 32) {
+    for (int q = tid; q < 32 * 32; q += 256) {
+      const int rr = q >> 5, kk = q & 31;
+      const int c = c0 + rr, k = k0 + kk;
+      Bs[rr][kk] = (c < Ne && k < Ne) ? Bb[(size_t)c * Ne + k] : T(0);
+    }
+    for (int q = tid; q < 32 * ncol; q += 256) {
+      const int kk = q / ncol, col = q - kk * ncol;
+      const int s = col / h, cc = col - s * h, k = k0 + kk;
+      Ws[kk][col] = (k < Ne) ? proj_w[(size_t)cc * 2 * Ne + s * Ne + k] : T(0);
+    }
+    __syncthreads();
+    for (int kk = 0; kk < 32; ++kk) {
+      const T bv = Bs[row][kk];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int col = grp + 8 * u;
+        if (col < ncol) acc[u] += bv * Ws[kk][col];
+      }
+    }
+    __syncthreads();
+  }
+  const int c = c0 + row;
+  if (c >= Ne) return;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int col = grp + 8 * u;
+    if (col < ncol) {
+      const int s = col / h, cc = col - s * h;
+      Pt[(((size_t)b * 2 + s) * Ne + c) * h + cc] = acc[u];
+    }
+  }
+}
+
+template <typename T>
+size_t eloc_smem(int N) {
+  return sizeof(MoveScratch<T>) * kWarps + sizeof(MoveDesc) * kChunk + sizeof(double) * 2 * kChunk +
+         sizeof(int32_t) * 2 * N + N + 16;
+}
+
+template <typename T>
+size_t ratio_smem(int N) {
+  return sizeof(MoveScratch<T>) * kWarps + sizeof(int32_t) * 2 * N + N + 16;
+}
+
+LowrankArgs make_args(scale_ctx* c) {
+  LowrankArgs a{};
+  a.lat = c->lat;
+  a.k0 = c->k0;
+  a.occ = c->occ;
+  a.slot_of_orb = c->slot_of_orb;
+  a.z0 = c->z0;
+  a.HL = c->HL;
+  a.Binv = c->Binv;
+  a.Pt = c->Pt;
+  a.bonds = c->bonds;
+  a.nb_nn = c->nb_nn;
+  a.nb_nnn = c->nb_nnn;
+  a.status = c->status;
+  return a;
+}
+
+template <typename T>
+cudaError_t eloc_t(scale_ctx* c, double* eloc) {
+  LowrankArgs a = make_args(c);
+  a.out = eloc;
+  a.move_count = c->move_count;
+  const size_t smem = eloc_smem<T>(c->N);
+  cudaError_t e = cudaFuncSetAttribute(k_eloc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_eloc<T><<<c->B, kWarps * 32, smem, c->stream>>>(a, make_net<T>(c));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ratios_t(scale_ctx* c, const int32_t* moves, int M, double* ratio) {
+  LowrankArgs a = make_args(c);
+  a.out = ratio;
+  a.moves = moves;
+  a.M = M;
+  const size_t smem = ratio_smem<T>(c->N);
+  cudaError_t e = cudaFuncSetAttribute(k_ratios<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_ratios<T><<<c->B, kWarps * 32, smem, c->stream>>>(a, make_net<T>(c));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t project_t(scale_ctx* c, int B, const int32_t* list) {
+  dim3 grid((c->Ne + 31) / 32, B);
+  k_project<T><<<grid, 256, 0, c->stream>>>(c->Ne, c->h, make_net<T>(c).proj_w, (const T*)c->Binv, (T*)c->Pt, list);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_eloc_lowrank(scale_ctx* c, double* eloc) {
+  return c->fp64 ? eloc_t<double>(c, eloc) : eloc_t<float>(c, eloc);
+}
+
+cudaError_t launch_ratios(scale_ctx* c, const int32_t* moves, int M, double* ratio) {
+  return c->fp64 ? ratios_t<double>(c, moves, M, ratio) : ratios_t<float>(c, moves, M, ratio);
+}
+
+cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list) {
+  return c->fp64 ? project_t<double>(c, B, list) : project_t<float>(c, B, list);
+}
+
+}  // namespace scale

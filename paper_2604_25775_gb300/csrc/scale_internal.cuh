@@ -1,0 +1,181 @@
+// scale_internal.cuh -- shared declarations of the SCALE CUDA library (sm_103a).
+//
+// Data layout in HBM (per context, B = loaded samples, T = double in FP64 mode, float in
+// mixed mode):
+//   occ          int8  [B][N]            local states 0,1,2,3
+//   orb_of_slot  int32 [B][Ne]           orbital o = s*N + i held by each determinant row
+//   slot_of_orb  int32 [B][2N]           inverse map, -1 when the orbital is empty
+//   z0           T     [B][N][h]         pre-activation of layer 0 (kept for the additive
+//                                        receptive-field update of Eq. neighbor)
+//   HL           T     [B][N][h]         last-layer features H(L)
+//   Binv         T     [B][Ne][Ne]       Binv[c][k] = (Phi^-1)[k][c]: row c is the dual
+//                                        vector of determinant row c (M[o_a] . Binv[c] = delta)
+//   Pt           T     [B][2][Ne][h]     Pt[s][c] = W_s Binv[c], W_s = proj_w[:, s*Ne:(s+1)*Ne]
+//   logabs       f64   [B]               log|det Phi| in slot order, sign_slot int32 [B]
+// Parameters are kept as FP64 and T copies; the layer-0 conv-of-embedding table
+//   KE [Ns][4][k0*k0][h] = K_0[d]^T E_t[n]   (Ns = N with per-site tables, else 1)
+// turns the layer-0 receptive-field update into table additions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/scale.h"
+
+namespace scale {
+
+constexpr int kMaxLayers = SCALE_MAX_LAYERS;
+constexpr int kMaxH = 64;
+
+// Lattice geometry and Hamiltonian constants, passed by value to kernels.
+struct Lattice {
+  int Lx, Ly, pbc_x, pbc_y, N, n_up, n_dn, Ne, model;
+  double t, tp, U, J;
+};
+
+// Site reached from i by (dx, dy), or -1 past an open edge.
+__host__ __device__ __forceinline__ int site_off(const Lattice& lat, int i, int dx, int dy) {
+  int x = i % lat.Lx + dx, y = i / lat.Lx + dy;
+  if (x < 0 || x >= lat.Lx) {
+    if (!lat.pbc_x) return -1;
+    x = ((x % lat.Lx) + lat.Lx) % lat.Lx;
+  }
+  if (y < 0 || y >= lat.Ly) {
+    if (!lat.pbc_y) return -1;
+    y = ((y % lat.Ly) + lat.Ly) % lat.Ly;
+  }
+  return y * lat.Lx + x;
+}
+
+// Network parameters in precision T (device pointers).
+template <typename T>
+struct Net {
+  int h, L, act, per_site;
+  int ksize[kMaxLayers];
+  int resid[kMaxLayers];
+  const T* embed;                // [Ns][4][h]
+  const T* kernel[kMaxLayers];   // [k][k][h][h]
+  const T* bias[kMaxLayers];     // [h]
+  const T* proj_w;               // [h][2Ne]
+  const T* proj_b;               // [2Ne]
+  const T* M0;                   // [2N][Ne]
+  const T* KE;                   // [Ns][4][k0*k0][h]
+};
+
+template <typename T>
+__device__ __forceinline__ T act_fn(int act, T z) {
+  if (act == SCALE_ACT_TANH) return tanh(z);
+  return z / (T(1) + exp(-z));
+}
+
+template <typename T>
+__device__ __forceinline__ T act_grad(int act, T z) {
+  if (act == SCALE_ACT_TANH) {
+    T th = tanh(z);
+    return T(1) - th * th;
+  }
+  T s = T(1) / (T(1) + exp(-z));
+  return s * (T(1) + z * (T(1) - s));
+}
+
+}  // namespace scale
+
+// The context (opaque to callers).
+struct scale_ctx {
+  scale_system sys;
+  scale_arch arch;
+  scale::Lattice lat;
+  int N = 0, Ne = 0, h = 0, L = 0, k0 = 1, r0 = 0;
+  bool fp64 = true;
+  bool lowrank_ok = false;  // SCALE layer layout (k_l = 1 for l >= 1)
+  int64_t P = 0;
+  int B_max = 0, B = 0;
+  int max_moves = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0, allocated = 0;
+  std::string err;
+  bool params_set = false;
+
+  // parameters
+  double* params64 = nullptr;
+  float* params32 = nullptr;
+  double* M0_64 = nullptr;
+  float* M0_32 = nullptr;
+  void* KE = nullptr;
+
+  // lattice tables
+  int32_t* bonds = nullptr;  // [nb_nn + nb_nnn][2]
+  int nb_nn = 0, nb_nnn = 0;
+
+  // per-sample state
+  int8_t* occ = nullptr;
+  int32_t* orb_of_slot = nullptr;
+  int32_t* slot_of_orb = nullptr;
+  void* z0 = nullptr;
+  void* HL = nullptr;
+  void* Binv = nullptr;
+  void* Pt = nullptr;
+  double* logabs = nullptr;
+  int32_t* sign_slot = nullptr;
+  int32_t* status = nullptr;
+  int32_t* commits = nullptr;
+  double* drift = nullptr;
+
+  // scratch
+  double* Phi64 = nullptr;     // [B][Ne][Ne]
+  void* act_a = nullptr;       // [B][N][h]
+  void* act_b = nullptr;       // [B][N][h]
+  int32_t* list = nullptr;     // [B] sample list for partial refresh
+  int32_t* list_count = nullptr;
+  double* stat_dev = nullptr;  // [4]: drift maximum (bits), then int32 commits, refreshes, drift refreshes
+  void* commit_scratch = nullptr;  // [B][3*32*Ne + 2*32*kMaxH] T
+  double* la_tmp = nullptr;     // [B] log|psi| scratch (ascending)
+  int32_t* sg_tmp = nullptr;    // [B]
+  double* full_la = nullptr;    // [chunk]
+  int32_t* full_sg = nullptr;   // [chunk]
+  double* full_diag = nullptr;  // [B]
+  int64_t* full_offsets = nullptr;  // [B+1] device copy of the packed offsets
+  void* grad_scratch = nullptr;
+  size_t grad_scratch_bytes = 0;
+  int32_t* move_count = nullptr;  // [B] connected configurations last enumerated
+
+  // full-recompute path scratch
+  int full_chunk = 0;
+  int8_t* full_occ = nullptr;      // [chunk][N]
+  int32_t* full_owner = nullptr;   // [chunk]
+  double* full_coeff = nullptr;    // [chunk]
+  double* full_terms = nullptr;    // [B][max_moves]
+  int32_t* full_moves = nullptr;   // [B][max_moves][4]
+
+  scale_stats stats{};
+};
+
+namespace scale {
+
+// kernels (launch wrappers), each enqueued on ctx->stream
+cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t* sample_list,
+                           bool keep_cache, double* phi_out);
+cudaError_t launch_slots(scale_ctx* c, const int8_t* occ, int B);
+cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32_t* list,
+                      bool inverse, bool out_fp64, void* Binv, double* logabs, int32_t* sign,
+                      int32_t* status);
+cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list);
+cudaError_t launch_build_ke(scale_ctx* c);
+cudaError_t launch_logpsi_out(scale_ctx* c, double* logabs, int32_t* sign);
+cudaError_t launch_eloc_lowrank(scale_ctx* c, double* eloc);
+cudaError_t launch_ratios(scale_ctx* c, const int32_t* moves, int M, double* ratio);
+cudaError_t launch_commit(scale_ctx* c, const int32_t* moves);
+cudaError_t launch_eloc_full(scale_ctx* c, double* eloc);
+cudaError_t launch_grad(scale_ctx* c, double* grad, int recompute);
+cudaError_t refresh_samples(scale_ctx* c, bool force_all);
+cudaError_t launch_mark_refresh(scale_ctx* c, bool force_all);
+cudaError_t launch_slots_list(scale_ctx* c, const int32_t* list, int B);
+cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, void* phi);
+cudaError_t launch_det_f32(scale_ctx* c, float* mats, int n, int B, double* logabs, int32_t* sign);
+
+template <typename T>
+Net<T> make_net(scale_ctx* c);
+
+}  // namespace scale

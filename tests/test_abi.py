@@ -1,0 +1,48 @@
+"""C-ABI library: builds for sm_103a, loads, exports every entry point of include/scale.h,
+and its host-only calls agree with the parameter layout (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2604_25775_gb300 import binding as Bd
+from paper_2604_25775_gb300 import inputs as I
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "scale.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(scale_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = Bd.load_library()
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(Bd.EXPORTED)
+
+
+@pytest.mark.parametrize("name", ["hubbard4x4", "hubbard16x16", "cylinder16x4", "tj8x8", "hubbard32x32"])
+def test_param_count_matches_layout(name):
+    pb = I.workload(name)
+    assert Bd.scale_param_count(pb) == I.param_count(pb)
+    assert Bd.scale_footprint_bytes(pb, 16) > 0
+
+
+def test_invalid_descriptors_rejected_on_host():
+    bad = [
+        I.workload("hubbard4x4").replace(Lx=2),          # periodic extent 2
+        I.workload("hubbard4x4").replace(h=65),          # too many channels
+        I.workload("hubbard4x4").replace(ksize=[2, 1]),  # even kernel
+        I.workload("hubbard4x4").replace(n_up=17),       # more electrons than sites
+        I.workload("tj8x8").replace(n_up=40, n_dn=40),   # t-J overfilled
+        I.workload("hubbard4x4").replace(refresh_every=0),
+    ]
+    for pb in bad:
+        assert Bd.scale_param_count(pb) == -1
+        assert Bd.scale_footprint_bytes(pb, 4) == 0

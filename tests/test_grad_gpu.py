@@ -1,0 +1,69 @@
+"""GPU per-sample gradients d log|psi| / d theta against the FP64 oracle's backward pass and
+against central finite differences of the GPU's own log|psi| (16x4 cylinder, 12 residual
+3x3 layers, t' = -0.2)."""
+import numpy as np
+import pytest
+
+from paper_2604_25775_gb300 import inputs as I
+from tests.gpu_common import conditioning, setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_grad_matches_oracle_fp64(recompute):
+    pb = I.workload("cylinder16x4")
+    pseed, cseed = I.workload_seeds("cylinder16x4")
+    ctx, ora, occ, st = setup(pb, 32, pseed, cseed)
+    g = ctx.grad_logpsi(recompute=recompute).cpu().numpy()
+    g_o = ora.grad_logpsi(occ)
+    cond = conditioning(ora, occ)
+    good = cond < 1e6
+    scale = np.maximum(np.abs(g_o[good]).max(axis=1, keepdims=True), 1.0)
+    err = np.abs(g[good] - g_o[good]) / scale
+    print(f"grad recompute={recompute}: max rel err {err.max():.3e}")
+    assert err.max() <= 1e-10
+
+
+def test_grad_mixed_8x8():
+    """Mixed mode (FP32 network and inverse): gradients within 1e-4 of the FP64 oracle,
+    relative to the largest gradient entry of the sample, for cond(Phi) <= 1e3."""
+    pb = I.workload("hubbard8x8")
+    ctx, ora, occ, st = setup(pb, 32, 3, 4)
+    g = ctx.grad_logpsi().cpu().numpy()
+    g_o = ora.grad_logpsi(occ)
+    cond = conditioning(ora, occ)
+    good = cond < 1e3
+    assert good.sum() >= 4
+    scale = np.maximum(np.abs(g_o[good]).max(axis=1, keepdims=True), 1.0)
+    err = (np.abs(g[good] - g_o[good]) / scale).max()
+    print(f"grad mixed 8x8: max rel err {err:.3e}")
+    assert err <= 1e-4
+
+
+def test_grad_central_differences_gpu():
+    """Central differences (h = 1e-6, FP64) of the GPU log|psi| on 20 random parameters."""
+    import torch
+    from paper_2604_25775_gb300 import binding as Bd
+    pb = I.workload("cylinder16x4")
+    pseed, cseed = I.workload_seeds("cylinder16x4")
+    params = I.random_params(pb, pseed)
+    occ = I.random_configs(pb, 16, cseed)
+    ctx, ora, _, _ = setup(pb, 16, params=params, occ=occ)
+    g = ctx.grad_logpsi().cpu().numpy()
+    M0 = I.plane_wave_M0(pb)
+    occ_d = torch.from_numpy(occ).cuda()
+    rng = np.random.default_rng(7)
+    idx = rng.choice(params.size, 20, replace=False)
+    h = 1e-6
+    for q in idx:
+        vals = []
+        for sgn in (1, -1):
+            p2 = params.copy()
+            p2[q] += sgn * h
+            c2 = Bd.make_context(pb, p2, M0, 16)
+            c2.scale_load(occ_d)
+            vals.append(c2.log_psi()[0].cpu().numpy())
+            c2.close()
+        fd = (vals[0] - vals[1]) / (2 * h)
+        np.testing.assert_allclose(g[:, q], fd, rtol=2e-5, atol=2e-7)

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on the same
+seeded inputs.
+
+Tolerances (relative error |x_gpu - x_ora| / max(|x_ora|, 1)):
+  FP64 mode   E_loc, ratios, gradients <= 1e-10 and log|psi| absolute <= 1e-10 on samples
+              with cond(Phi) <= 1e6; signs exact.
+  mixed mode  E_loc, ratios, log|psi| <= 1e-4 on samples with cond(Phi) <= 1e3.
+Beyond those condition numbers every sample must still satisfy err <= cond * c * u with
+u = 2^-53 (FP64) or 2^-24 (mixed) and c = 1e3 (FP64) / 8 (mixed): an FP32-stored Phi^-1
+perturbs each ratio by about cond(Phi) * 2^-24, and any FP64 evaluation of an
+ill-conditioned determinant carries cond * 2^-53.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2604_25775_gb300 import binding as Bd
+from paper_2604_25775_gb300 import inputs as I
+from tests.gpu_common import conditioning, rel_err, setup
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-4
+
+
+def _check(name, gpu, ora, cond, tol, cond_ok, min_good=None):
+    err = rel_err(gpu, ora)
+    good = cond < cond_ok
+    mixed = tol > 1e-8
+    unit, c = (2.0 ** -24, 8.0) if mixed else (2.0 ** -53, 1e3)
+    print(f"{name}: n={len(err)} cond<{cond_ok:.0e}: {good.sum()} max_err={err[good].max() if good.any() else 0:.3e} "
+          f"median_all={np.median(err):.3e} max_err/cond={np.max(err / cond):.3e}")
+    for lo, hi in ((0, 1e2), (1e2, 1e3), (1e3, 1e4), (1e4, 1e5), (1e5, 1e6), (1e6, np.inf)):
+        sel = (cond >= lo) & (cond < hi)
+        if sel.any():
+            print(f"    cond in [{lo:.0e},{hi:.0e}): n={sel.sum():4d} max_err={err[sel].max():.3e} "
+                  f"median={np.median(err[sel]):.3e}")
+    assert good.sum() >= (min_good if min_good is not None else max(1, len(err) // 4))
+    if good.any():
+        assert err[good].max() <= tol
+    assert np.all(err <= np.maximum(tol, cond * c * unit)), np.max(err / (cond * c * unit))
+
+
+@pytest.fixture(scope="module")
+def fp64_4x4():
+    pb = I.workload("hubbard4x4")
+    ctx, ora, occ, st = setup(pb, 256, 1234, 5678)
+    cond = conditioning(ora, occ)
+    return pb, ctx, ora, occ, st, cond
+
+
+def test_load_status_fp64(fp64_4x4):
+    pb, ctx, ora, occ, st, cond = fp64_4x4
+    assert (st[np.isfinite(cond) & (cond < 1e12)] == 0).all()
+
+
+def test_log_psi_fp64(fp64_4x4):
+    pb, ctx, ora, occ, st, cond = fp64_4x4
+    la, sg = ctx.log_psi()
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    la_o, sg_o = ora.log_psi(occ)
+    good = cond < 1e6
+    assert (sg[good] == sg_o[good]).all()
+    assert np.abs(la[good] - la_o[good]).max() <= FP64_TOL
+
+
+def test_local_energy_lowrank_fp64(fp64_4x4):
+    pb, ctx, ora, occ, st, cond = fp64_4x4
+    e = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    _check("4x4 fp64 lowrank", e, e_o, cond, FP64_TOL, 1e6)
+
+
+def test_local_energy_full_fp64(fp64_4x4):
+    pb, ctx, ora, occ, st, cond = fp64_4x4
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    _check("4x4 fp64 full", e, e_o, cond, FP64_TOL, 1e6)
+
+
+def test_lowrank_equals_full_fp64(fp64_4x4):
+    pb, ctx, ora, occ, st, cond = fp64_4x4
+    e1 = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    e2 = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    good = cond < 1e6
+    assert rel_err(e1[good], e2[good]).max() <= FP64_TOL
+
+
+@pytest.mark.parametrize("variant", ["tp", "tj", "tj_tp", "open_silu", "shared_embed"])
+def test_local_energy_variants_fp64(variant):
+    """Hamiltonian and network variants at FP64: NNN hopping, t-J exchange and projection,
+    open boundaries with SiLU, a shared embedding table."""
+    ks, rs = I.scale_layout(3)
+    base = I.Problem(6, 5, 1, 1, 9, 8, I.MODEL_HUBBARD, 1.0, 0.0, 6.0, 0.0, 3, 8, ks, rs)
+    pb = {
+        "tp": base.replace(tp=-0.25),
+        "tj": base.replace(model=I.MODEL_TJ, U=0.0, J=0.4),
+        "tj_tp": base.replace(model=I.MODEL_TJ, U=0.0, J=1 / 3, tp=0.2, pbc_y=0),
+        "open_silu": base.replace(pbc_x=0, pbc_y=0, act=I.ACT_SILU, tp=0.1),
+        "shared_embed": base.replace(per_site_embed=0, tp=-0.1),
+    }[variant]
+    ctx, ora, occ, st, = setup(pb, 48, 31, 41, scale=0.2)
+    cond = conditioning(ora, occ)
+    e1 = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    e2 = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    _check(f"{variant} lowrank", e1, e_o, cond, FP64_TOL, 1e6)
+    _check(f"{variant} full", e2, e_o, cond, FP64_TOL, 1e6)
+
+
+def test_ratios_fp64():
+    pb = I.workload("hubbard8x8").replace(precision=I.PREC_FP64, tp=-0.2)
+    ctx, ora, occ, st = setup(pb, 32, 3, 4, scale=0.1)
+    import torch
+    M = 6
+    mv = np.stack([I.random_hop_moves(pb, occ, 100 + k) for k in range(M)], axis=1)
+    r = ctx.ratios(torch.from_numpy(mv).cuda()).cpu().numpy()
+    cond = conditioning(ora, occ)
+    good = cond < 1e6
+    for k in range(M):
+        r_o = ora.ratio(occ, mv[:, k])
+        err = rel_err(r[good, k], r_o[good])
+        assert err.max() <= FP64_TOL, err.max()
+    # a move into an occupied orbital is outside the space: ratio 0; kind -1: ratio 1
+    bad = mv[:, :2].copy()
+    bad[:, 1] = (I.MOVE_NONE, 0, 0, 0)
+    for b in range(32):
+        src = int(np.where(occ[b] & 1)[0][0])
+        dst = int(np.where(occ[b] & 1)[0][1])
+        bad[b, 0] = (I.MOVE_HOP, src, dst, 0)
+    rb = ctx.ratios(torch.from_numpy(np.ascontiguousarray(bad)).cuda()).cpu().numpy()
+    assert (rb[:, 0] == 0).all() and (rb[:, 1] == 1).all()
+
+
+@pytest.mark.parametrize("name", ["hubbard8x8", "tj8x8"])
+def test_local_energy_mixed_8x8(name):
+    pb = I.workload(name)
+    ctx, ora, occ, st = setup(pb, 256, 1235, 5679)
+    cond = conditioning(ora, occ)
+    e1 = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    _check(f"{name} mixed lowrank", e1, e_o, cond, MIXED_TOL, 1e3)
+    la, sg = ctx.log_psi()
+    la_o, sg_o = ora.log_psi(occ)
+    good = cond < 1e3
+    assert (sg.cpu().numpy()[good] == sg_o[good]).all()
+    assert rel_err(la.cpu().numpy()[good], la_o[good]).max() <= MIXED_TOL
+
+
+def test_local_energy_mixed_16x16_full_batch_sampled():
+    """The 16x16 workload at its full batch (8192) in the bench's launch configuration;
+    24 sampled outputs recomputed by the oracle."""
+    pb = I.workload("hubbard16x16")
+    pseed, cseed = I.workload_seeds("hubbard16x16")
+    ctx, ora, occ, st = setup(pb, 8192, pseed, cseed)
+    e = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    la, sg = ctx.log_psi()
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(8192, 32, replace=False))
+    cond = conditioning(ora, occ[pick])
+    e_o, _ = ora.local_energy(occ[pick])
+    _check("16x16 mixed lowrank (sampled)", e[pick], e_o, cond, MIXED_TOL, 1e3, min_good=1)
+    la_o, sg_o = ora.log_psi(occ[pick])
+    good = cond < 1e3
+    assert rel_err(la.cpu().numpy()[pick][good], la_o[good]).max() <= MIXED_TOL
+    assert np.isfinite(e).all()
+
+
+def test_zero_backflow_closed_form_on_gpu():
+    """All weights zero: E_loc = E0 + U * D exactly (both paths)."""
+    pb = I.workload("hubbard8x8").replace(precision=I.PREC_FP64)
+    params = np.zeros(I.param_count(pb))
+    ctx, ora, occ, st = setup(pb, 64, params=params, cseed=77)
+    cond = conditioning(ora, occ)
+    good = cond < 1e8
+    e = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    E0 = -101.25483399593904
+    ref = E0 + pb.U * (occ == 3).sum(1)
+    assert rel_err(e[good], ref[good]).max() < 1e-9
+
+
+def test_invalid_samples_flagged():
+    import torch
+    pb = I.workload("tj8x8").replace(precision=I.PREC_FP64)
+    occ = I.random_configs(pb, 4, 3)
+    occ[1, np.where(occ[1] == 1)[0][0]] = 3          # double occupancy
+    occ[1, np.where(occ[1] == 2)[0][0]] = 0
+    occ[2, np.where(occ[2] == 1)[0][0]] = 0          # missing electron
+    ctx, ora, _, st = setup(pb, 4, occ=occ)
+    assert st[0] == 0 and st[3] == 0
+    assert st[1] & Bd.SAMPLE_DOUBLE_OCC and st[2] & Bd.SAMPLE_BAD_COUNT
+    e = ctx.local_energy().cpu().numpy()
+    la, sg = ctx.log_psi()
+    assert np.isnan(e[1]) and np.isnan(e[2]) and np.isfinite(e[0])
+    assert sg.cpu().numpy()[1] == 0 and np.isneginf(la.cpu().numpy()[2])
+
+
+def test_deterministic():
+    pb = I.workload("hubbard8x8")
+    ctx, ora, occ, st = setup(pb, 128, 1, 2)
+    e1 = ctx.local_energy().cpu().numpy()
+    e2 = ctx.local_energy().cpu().numpy()
+    assert np.array_equal(e1, e2, equal_nan=True)
