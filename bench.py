@@ -144,7 +144,7 @@ def lowrank_flops_per_sample(pb, occ, n=32):
     r0 = (pb.ksize[0] - 1) // 2
     tot = 0.0
     for b in range(min(n, occ.shape[0])):
-        x = occ[b]
+        x = occ[b].astype(np.int64)
         for i in range(N):
             for (dx, dy) in ((1, 0), (0, 1)):
                 xx, yy = (i % pb.Lx + dx) % pb.Lx, (i // pb.Lx + dy) % pb.Ly
@@ -162,7 +162,7 @@ def lowrank_flops_per_sample(pb, occ, n=32):
                     y = x.copy()
                     y[src] &= ~(1 << s)
                     y[dst] |= 1 << s
-                    r = sum(((y[q] & 1) + ((y[q] >> 1) & 1)) for q in S)
+                    r = int(sum(((y[q] & 1) + ((y[q] >> 1) & 1)) for q in S))
                     tot += len(S) * (L - 1) * 2 * h * h + 2 * r * Ne + 2 * r * h + 2 * r * r * h + 2 * r ** 3 / 3
     return tot / min(n, occ.shape[0])
 

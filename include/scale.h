@@ -102,8 +102,11 @@ typedef struct {
   int32_t refresh_every;  /* FP64 re-factorisation of Phi every this many commits (>= 1);
                              counters start staggered at load (sample b at b mod
                              refresh_every) so refreshes spread evenly over calls */
-  double drift_tol;       /* drift check threshold: max |Phi' Phi'^-1 - I| on the changed
-                             rows after a commit; above it the sample is refreshed early */
+  double drift_tol;       /* drift check threshold on the changed rows after a commit,
+                             max_ab |M'_a . Binv'_b - delta_ab| / (|M'_a| |Binv'_b|)
+                             (FP64, normalised backward error of the maintained
+                             inverse); above it the sample is refreshed in FP64 within
+                             the same call */
   int32_t ksize[SCALE_MAX_LAYERS];    /* odd kernel size per layer, 1 = site-wise */
   int32_t residual[SCALE_MAX_LAYERS]; /* 1: add the layer input (Eq. conv residual) */
 } scale_arch;
