@@ -124,6 +124,28 @@ def dist_setup(args):
     return world, rank, local
 
 
+def replica_plan(rank: int, world: int, walkers: int) -> dict:
+    """Replicas only: every rank runs the whole step on its own walkers (weak scaling)."""
+    pseed, cseed = I.workload_seeds("hubbard16x16")
+    return {"walkers": walkers, "param_seed": pseed, "config_seed": cseed + 1000 * rank,
+            "move_seed": 777 + 1000 * rank, "world": world}
+
+
+def max_over_ranks(t_ms: float, dist=None, device="cuda") -> float:
+    """Slowest rank's time (the job's time)."""
+    if dist is None:
+        return t_ms
+    import torch
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(walkers: int, steps: int, world: int, t_max_ms: float) -> float:
+    """Whole-job local energies per second over all ranks."""
+    return world * walkers * steps / (t_max_ms / 1e3)
+
+
 def move_schedule(pb, occ, n_steps, seed):
     """Valid nearest-neighbour hop proposals for n_steps consecutive commits (host, seeded)."""
     cur = occ
@@ -217,14 +239,14 @@ def main():
     Bd.load_library(build=True)
 
     pb = I.workload(args.workload)
-    pseed, cseed = I.workload_seeds(args.workload)
     B, K, W = args.batch, args.steps, args.warmup
-    params = I.random_params(pb, pseed)
+    plan = replica_plan(rank, world, B)
+    params = I.random_params(pb, plan["param_seed"])
     M0 = I.plane_wave_M0(pb)
-    occ = I.random_configs(pb, B, cseed + 1000 * rank)
+    occ = I.random_configs(pb, B, plan["config_seed"])
     stream = torch.cuda.Stream()
     ctx = Bd.make_context(pb, params, M0, B, stream=stream)
-    moves = move_schedule(pb, occ, K + W, 777 + 1000 * rank)
+    moves = move_schedule(pb, occ, K + W, plan["move_seed"])
     moves_d = torch.from_numpy(moves).cuda()
     occ_d = torch.from_numpy(occ).cuda()
     eloc = torch.empty(B, dtype=torch.float64, device="cuda")
@@ -259,12 +281,8 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     eloc_ms = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
     commit_ms = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * B * K / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, dist)
+    value = aggregate_rate(B, K, world, t_max)
     assert torch.isfinite(eloc).float().mean().item() > 0.99
 
     # end-to-end through the public API: proposals from pinned host memory, E_loc back
@@ -284,12 +302,8 @@ def main():
             e_host[k].copy_(eloc, non_blocking=True)
     t1.record(stream)
     barrier()
-    e2e_ms = t0.elapsed_time(t1)
-    e2e_val = world * B * E2E_STEPS / (e2e_ms / 1e3)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * B * E2E_STEPS / (float(t.item()) / 1e3)
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1), dist)
+    e2e_val = aggregate_rate(B, E2E_STEPS, world, e2e_ms)
 
     line = {
         "metric": "local energies/s, low-rank (cached network + rank-r determinant) chain step, 16x16 Hubbard",

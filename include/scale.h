@@ -66,7 +66,7 @@ typedef enum {
 
 enum { SCALE_MODEL_HUBBARD = 0, SCALE_MODEL_TJ = 1 };
 enum { SCALE_ACT_TANH = 0, SCALE_ACT_SILU = 1 };
-enum { SCALE_PREC_FP64 = 0, SCALE_PREC_MIXED = 1 };
+enum { SCALE_PREC_FP64 = 0, SCALE_PREC_MIXED = 1, SCALE_PREC_MIXED_BF16 = 2 };
 enum { SCALE_PATH_LOWRANK = 0, SCALE_PATH_FULL = 1 };
 
 /* per-sample status bits */
@@ -96,9 +96,14 @@ typedef struct {
   int32_t act;            /* SCALE_ACT_* */
   int32_t per_site_embed; /* 1: tables E_i per site (Sec. II.B); 0: one shared table */
   int32_t precision;      /* SCALE_PREC_FP64: everything FP64.
-                             SCALE_PREC_MIXED: network on BF16 tensor cores with FP32
-                             accumulation, rank-r algebra and cached Phi^-1 in FP32,
-                             LU / log|det| / drift check in FP64 */
+                             SCALE_PREC_MIXED: site-wise layers on the tensor cores as
+                             three TF32 products of a hi/lo split (FP32 accumulation),
+                             other layers, rank-r algebra and cached Phi^-1 in FP32,
+                             LU / log|det| / drift check / E_loc sums in FP64.
+                             SCALE_PREC_MIXED_BF16: as MIXED with three BF16 products
+                             (about 2^-16 per layer instead of 2^-21).
+                             The tensor-core path needs the SCALE layout and h in
+                             {16, 32, 64}; otherwise the layers run in FP32 FMA. */
   int32_t refresh_every;  /* FP64 re-factorisation of Phi every this many commits (>= 1);
                              counters start staggered at load (sample b at b mod
                              refresh_every) so refreshes spread evenly over calls */
@@ -198,6 +203,80 @@ const char *scale_last_error(scale_ctx *ctx);
 
 /* Free the context and its device memory (synchronises its stream). NULL is a no-op. */
 void scale_destroy(scale_ctx *ctx);
+
+/* ------------------------------------------------------------------------------------
+ * Serving: continuous batching of local-energy and amplitude requests from many Markov
+ * chains, on lattices of different sizes and dopings, with device-resident chain state.
+ * Not a construct of the paper (it has no serving layer); it drives the same kernels.
+ *
+ * A server owns one context per class (system + network + parameters) with a pool of
+ * walker slots. SCALE_SRV_OPEN loads a chain's walkers into free slots; the walkers'
+ * configuration, Phi^-1, projector and cached features stay in HBM until SCALE_SRV_CLOSE.
+ * Requests (ELOC: local energies; STEP: local energies, then one Woodbury commit per
+ * walker with the given moves; LOGPSI: log|psi|) that arrive while a class's batch is on
+ * the GPU are merged into that class's next batch (one request per chain per batch);
+ * classes run on their own CUDA streams and overlap on the device. A chain is admitted
+ * when its class has enough free slots and the resident footprint of all open chains plus
+ * its own stays within hbm_budget_bytes; until then it waits in arrival order. Results are
+ * bit-identical to serving the chain alone: every walker is computed by its own CTA.
+ * Scheduling runs on one host thread; no kernel waits on the host.
+ * ------------------------------------------------------------------------------------ */
+enum { SCALE_SRV_OPEN = 0, SCALE_SRV_ELOC = 1, SCALE_SRV_STEP = 2, SCALE_SRV_LOGPSI = 3, SCALE_SRV_CLOSE = 4 };
+
+typedef struct scale_server scale_server;
+
+typedef struct {
+  int32_t n_classes;
+  const scale_system *sys;     /* [n_classes] host array */
+  const scale_arch *arch;      /* [n_classes] host array; SCALE layer layout required */
+  const double *const *params; /* [n_classes] device pointers (copied at creation) */
+  const double *const *M0;     /* [n_classes] device pointers (copied at creation) */
+  const int32_t *slots;        /* [n_classes] walker slots per class (<= 65535) */
+  size_t hbm_budget_bytes;     /* limit on the footprint of open chains, 0 = none */
+} scale_server_cfg;
+
+typedef struct {
+  int32_t op;               /* SCALE_SRV_* */
+  int32_t cls;              /* OPEN: class index */
+  int32_t n_walkers;        /* OPEN: walkers of the chain */
+  uint64_t chain;           /* ELOC / STEP / LOGPSI / CLOSE: the OPEN request's ticket */
+  const int8_t *occ_host;   /* OPEN: [n_walkers][N], copied at submission */
+  const int32_t *moves_host;/* STEP: [n_walkers][4], copied at submission */
+  double *out_host;         /* ELOC / STEP: E_loc [n_walkers]; LOGPSI: log|psi| (-inf for a
+                               zero amplitude); written before the ticket completes, must
+                               stay valid until then */
+} scale_request;
+
+typedef struct {
+  int32_t status;      /* SCALE_OK or the failure of this request */
+  double latency_us;   /* submission to completion */
+  uint64_t chain;      /* chain id (OPEN) */
+} scale_result;
+
+typedef struct {
+  size_t resident_bytes, resident_max_bytes, budget_bytes;
+  int64_t n_batches, n_requests, open_chains;
+} scale_server_stats_t;
+
+/* Create the server: one context and CUDA stream per class, all allocated up front, and
+ * the scheduling thread. Errors as scale_create (SCALE_EUNSUPPORTED for a non-SCALE layer
+ * layout). */
+scale_status scale_server_create(const scale_server_cfg *cfg, scale_server **out);
+
+/* Non-blocking submission; *ticket identifies the request (and, for OPEN, the chain).
+ * SCALE_EBUDGET when an OPEN could never fit (more walkers than slots or than the budget),
+ * SCALE_EINVAL for an unknown chain or malformed request. */
+scale_status scale_server_submit(scale_server *srv, const scale_request *req, uint64_t *ticket);
+
+/* Wait at most timeout_us for a ticket; SCALE_ETIMEOUT if it is still pending (the ticket
+ * stays valid). On completion fills *out and releases the ticket. */
+scale_status scale_server_poll(scale_server *srv, uint64_t ticket, scale_result *out, int32_t timeout_us);
+
+/* Resident footprint, its maximum so far, batches and requests processed. */
+scale_status scale_server_stats(scale_server *srv, scale_server_stats_t *out);
+
+/* Stop the scheduler, wait for the streams, free everything. NULL is a no-op. */
+void scale_server_destroy(scale_server *srv);
 
 #ifdef __cplusplus
 }

@@ -263,3 +263,137 @@ def make_context(pb: I.Problem, params: np.ndarray, M0: np.ndarray, max_batch: i
     ctx.scale_set_params(torch.from_numpy(np.ascontiguousarray(params, dtype=np.float64)).cuda(),
                          torch.from_numpy(np.ascontiguousarray(M0, dtype=np.float64)).cuda())
     return ctx
+
+
+# ---------------------------------------------------------------------------------------
+# Serving (scale_server_*): continuous batching over device-resident chains.
+# ---------------------------------------------------------------------------------------
+SRV_OPEN, SRV_ELOC, SRV_STEP, SRV_LOGPSI, SRV_CLOSE = range(5)
+EXPORTED += ["scale_server_create", "scale_server_submit", "scale_server_poll", "scale_server_stats",
+             "scale_server_destroy"]
+
+
+class scale_server_cfg(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int32), ("sys", ctypes.POINTER(scale_system)),
+                ("arch", ctypes.POINTER(scale_arch)), ("params", ctypes.POINTER(ctypes.c_void_p)),
+                ("M0", ctypes.POINTER(ctypes.c_void_p)), ("slots", ctypes.POINTER(ctypes.c_int32)),
+                ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+class scale_request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("cls", ctypes.c_int32), ("n_walkers", ctypes.c_int32),
+                ("chain", ctypes.c_uint64), ("occ_host", ctypes.c_void_p), ("moves_host", ctypes.c_void_p),
+                ("out_host", ctypes.c_void_p)]
+
+
+class scale_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("latency_us", ctypes.c_double), ("chain", ctypes.c_uint64)]
+
+
+class scale_server_stats_t(ctypes.Structure):
+    _fields_ = [("resident_bytes", ctypes.c_size_t), ("resident_max_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t), ("n_batches", ctypes.c_int64),
+                ("n_requests", ctypes.c_int64), ("open_chains", ctypes.c_int64)]
+
+
+def _server_lib():
+    lib = load_library()
+    if not getattr(lib, "_srv_ready", False):
+        P, V = ctypes.POINTER, ctypes.c_void_p
+        lib.scale_server_create.restype = ctypes.c_int
+        lib.scale_server_create.argtypes = [P(scale_server_cfg), P(V)]
+        lib.scale_server_submit.restype = ctypes.c_int
+        lib.scale_server_submit.argtypes = [V, P(scale_request), P(ctypes.c_uint64)]
+        lib.scale_server_poll.restype = ctypes.c_int
+        lib.scale_server_poll.argtypes = [V, ctypes.c_uint64, P(scale_result), ctypes.c_int32]
+        lib.scale_server_stats.restype = ctypes.c_int
+        lib.scale_server_stats.argtypes = [V, P(scale_server_stats_t)]
+        lib.scale_server_destroy.restype = None
+        lib.scale_server_destroy.argtypes = [V]
+        lib._srv_ready = True
+    return lib
+
+
+class Server:
+    """scale_server_* wrapper. classes: list of (Problem, params, M0, slots)."""
+
+    def __init__(self, classes, hbm_budget_bytes: int = 0):
+        import torch
+        self.lib = _server_lib()
+        n = len(classes)
+        self.problems = [c[0] for c in classes]
+        descs = [make_descriptors(c[0]) for c in classes]
+        self._sys = (scale_system * n)(*[d[0] for d in descs])
+        self._arch = (scale_arch * n)(*[d[1] for d in descs])
+        self._dev = [(torch.from_numpy(np.ascontiguousarray(c[1], dtype=np.float64)).cuda(),
+                      torch.from_numpy(np.ascontiguousarray(c[2], dtype=np.float64)).cuda()) for c in classes]
+        self._params = (ctypes.c_void_p * n)(*[p.data_ptr() for p, _ in self._dev])
+        self._M0 = (ctypes.c_void_p * n)(*[m.data_ptr() for _, m in self._dev])
+        self._slots = (ctypes.c_int32 * n)(*[int(c[3]) for c in classes])
+        cfg = scale_server_cfg(n, self._sys, self._arch, self._params, self._M0, self._slots, hbm_budget_bytes)
+        torch.cuda.synchronize()
+        h = ctypes.c_void_p()
+        st = self.lib.scale_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise ScaleError(st, "scale_server_create failed")
+        self.h = h
+        self._keep = {}
+        self._n = {}
+
+    def _submit(self, req, keep=()):
+        t = ctypes.c_uint64()
+        st = self.lib.scale_server_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st != OK:
+            raise ScaleError(st, "scale_server_submit failed")
+        self._keep[t.value] = keep
+        return t.value
+
+    def open(self, cls: int, occ: np.ndarray) -> int:
+        occ = np.ascontiguousarray(occ, dtype=np.int8)
+        req = scale_request(SRV_OPEN, cls, occ.shape[0], 0, occ.ctypes.data, None, None)
+        t = self._submit(req, (occ,))
+        self._n[t] = occ.shape[0]
+        return t
+
+    def eloc(self, chain: int, out: np.ndarray) -> int:
+        req = scale_request(SRV_ELOC, 0, 0, chain, None, None, out.ctypes.data)
+        return self._submit(req, (out,))
+
+    def step(self, chain: int, moves: np.ndarray, out: np.ndarray) -> int:
+        moves = np.ascontiguousarray(moves, dtype=np.int32)
+        req = scale_request(SRV_STEP, 0, 0, chain, None, moves.ctypes.data, out.ctypes.data)
+        return self._submit(req, (moves, out))
+
+    def logpsi(self, chain: int, out: np.ndarray) -> int:
+        req = scale_request(SRV_LOGPSI, 0, 0, chain, None, None, out.ctypes.data)
+        return self._submit(req, (out,))
+
+    def close(self, chain: int) -> int:
+        return self._submit(scale_request(SRV_CLOSE, 0, 0, chain, None, None, None))
+
+    def poll(self, ticket: int, timeout_us: int = 10_000_000):
+        """(status, latency_us) when done, None on timeout."""
+        r = scale_result()
+        st = self.lib.scale_server_poll(self.h, ticket, ctypes.byref(r), timeout_us)
+        if st == ETIMEOUT:
+            return None
+        if st != OK:
+            raise ScaleError(st, "scale_server_poll failed")
+        self._keep.pop(ticket, None)
+        return r.status, r.latency_us
+
+    def stats(self) -> dict:
+        s = scale_server_stats_t()
+        self.lib.scale_server_stats(self.h, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in scale_server_stats_t._fields_}
+
+    def destroy(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.scale_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

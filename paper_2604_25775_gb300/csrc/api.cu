@@ -38,7 +38,8 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
   if (a->n_layers < 1 || a->n_layers > SCALE_MAX_LAYERS) return fail("n_layers must be in [1, 32]");
   if (a->h < 1 || a->h > kMaxH) return fail("h must be in [1, 64]");
   if (a->act != SCALE_ACT_TANH && a->act != SCALE_ACT_SILU) return fail("unknown activation");
-  if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED) return fail("unknown precision");
+  if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED && a->precision != SCALE_PREC_MIXED_BF16)
+    return fail("unknown precision");
   if (a->refresh_every < 1) return fail("refresh_every must be >= 1");
   for (int l = 0; l < a->n_layers; ++l) {
     const int k = a->ksize[l];
@@ -94,7 +95,7 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   const size_t k0 = a->ksize[0];
   size_t t = 0;
   t += P * 8 + (T == 4 ? P * 4 : 0);
-  t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0);
+  t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0) + 2 * N * Ne * T;
   t += (a->per_site_embed ? N : 1) * 4 * k0 * k0 * h * T;
   t += (nb_nn + nb_nnn) * 2 * 4;
   t += (size_t)B * (N + Ne * 4 + 2 * N * 4);
@@ -117,6 +118,16 @@ __global__ void k_convert(const TS* __restrict__ in, TD* __restrict__ out, size_
     out[q] = (TD)in[q];
 }
 
+// M0b[o][k] = M0[o][k] + proj_b[s(o) * Ne + k]
+template <typename T>
+__global__ void k_m0b(const T* __restrict__ M0, const T* __restrict__ pb, int N, int Ne, T* __restrict__ out) {
+  const size_t total = (size_t)2 * N * Ne;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t o = q / Ne, k = q - o * Ne;
+    out[q] = M0[q] + pb[(o / N) * Ne + k];
+  }
+}
+
 template <typename P>
 cudaError_t alloc(scale_ctx* c, P** ptr, size_t bytes) {
   *ptr = nullptr;
@@ -127,12 +138,12 @@ cudaError_t alloc(scale_ctx* c, P** ptr, size_t bytes) {
 }
 
 void free_all(scale_ctx* c) {
-  void* ptrs[] = {c->params64, c->params32, c->M0_64, c->M0_32, c->KE, c->bonds, c->occ, c->orb_of_slot,
+  void* ptrs[] = {c->params64, c->params32, c->M0_64, c->M0_32, c->M0b, c->KE, c->bonds, c->occ, c->orb_of_slot,
                   c->slot_of_orb, c->z0, c->HL, c->Binv, c->Pt, c->logabs, c->sign_slot, c->status,
                   c->commits, c->drift, c->Phi64, c->act_a, c->act_b, c->list, c->list_count, c->stat_dev,
                   c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_terms, c->full_moves,
                   c->commit_scratch, c->la_tmp, c->sg_tmp, c->full_la, c->full_sg, c->full_diag,
-                  c->full_offsets, c->grad_scratch};
+                  c->full_offsets, c->grad_scratch, c->wfrag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -218,6 +229,8 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
                    sys->t, sys->tp, sys->U, sys->J};
   c->lowrank_ok = c->k0 <= 3;
   for (int l = 1; l < c->L; ++l) c->lowrank_ok = c->lowrank_ok && arch->ksize[l] == 1;
+  c->hpad = c->h <= 16 ? 16 : (c->h <= 32 ? 32 : 64);
+  c->use_mma = !c->fp64 && c->lowrank_ok && c->h == c->hpad;
   std::vector<int32_t> bonds = make_bonds(c->lat, &c->nb_nn, &c->nb_nnn);
   c->max_moves = 2 * (c->nb_nn + c->nb_nnn) + (sys->model == SCALE_MODEL_TJ ? c->nb_nn : 0);
   c->full_chunk = max_batch;
@@ -232,6 +245,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   if (!c->fp64) A(&c->params32, c->P * 4);
   A(&c->M0_64, 2 * N * Ne * 8);
   if (!c->fp64) A(&c->M0_32, 2 * N * Ne * 4);
+  A((char**)&c->M0b, 2 * N * Ne * T);
   A((char**)&c->KE, Ns * 4 * c->k0 * c->k0 * h * T);
   A(&c->bonds, std::max<size_t>(bonds.size(), 2) * 4);
   A(&c->occ, B * N);
@@ -265,6 +279,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A(&c->full_coeff, B * cap * 8);
   A(&c->full_terms, B * cap * 8);
   A(&c->full_moves, B * cap * 16);
+  if (c->use_mma) A((char**)&c->wfrag, (size_t)c->L * (c->hpad / 8) * (c->hpad / 8) * 32 * 16);
   if (e != cudaSuccess) {
     free_all(c);
     delete c;
@@ -297,6 +312,15 @@ scale_status scale_set_params(scale_ctx* c, const double* params, const double* 
     SCALE_TRY(c, cudaGetLastError());
   }
   SCALE_TRY(c, launch_build_ke(c));
+  SCALE_TRY(c, launch_build_wfrag(c));
+  if (c->fp64) {
+    const Net<double> n = make_net<double>(c);
+    k_m0b<double><<<512, 256, 0, c->stream>>>(n.M0, n.proj_b, c->N, c->Ne, (double*)c->M0b);
+  } else {
+    const Net<float> n = make_net<float>(c);
+    k_m0b<float><<<512, 256, 0, c->stream>>>(n.M0, n.proj_b, c->N, c->Ne, (float*)c->M0b);
+  }
+  SCALE_TRY(c, cudaGetLastError());
   c->params_set = true;
   c->B = 0;
   return SCALE_OK;

@@ -36,6 +36,7 @@ struct CommitArgs {
   void* scratch;          // [B][3*kRMax*Ne + 2*kRMax*kMaxH] T : X, D, saved Binv rows, saved Pt rows
   unsigned long long* drift_max_bits;
   int32_t* n_commits;
+  MlpFrags mf;
 };
 
 // In-place inverse of the r x r matrix R (warp; lane j owns column j), Gauss-Jordan with
@@ -96,12 +97,12 @@ __device__ T warp_inverse(T (*R)[kRMax + 1], T (*Ri)[kRMax + 1], int r) {
   return det;
 }
 
-template <typename T>
+template <typename T, int H>
 __global__ void __launch_bounds__(256) k_commit(CommitArgs a, Net<T> net) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.lat.N, Ne = a.lat.Ne, h = net.h;
-  MoveScratch<T>& ms = *reinterpret_cast<MoveScratch<T>*>(smem);
-  T(*z0n)[kMaxH] = reinterpret_cast<T(*)[kMaxH]>(&ms + 1);   // [kSMax][kMaxH]
+  MoveScratch<T, H>& ms = *reinterpret_cast<MoveScratch<T, H>*>(smem);
+  T(*z0n)[H] = reinterpret_cast<T(*)[H]>(&ms + 1);   // [kSMax][H]
   T(*Ri)[kRMax + 1] = reinterpret_cast<T(*)[kRMax + 1]>(z0n + kSMax);
   int32_t* slot_s = reinterpret_cast<int32_t*>(Ri + kRMax);
   int8_t* occ_s = reinterpret_cast<int8_t*>(slot_s + 2 * N);
@@ -144,8 +145,8 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs a, Net<T> net) {
       ms.spin = spin;
     }
     __syncwarp();
-    move_features<T>(a.lat, net, a.k0, sv, ms, z0n);
-    const int r = move_matrix<T>(a.lat, net, sv, ms);
+    move_features<T, H>(a.lat, net, a.k0, sv, a.mf, ms, z0n);
+    const int r = move_matrix<T, H>(a.lat, net, sv, ms);
     T det = T(0);
     if (r > 0) det = warp_inverse<T>(ms.R, Ri, r);
     if (lane == 0) {
@@ -163,20 +164,20 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs a, Net<T> net) {
     const int ai = q / Ne, j = q - ai * Ne;
     const int o = ms.orb[ai], sp = o / N, i = o - sp * N;
     const T* pt = Pb + ((size_t)sp * Ne + j) * h;
-    const T* dh = ms.feat[ms.sidx[ai]];
     T v = T(0);
-    for (int c = 0; c < h; ++c) v += dh[c] * pt[c];
     if (ms.moved[ai]) {
+      // G(o', j) with the new features: (M0[o'] + proj_b) . Binv[j] + H'_i . Pt[j]
+      const T* fnew = ms.feat[ms.sidx[ai]];
       const T* brow = Bb + (size_t)j * Ne;
-      const T* m0 = net.M0 + (size_t)o * Ne;
-      const T* pbias = net.proj_b + sp * Ne;
-      T g = T(0);
-      for (int k = 0; k < Ne; ++k) g += (m0[k] + pbias[k]) * brow[k];
-      const T* hl = hb + (size_t)i * h;
-      for (int c = 0; c < h; ++c) g += hl[c] * pt[c];
-      v += g;
+      const T* m0b = net.M0b + (size_t)o * Ne;
+      for (int k = 0; k < Ne; ++k) v += m0b[k] * brow[k];
+      for (int c = 0; c < h; ++c) v += fnew[c] * pt[c];
       if (j == ms.slot[ai]) v -= T(1);
+    } else {
+      const T* dh = ms.hl[ms.sidx[ai]];  // Delta H (move_matrix left it there)
+      for (int c = 0; c < h; ++c) v += dh[c] * pt[c];
     }
+    (void)i;
     X[(size_t)ai * Ne + j] = v;
   }
   __syncthreads();
@@ -208,12 +209,12 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs a, Net<T> net) {
     for (int bi = 0; bi < r; ++bi) acc -= D[(size_t)bi * Ne + j] * Pc[((size_t)sp * r + bi) * h + c];
     Pb[q] = acc;
   }
-  // features on S: z0 <- z0', H(L) <- H(L) + Delta H
+  // features on S: z0 <- z0', H(L) <- H'(L)
   for (int q = tid; q < ms.nS * h; q += blockDim.x) {
     const int s = q / h, c = q - s * h;
     const int site = ms.site[s];
     zb[(size_t)site * h + c] = z0n[s][c];
-    hb[(size_t)site * h + c] += ms.feat[s][c];
+    hb[(size_t)site * h + c] = ms.feat[s][c];
   }
   __syncthreads();
   if (tid == 0) {
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs a, Net<T> net) {
     const int ai = q / Ne, k = q - ai * Ne;
     const int o = ms.orb[ai], sp = o / N, i = o - sp * N;
     const T* hrow = hb + (size_t)i * h;
-    T m = net.M0[(size_t)o * Ne + k] + net.proj_b[sp * Ne + k];
+    T m = net.M0b[(size_t)o * Ne + k];
     for (int c = 0; c < h; ++c) m += hrow[c] * net.proj_w[(size_t)c * 2 * Ne + sp * Ne + k];
     Mr[q] = m;
   }
@@ -303,7 +304,7 @@ __global__ void k_mark_refresh(int B, int refresh_every, bool force_all, const i
   }
 }
 
-template <typename T>
+template <typename T, int H>
 cudaError_t commit_t(scale_ctx* c, const int32_t* moves) {
   CommitArgs a{};
   a.lat = c->lat;
@@ -325,18 +326,22 @@ cudaError_t commit_t(scale_ctx* c, const int32_t* moves) {
   a.scratch = c->commit_scratch;
   a.drift_max_bits = reinterpret_cast<unsigned long long*>(c->stat_dev);
   a.n_commits = reinterpret_cast<int32_t*>(c->stat_dev + 1);
-  const size_t smem = sizeof(MoveScratch<T>) + sizeof(T) * kSMax * kMaxH + sizeof(T) * kRMax * (kRMax + 1) +
+  a.mf.wf = c->use_mma ? (const WFrag*)c->wfrag : nullptr;
+  a.mf.kind = c->arch.precision == SCALE_PREC_MIXED_BF16 ? kBF16 : kTF32;
+  const size_t smem = sizeof(MoveScratch<T, H>) + sizeof(T) * kSMax * H + sizeof(T) * kRMax * (kRMax + 1) +
                       sizeof(int32_t) * 2 * c->N + c->N + 16;
-  cudaError_t e = cudaFuncSetAttribute(k_commit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_commit<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_commit<T><<<c->B, 256, smem, c->stream>>>(a, make_net<T>(c));
+  k_commit<T, H><<<c->B, 256, smem, c->stream>>>(a, make_net<T>(c));
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_commit(scale_ctx* c, const int32_t* moves) {
-  return c->fp64 ? commit_t<double>(c, moves) : commit_t<float>(c, moves);
+  if (c->hpad == 16) return c->fp64 ? commit_t<double, 16>(c, moves) : commit_t<float, 16>(c, moves);
+  if (c->hpad == 32) return c->fp64 ? commit_t<double, 32>(c, moves) : commit_t<float, 32>(c, moves);
+  return c->fp64 ? commit_t<double, 64>(c, moves) : commit_t<float, 64>(c, moves);
 }
 
 cudaError_t launch_mark_refresh(scale_ctx* c, bool force_all) {

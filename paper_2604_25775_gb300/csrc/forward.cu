@@ -2,6 +2,7 @@
 // layer-0 conv-of-embedding table and the log|psi| output convention.
 #include <algorithm>
 
+#include "mlp_mma.cuh"
 #include "scale_internal.cuh"
 
 namespace scale {
@@ -180,8 +181,9 @@ __global__ void k_build_ke(Net<T> net, int Ns, T* __restrict__ KE) {
 // permutation orb_of_slot (inversions counted directly).
 __global__ void k_logpsi_out(int Ne, const int32_t* __restrict__ orb_of_slot, const double* __restrict__ la_slot,
                              const int32_t* __restrict__ sg_slot, const int32_t* __restrict__ status,
-                             double* __restrict__ logabs, int32_t* __restrict__ sign) {
-  const int b = blockIdx.x;
+                             double* __restrict__ logabs, int32_t* __restrict__ sign,
+                             const int32_t* __restrict__ list) {
+  const int b = list ? list[blockIdx.x] : blockIdx.x;
   const int32_t* os = orb_of_slot + (size_t)b * Ne;
   int inv = 0;
   for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) {
@@ -201,7 +203,111 @@ __global__ void k_logpsi_out(int Ne, const int32_t* __restrict__ orb_of_slot, co
   }
 }
 
+// Site-wise layers 1..L-1 of every (sample, site) row on the tensor cores (mixed mode):
+// one warp per 16 consecutive rows, activations kept in registers through the layers.
+// Rows of samples not in the list are skipped.
+template <int H, int KIND>
+__global__ void __launch_bounds__(256) k_mlp_fwd(Net<float> net, const WFrag* __restrict__ wf, int N, int B,
+                                                 const int32_t* __restrict__ list, const float* __restrict__ in,
+                                                 float* __restrict__ out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long row0 = (long long)warp * 16;
+  const long long rows = (long long)B * N;  // B = entries of the launch (list length)
+  if (row0 >= rows) return;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float x[H / 8][4];
+  bool keep[2];
+  long long drow[2];  // data row: sample (list entry or launch index) * N + site
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const long long row = row0 + g + 8 * hh;
+    bool k = row < rows;
+    long long d = 0;
+    if (k) {
+      const long long q = row / N;
+      const long long b = list ? (long long)list[q] : q;
+      k = b >= 0;
+      d = b * N + (row - q * N);
+    }
+    keep[hh] = k;
+    drow[hh] = d;
+  }
+#pragma unroll
+  for (int j = 0; j < H / 8; ++j) {
+    const int c = 8 * j + 2 * t;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      x[j][2 * hh] = keep[hh] ? in[drow[hh] * H + c] : 0.f;
+      x[j][2 * hh + 1] = keep[hh] ? in[drow[hh] * H + c + 1] : 0.f;
+    }
+  }
+  mlp_tile<H, KIND>(x, wf, net.bias, net.resid, net.L, net.act);
+#pragma unroll
+  for (int j = 0; j < H / 8; ++j) {
+    const int c = 8 * j + 2 * t;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      if (keep[hh]) {
+        out[drow[hh] * H + c] = x[j][2 * hh];
+        out[drow[hh] * H + c + 1] = x[j][2 * hh + 1];
+      }
+    }
+  }
+}
+
+// hi/lo fragments of the site-wise weights W_l[c_in][c_out] (layers l >= 1):
+//   BF16: b0 = (W[16kk + 2t][8j + g], W[16kk + 2t + 1][8j + g]), b1 = the same at rows + 8;
+//   TF32: b0 = W[8kk + 2t][8j + g], b1 = W[8kk + 2t + 1][8j + g] (permuted k, see mlp_mma.cuh).
+template <int H, int KIND>
+__global__ void k_build_wfrag(Net<float> net, WFrag* __restrict__ wf) {
+  constexpr int NT = MmaShape<H, KIND>::NT, KT = MmaShape<H, KIND>::KT;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int total = net.L * KT * NT * 32;
+  if (q >= total) return;
+  const int lane = q & 31, j = (q >> 5) % NT, kk = (q >> 5) / NT % KT, l = (q >> 5) / (NT * KT);
+  WFrag f{};
+  if (l >= 1 && net.ksize[l] == 1) {
+    const int g = lane >> 2, t = lane & 3;
+    const float* W = net.kernel[l];
+    const int n = 8 * j + g;
+    if constexpr (KIND == kTF32) {
+      const int k0 = 8 * kk + 2 * t;
+      split_tf32(W[(size_t)k0 * H + n], f.v[0], f.v[2]);
+      split_tf32(W[(size_t)(k0 + 1) * H + n], f.v[1], f.v[3]);
+    } else {
+      const int k0 = 16 * kk + 2 * t;
+      split2(W[(size_t)k0 * H + n], W[(size_t)(k0 + 1) * H + n], f.v[0], f.v[2]);
+      split2(W[(size_t)(k0 + 8) * H + n], W[(size_t)(k0 + 9) * H + n], f.v[1], f.v[3]);
+    }
+  }
+  wf[q] = f;
+}
+
+// occ rows of a packed batch into the listed samples' rows.
+__global__ void k_scatter_occ(int N, const int8_t* __restrict__ src, const int32_t* __restrict__ list,
+                              int8_t* __restrict__ dst) {
+  const int w = blockIdx.x, b = list[w];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) dst[(size_t)b * N + i] = src[(size_t)w * N + i];
+}
+
 }  // namespace
+
+template <int KIND>
+void build_wfrag_k(scale_ctx* c) {
+  const Net<float> net = make_net<float>(c);
+  const int total = c->L * (KIND == kTF32 ? c->hpad / 8 : c->hpad / 16) * (c->hpad / 8) * 32;
+  const int blocks = (total + 255) / 256;
+  if (c->hpad == 16) k_build_wfrag<16, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag);
+  else if (c->hpad == 32) k_build_wfrag<32, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag);
+  else k_build_wfrag<64, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag);
+}
+
+cudaError_t launch_build_wfrag(scale_ctx* c) {
+  if (!c->use_mma) return cudaSuccess;
+  if (c->arch.precision == SCALE_PREC_MIXED_BF16) build_wfrag_k<kBF16>(c);
+  else build_wfrag_k<kTF32>(c);
+  return cudaGetLastError();
+}
 
 template <typename T>
 Net<T> make_net(scale_ctx* c) {
@@ -226,6 +332,7 @@ Net<T> make_net(scale_ctx* c) {
   p += (int64_t)c->h * 2 * c->Ne;
   n.proj_b = base + p;
   n.M0 = c->fp64 ? (const T*)c->M0_64 : (const T*)c->M0_32;
+  n.M0b = (const T*)c->M0b;
   n.KE = (const T*)c->KE;
   return n;
 }
@@ -242,11 +349,32 @@ cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* lis
   dim3 grid((N * h + 127) / 128, B);
   T* bufs[2] = {(T*)c->act_a, (T*)c->act_b};
   const T* in = nullptr;
-  for (int l = 0; l < c->L; ++l) {
+  const bool mma = c->use_mma && c->L > 1;
+  for (int l = 0; l < (mma ? 1 : c->L); ++l) {
     T* out = (l == c->L - 1 && keep_cache) ? (T*)c->HL : bufs[l & 1];
     T* zo = (l == 0 && keep_cache) ? (T*)c->z0 : nullptr;
     k_layer<T><<<grid, 128, 0, c->stream>>>(c->lat, net, l, occ, list, in, out, zo, B);
     in = out;
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (mma) {
+      float* out = keep_cache ? (float*)c->HL : (float*)bufs[1];
+      const long long tiles = ((long long)B * N + 15) / 16;
+      const int blocks = (int)((tiles + 7) / 8);
+      const Net<float> nf = make_net<float>(c);
+      const WFrag* wf = (const WFrag*)c->wfrag;
+      const float* fin = (const float*)in;
+      if (c->arch.precision == SCALE_PREC_MIXED_BF16) {
+        if (c->hpad == 16) k_mlp_fwd<16, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
+        else if (c->hpad == 32) k_mlp_fwd<32, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
+        else k_mlp_fwd<64, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
+      } else {
+        if (c->hpad == 16) k_mlp_fwd<16, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
+        else if (c->hpad == 32) k_mlp_fwd<32, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
+        else k_mlp_fwd<64, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
+      }
+      in = (const T*)out;
+    }
   }
   const size_t smem = sizeof(int) * (2 * N + 257);
   if (phi_out)
@@ -298,8 +426,28 @@ cudaError_t launch_build_ke(scale_ctx* c) {
 
 cudaError_t launch_logpsi_out(scale_ctx* c, double* logabs, int32_t* sign) {
   k_logpsi_out<<<c->B, 256, 0, c->stream>>>(c->Ne, c->orb_of_slot, c->logabs, c->sign_slot, c->status,
-                                             logabs, sign);
+                                             logabs, sign, nullptr);
   return cudaGetLastError();
+}
+
+cudaError_t launch_logpsi_list(scale_ctx* c, const int32_t* list, int n, double* logabs, int32_t* sign) {
+  k_logpsi_out<<<n, 256, 0, c->stream>>>(c->Ne, c->orb_of_slot, c->logabs, c->sign_slot, c->status, logabs, sign,
+                                         list);
+  return cudaGetLastError();
+}
+
+// Load the packed configurations occ[n][N] into the listed samples and build their cache
+// (slot maps, forward, FP64 inverse, projector) -- the load sequence restricted to a list.
+cudaError_t launch_load_list(scale_ctx* c, const int8_t* occ, const int32_t* list, int n) {
+  cudaError_t e;
+  k_scatter_occ<<<n, 128, 0, c->stream>>>(c->N, occ, list, c->occ);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_slots_list(c, list, n)) != cudaSuccess) return e;
+  if ((e = launch_forward(c, c->occ, n, list, true, c->Phi64)) != cudaSuccess) return e;
+  if ((e = launch_gj(c, c->Phi64, c->Ne, n, list, true, c->fp64, c->Binv, c->logabs, c->sign_slot, c->status)) !=
+      cudaSuccess)
+    return e;
+  return launch_projector(c, n, list);
 }
 
 }  // namespace scale

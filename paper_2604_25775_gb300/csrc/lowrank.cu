@@ -44,6 +44,8 @@ struct LowrankArgs {
   int32_t* move_count;   // [B] (eloc only)
   const int32_t* moves;  // explicit moves [B][M][4] (ratios only)
   int M;
+  MlpFrags mf;
+  const int32_t* list;   // optional: CTA i handles sample list[i]
 };
 
 // Candidate id -> move (kind -1 when not allowed in the current configuration).
@@ -78,11 +80,11 @@ __device__ __forceinline__ MoveDesc candidate(const LowrankArgs& a, const int8_t
   return m;
 }
 
-template <typename T>
+template <typename T, int H>
 __global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.lat.N, Ne = a.lat.Ne, h = net.h;
-  MoveScratch<T>* ms_all = reinterpret_cast<MoveScratch<T>*>(smem);
+  MoveScratch<T, H>* ms_all = reinterpret_cast<MoveScratch<T, H>*>(smem);
   MoveDesc* moves = reinterpret_cast<MoveDesc*>(ms_all + kWarps);
   double* contrib = reinterpret_cast<double*>(moves + kChunk);
   double* coeffs = contrib + kChunk;
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net)
   __shared__ int warp_cnt[kWarps];
   __shared__ double s_diag;
 
-  const int b = blockIdx.x;
+  const int b = a.list ? a.list[blockIdx.x] : blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int st = a.status[b];
   if (st & (SCALE_SAMPLE_BAD_COUNT | SCALE_SAMPLE_DOUBLE_OCC | SCALE_SAMPLE_SINGULAR)) {
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net)
   sv.HL = (const T*)a.HL + (size_t)b * N * h;
   sv.Binv = (const T*)a.Binv + (size_t)b * Ne * Ne;
   sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
-  MoveScratch<T>& ms = ms_all[warp];
+  MoveScratch<T, H>& ms = ms_all[warp];
 
   const int nb = a.nb_nn + a.nb_nnn;
   const int ncand = 2 * nb + ((a.lat.model == SCALE_MODEL_TJ && a.lat.J != 0.0) ? a.nb_nn : 0);
@@ -161,9 +163,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net)
         ms.spin = moves[mi].spin;
       }
       __syncwarp();
-      move_features<T>(a.lat, net, a.k0, sv, ms);
-      const int r = move_matrix<T>(a.lat, net, sv, ms);
-      const T det = (r < 0) ? T(CUDART_NAN) : warp_det<T>(ms, r);
+      move_features<T, H>(a.lat, net, a.k0, sv, a.mf, ms);
+      const int r = move_matrix<T, H>(a.lat, net, sv, ms);
+      const T det = (r < 0) ? T(CUDART_NAN) : warp_det<T, H>(ms, r);
       if (lane == 0) contrib[mi] = coeffs[mi] * (double)det;
       __syncwarp();
     }
@@ -181,11 +183,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net)
 }
 
 // psi(n')/psi(n) in the ascending convention for M explicit moves per sample.
-template <typename T>
+template <typename T, int H>
 __global__ void __launch_bounds__(kWarps * 32) k_ratios(LowrankArgs a, Net<T> net) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.lat.N, Ne = a.lat.Ne, h = net.h;
-  MoveScratch<T>* ms_all = reinterpret_cast<MoveScratch<T>*>(smem);
+  MoveScratch<T, H>* ms_all = reinterpret_cast<MoveScratch<T, H>*>(smem);
   int32_t* slot_s = reinterpret_cast<int32_t*>(ms_all + kWarps);
   int8_t* occ_s = reinterpret_cast<int8_t*>(slot_s + 2 * N);
   const int b = blockIdx.x;
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_ratios(LowrankArgs a, Net<T> ne
   sv.HL = (const T*)a.HL + (size_t)b * N * h;
   sv.Binv = (const T*)a.Binv + (size_t)b * Ne * Ne;
   sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
-  MoveScratch<T>& ms = ms_all[warp];
+  MoveScratch<T, H>& ms = ms_all[warp];
   for (int mi = warp; mi < a.M; mi += kWarps) {
     const int32_t* mv = a.moves + ((size_t)b * a.M + mi) * 4;
     const int kind = mv[0], src = mv[1], dst = mv[2], spin = mv[3];
@@ -223,9 +225,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_ratios(LowrankArgs a, Net<T> ne
         ms.spin = spin;
       }
       __syncwarp();
-      move_features<T>(a.lat, net, a.k0, sv, ms);
-      const int r = move_matrix<T>(a.lat, net, sv, ms);
-      const T det = (r < 0) ? T(CUDART_NAN) : warp_det<T>(ms, r);
+      move_features<T, H>(a.lat, net, a.k0, sv, a.mf, ms);
+      const int r = move_matrix<T, H>(a.lat, net, sv, ms);
+      const T det = (r < 0) ? T(CUDART_NAN) : warp_det<T, H>(ms, r);
       int par;
       if (kind == 0) {
         par = between_parity(occ_s, N, spin * N + src, spin * N + dst);
@@ -292,15 +294,15 @@ __global__ void __launch_bounds__(256) k_project(int Ne, int h, const T* __restr
   }
 }
 
-template <typename T>
+template <typename T, int H>
 size_t eloc_smem(int N) {
-  return sizeof(MoveScratch<T>) * kWarps + sizeof(MoveDesc) * kChunk + sizeof(double) * 2 * kChunk +
+  return sizeof(MoveScratch<T, H>) * kWarps + sizeof(MoveDesc) * kChunk + sizeof(double) * 2 * kChunk +
          sizeof(int32_t) * 2 * N + N + 16;
 }
 
-template <typename T>
+template <typename T, int H>
 size_t ratio_smem(int N) {
-  return sizeof(MoveScratch<T>) * kWarps + sizeof(int32_t) * 2 * N + N + 16;
+  return sizeof(MoveScratch<T, H>) * kWarps + sizeof(int32_t) * 2 * N + N + 16;
 }
 
 LowrankArgs make_args(scale_ctx* c) {
@@ -317,31 +319,34 @@ LowrankArgs make_args(scale_ctx* c) {
   a.nb_nn = c->nb_nn;
   a.nb_nnn = c->nb_nnn;
   a.status = c->status;
+  a.mf.wf = c->use_mma ? (const WFrag*)c->wfrag : nullptr;
+  a.mf.kind = c->arch.precision == SCALE_PREC_MIXED_BF16 ? kBF16 : kTF32;
   return a;
 }
 
-template <typename T>
-cudaError_t eloc_t(scale_ctx* c, double* eloc) {
+template <typename T, int H>
+cudaError_t eloc_t(scale_ctx* c, double* eloc, const int32_t* list, int n) {
   LowrankArgs a = make_args(c);
   a.out = eloc;
   a.move_count = c->move_count;
-  const size_t smem = eloc_smem<T>(c->N);
-  cudaError_t e = cudaFuncSetAttribute(k_eloc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  a.list = list;
+  const size_t smem = eloc_smem<T, H>(c->N);
+  cudaError_t e = cudaFuncSetAttribute(k_eloc<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_eloc<T><<<c->B, kWarps * 32, smem, c->stream>>>(a, make_net<T>(c));
+  k_eloc<T, H><<<n, kWarps * 32, smem, c->stream>>>(a, make_net<T>(c));
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int H>
 cudaError_t ratios_t(scale_ctx* c, const int32_t* moves, int M, double* ratio) {
   LowrankArgs a = make_args(c);
   a.out = ratio;
   a.moves = moves;
   a.M = M;
-  const size_t smem = ratio_smem<T>(c->N);
-  cudaError_t e = cudaFuncSetAttribute(k_ratios<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = ratio_smem<T, H>(c->N);
+  cudaError_t e = cudaFuncSetAttribute(k_ratios<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_ratios<T><<<c->B, kWarps * 32, smem, c->stream>>>(a, make_net<T>(c));
+  k_ratios<T, H><<<c->B, kWarps * 32, smem, c->stream>>>(a, make_net<T>(c));
   return cudaGetLastError();
 }
 
@@ -354,12 +359,22 @@ cudaError_t project_t(scale_ctx* c, int B, const int32_t* list) {
 
 }  // namespace
 
+#define SCALE_DISPATCH_H(c, FN, ...)                                                          \
+  ((c)->hpad == 16   ? ((c)->fp64 ? FN<double, 16>(__VA_ARGS__) : FN<float, 16>(__VA_ARGS__)) \
+   : (c)->hpad == 32 ? ((c)->fp64 ? FN<double, 32>(__VA_ARGS__) : FN<float, 32>(__VA_ARGS__)) \
+                     : ((c)->fp64 ? FN<double, 64>(__VA_ARGS__) : FN<float, 64>(__VA_ARGS__)))
+
 cudaError_t launch_eloc_lowrank(scale_ctx* c, double* eloc) {
-  return c->fp64 ? eloc_t<double>(c, eloc) : eloc_t<float>(c, eloc);
+  return SCALE_DISPATCH_H(c, eloc_t, c, eloc, nullptr, c->B);
+}
+
+// E_loc of the listed samples only (outputs indexed by sample).
+cudaError_t launch_eloc_lowrank_list(scale_ctx* c, const int32_t* list, int n, double* eloc) {
+  return SCALE_DISPATCH_H(c, eloc_t, c, eloc, list, n);
 }
 
 cudaError_t launch_ratios(scale_ctx* c, const int32_t* moves, int M, double* ratio) {
-  return c->fp64 ? ratios_t<double>(c, moves, M, ratio) : ratios_t<float>(c, moves, M, ratio);
+  return SCALE_DISPATCH_H(c, ratios_t, c, moves, M, ratio);
 }
 
 cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list) {

@@ -61,6 +61,7 @@ struct Net {
   const T* proj_w;               // [h][2Ne]
   const T* proj_b;               // [2Ne]
   const T* M0;                   // [2N][Ne]
+  const T* M0b;                  // [2N][Ne] M0[o] + proj_b[s(o)] (derived at set_params)
   const T* KE;                   // [Ns][4][k0*k0][h]
 };
 
@@ -90,6 +91,9 @@ struct scale_ctx {
   int N = 0, Ne = 0, h = 0, L = 0, k0 = 1, r0 = 0;
   bool fp64 = true;
   bool lowrank_ok = false;  // SCALE layer layout (k_l = 1 for l >= 1)
+  bool use_mma = false;     // mixed mode, SCALE layout, h in {16, 32, 64}: site-wise layers on tensor cores
+  int hpad = 16;            // channel capacity of the per-warp scratch (16, 32 or 64)
+  void* wfrag = nullptr;    // BF16 hi/lo mma fragments of the site-wise layers
   int64_t P = 0;
   int B_max = 0, B = 0;
   int max_moves = 0;
@@ -103,6 +107,7 @@ struct scale_ctx {
   float* params32 = nullptr;
   double* M0_64 = nullptr;
   float* M0_32 = nullptr;
+  void* M0b = nullptr;  // [2N][Ne] T: M0[o] + proj_b[s(o)]
   void* KE = nullptr;
 
   // lattice tables
@@ -163,6 +168,10 @@ cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32
                       int32_t* status);
 cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list);
 cudaError_t launch_build_ke(scale_ctx* c);
+cudaError_t launch_build_wfrag(scale_ctx* c);
+cudaError_t launch_eloc_lowrank_list(scale_ctx* c, const int32_t* list, int n, double* eloc);
+cudaError_t launch_logpsi_list(scale_ctx* c, const int32_t* list, int n, double* logabs, int32_t* sign);
+cudaError_t launch_load_list(scale_ctx* c, const int8_t* occ, const int32_t* list, int n);
 cudaError_t launch_logpsi_out(scale_ctx* c, double* logabs, int32_t* sign);
 cudaError_t launch_eloc_lowrank(scale_ctx* c, double* eloc);
 cudaError_t launch_ratios(scale_ctx* c, const int32_t* moves, int M, double* ratio);

@@ -31,6 +31,7 @@ ACT_TANH = 0
 ACT_SILU = 1
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_MIXED_BF16 = 2
 
 MOVE_NONE = -1
 MOVE_HOP = 0

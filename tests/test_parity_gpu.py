@@ -160,9 +160,11 @@ def test_local_energy_mixed_16x16_full_batch_sampled():
     pick = np.sort(rng.choice(8192, 32, replace=False))
     cond = conditioning(ora, occ[pick])
     e_o, _ = ora.local_energy(occ[pick])
-    _check("16x16 mixed lowrank (sampled)", e[pick], e_o, cond, MIXED_TOL, 1e3, min_good=1)
+    # uniformly random 16x16 configurations have cond(Phi) >= 1e3; the strict band is
+    # cond < 1e4 here, every sample still within cond * 8 * 2^-24
+    _check("16x16 mixed lowrank (sampled)", e[pick], e_o, cond, MIXED_TOL, 1e4, min_good=5)
     la_o, sg_o = ora.log_psi(occ[pick])
-    good = cond < 1e3
+    good = cond < 1e4
     assert rel_err(la.cpu().numpy()[pick][good], la_o[good]).max() <= MIXED_TOL
     assert np.isfinite(e).all()
 
