@@ -204,6 +204,27 @@ const char *scale_last_error(scale_ctx *ctx);
 /* Free the context and its device memory (synchronises its stream). NULL is a no-op. */
 void scale_destroy(scale_ctx *ctx);
 
+/* log|psi| [B] and sign [B] (ascending convention, as scale_log_psi) of B configurations
+ * occ[B][N] for the given shape, parameters and reference orbitals, WITHOUT any device
+ * allocation by the call and without a context: for callers that cannot call cudaMalloc
+ * (code running under a memory pool or arena owned by another runtime, plugins inside a
+ * host application, code that may not allocate after setup). The paper has no counterpart;
+ * this is a packaging of the load path (forward, Slater matrices, FP64 LU with partial
+ * pivoting) for such callers.
+ * All pointers are device pointers owned by the caller: params (scale_param_count
+ * float64), M0 ([2N][Ne] float64), occ, logabs, sign. The working memory is one 64 MiB
+ * file-scope device array of the library that every GPU loading it holds until the process
+ * exits; larger batches are processed in chunks within the call, and a shape whose single
+ * sample does not fit returns SCALE_EBUDGET. Every call shares that array and leaves its
+ * contents behind: calls that overlap on the GPU (other streams or host threads on the same
+ * device) race and must be serialised by the caller. The first call on a device looks up the
+ * array's device address with that device current (cudaGetSymbolAddress); make that first
+ * call before any stream capture. Work is enqueued on cuda_stream (NULL = legacy stream).
+ * Per-sample problems as in scale_log_psi (-inf, sign 0). */
+scale_status scale_log_psi_noalloc(const scale_system *sys, const scale_arch *arch, const double *params,
+                                   const double *M0, const int8_t *occ, int32_t B, double *logabs,
+                                   int32_t *sign, void *cuda_stream);
+
 /* ------------------------------------------------------------------------------------
  * Serving: continuous batching of local-energy and amplitude requests from many Markov
  * chains, on lattices of different sizes and dopings, with device-resident chain state.

@@ -268,6 +268,31 @@ def make_context(pb: I.Problem, params: np.ndarray, M0: np.ndarray, max_batch: i
 # ---------------------------------------------------------------------------------------
 # Serving (scale_server_*): continuous batching over device-resident chains.
 # ---------------------------------------------------------------------------------------
+def scale_log_psi_noalloc(pb, params, M0, occ, logabs, sign, stream=None):
+    """scale_log_psi_noalloc: log|psi| / sign of occ without a context or a device
+    allocation (all tensors are the caller's CUDA tensors)."""
+    import torch
+    lib = load_library()
+    if not getattr(lib, "_na_ready", False):
+        V = ctypes.c_void_p
+        lib.scale_log_psi_noalloc.restype = ctypes.c_int
+        lib.scale_log_psi_noalloc.argtypes = [ctypes.POINTER(scale_system), ctypes.POINTER(scale_arch), V, V, V,
+                                              ctypes.c_int32, V, V, V]
+        lib._na_ready = True
+    s, a = make_descriptors(pb)
+    B = occ.shape[0]
+    st = stream if stream is not None else torch.cuda.current_stream()
+    status = lib.scale_log_psi_noalloc(
+        ctypes.byref(s), ctypes.byref(a), _ptr(params, torch.float64, (I.param_count(pb),), "params"),
+        _ptr(M0, torch.float64, (2 * pb.N, pb.Ne), "M0"), _ptr(occ, torch.int8, (B, pb.N), "occ"), B,
+        _ptr(logabs, torch.float64, (B,), "logabs"), _ptr(sign, torch.int32, (B,), "sign"),
+        ctypes.c_void_p(st.cuda_stream))
+    if status != OK:
+        raise ScaleError(status, "scale_log_psi_noalloc failed")
+
+
+EXPORTED += ["scale_log_psi_noalloc"]
+
 SRV_OPEN, SRV_ELOC, SRV_STEP, SRV_LOGPSI, SRV_CLOSE = range(5)
 EXPORTED += ["scale_server_create", "scale_server_submit", "scale_server_poll", "scale_server_stats",
              "scale_server_destroy"]
