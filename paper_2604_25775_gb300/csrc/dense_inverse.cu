@@ -26,7 +26,8 @@ namespace scale {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 1024;  // 32 warps: DFMA latency hidden within one CTA (refresh batches
+                                 // are often one CTA per SM)
 
 template <typename TW>
 struct ArgMax {
@@ -143,20 +144,31 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
       prow[j * n + c] = A[(size_t)piv[K0 + j] * n + c];
     }
     __syncthreads();
-    // rank-w update of the columns outside the panel
+    // rank-w update of the columns outside the panel: warp per row, lanes over columns,
+    // the row's multipliers u_j = U[i][j] in registers, two columns per lane in flight
     const int c_lo = kInverse ? 0 : K0 + w;
-    const int ncols = n - c_lo;
-    for (int q = tid; q < n * ncols; q += kThreads) {
-      const int i = q / ncols, c = c_lo + (q - i * ncols);
-      if (c >= K0 && c < K0 + w) continue;
+    for (int i = warp; i < n; i += kThreads / 32) {
       if (!kInverse && used[i]) continue;
-      TW acc = A[(size_t)i * n + c];
-#pragma unroll 4
-      for (int j = 0; j < w; ++j) {
-        const TW u = panel[i * W + j] - ((piv[K0 + j] == i) ? TW(1) : TW(0));
-        acc += u * prow[j * n + c];
+      TW u[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) u[j] = (j < w) ? panel[i * W + j] - ((piv[K0 + j] == i) ? TW(1) : TW(0)) : TW(0);
+      TW* Ai = A + (size_t)i * n;
+      for (int c = c_lo + lane; c < n; c += 64) {
+        const int c2 = c + 32;
+        const bool in1 = !(c >= K0 && c < K0 + w);
+        const bool in2 = c2 < n && !(c2 >= K0 && c2 < K0 + w);
+        TW a1 = in1 ? Ai[c] : TW(0);
+        TW a2 = in2 ? Ai[c2] : TW(0);
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          if (j < w) {
+            a1 += u[j] * prow[j * n + c];
+            if (c2 < n) a2 += u[j] * prow[j * n + c2];
+          }
+        }
+        if (in1) Ai[c] = a1;
+        if (in2) Ai[c2] = a2;
       }
-      A[(size_t)i * n + c] = acc;
     }
     // write the swept panel back
     for (int q = tid; q < n * w; q += kThreads) {

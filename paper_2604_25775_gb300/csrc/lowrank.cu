@@ -22,7 +22,6 @@ namespace scale {
 namespace {
 
 constexpr int kWarps = 8;
-constexpr int kChunk = 256;
 
 struct MoveDesc {
   int kind, src, dst, spin;
@@ -80,17 +79,20 @@ __device__ __forceinline__ MoveDesc candidate(const LowrankArgs& a, const int8_t
   return m;
 }
 
-template <typename T, int H>
-__global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net) {
+// WARPS warps per sample; with stage_pt the sample's projector rows (2 x Ne x h) are copied
+// to shared memory once and every move reads them from there.
+template <typename T, int H, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net, int stage_pt) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.lat.N, Ne = a.lat.Ne, h = net.h;
   MoveScratch<T, H>* ms_all = reinterpret_cast<MoveScratch<T, H>*>(smem);
-  MoveDesc* moves = reinterpret_cast<MoveDesc*>(ms_all + kWarps);
-  double* contrib = reinterpret_cast<double*>(moves + kChunk);
-  double* coeffs = contrib + kChunk;
-  int32_t* slot_s = reinterpret_cast<int32_t*>(coeffs + kChunk);
+  T* pt_s = reinterpret_cast<T*>(ms_all + WARPS);                  // [2][Ne][h] when staged
+  MoveDesc* moves = reinterpret_cast<MoveDesc*>(pt_s + (stage_pt ? (size_t)2 * Ne * h : 0));
+  double* contrib = reinterpret_cast<double*>(moves + WARPS * 32);
+  double* coeffs = contrib + WARPS * 32;
+  int32_t* slot_s = reinterpret_cast<int32_t*>(coeffs + WARPS * 32);
   int8_t* occ_s = reinterpret_cast<int8_t*>(slot_s + 2 * N);
-  __shared__ int warp_cnt[kWarps];
+  __shared__ int warp_cnt[WARPS];
   __shared__ double s_diag;
 
   const int b = a.list ? a.list[blockIdx.x] : blockIdx.x;
@@ -129,13 +131,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net)
   sv.HL = (const T*)a.HL + (size_t)b * N * h;
   sv.Binv = (const T*)a.Binv + (size_t)b * Ne * Ne;
   sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
+  if (stage_pt) {
+    const T* src = sv.Pt;
+    for (int q = tid; q < 2 * Ne * h; q += blockDim.x) pt_s[q] = src[q];
+    sv.Pt = pt_s;
+    __syncthreads();
+  }
   MoveScratch<T, H>& ms = ms_all[warp];
 
   const int nb = a.nb_nn + a.nb_nnn;
   const int ncand = 2 * nb + ((a.lat.model == SCALE_MODEL_TJ && a.lat.J != 0.0) ? a.nb_nn : 0);
   double total = 0.0;  // thread 0
   int nmoves = 0;
-  for (int cs = 0; cs < ncand; cs += kChunk) {
+  for (int cs = 0; cs < ncand; cs += WARPS * 32) {
     const int id = cs + tid;
     double cf = 0.0;
     MoveDesc m{-1, 0, 0, 0};
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net)
     if (lane == 0) warp_cnt[warp] = __popc(bal);
     __syncthreads();
     int off = 0, nm = 0;
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < WARPS; ++w) {
       if (w < warp) off += warp_cnt[w];
       nm += warp_cnt[w];
     }
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_eloc(LowrankArgs a, Net<T> net)
       coeffs[pos] = cf;
     }
     __syncthreads();
-    for (int mi = warp; mi < nm; mi += kWarps) {
+    for (int mi = warp; mi < nm; mi += WARPS) {
       if (lane == 0) {
         ms.kind = moves[mi].kind;
         ms.src = moves[mi].src;
@@ -294,10 +302,10 @@ __global__ void __launch_bounds__(256) k_project(int Ne, int h, const T* __restr
   }
 }
 
-template <typename T, int H>
-size_t eloc_smem(int N) {
-  return sizeof(MoveScratch<T, H>) * kWarps + sizeof(MoveDesc) * kChunk + sizeof(double) * 2 * kChunk +
-         sizeof(int32_t) * 2 * N + N + 16;
+template <typename T, int H, int WARPS>
+size_t eloc_smem(int N, int Ne, int h, bool stage_pt) {
+  return sizeof(MoveScratch<T, H>) * WARPS + (stage_pt ? sizeof(T) * 2 * Ne * h : 0) +
+         (sizeof(MoveDesc) + sizeof(double) * 2) * WARPS * 32 + sizeof(int32_t) * 2 * N + N + 16;
 }
 
 template <typename T, int H>
@@ -324,17 +332,29 @@ LowrankArgs make_args(scale_ctx* c) {
   return a;
 }
 
+template <typename T, int H, int WARPS>
+cudaError_t eloc_launch(scale_ctx* c, const LowrankArgs& a, int n, bool stage) {
+  const size_t smem = eloc_smem<T, H, WARPS>(c->N, c->Ne, c->h, stage);
+  cudaError_t e = cudaFuncSetAttribute(k_eloc<T, H, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_eloc<T, H, WARPS><<<n, WARPS * 32, smem, c->stream>>>(a, make_net<T>(c), stage ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Launch shape: 16 warps with the projector staged in shared memory when it fits (one CTA
+// per SM, 512 threads), otherwise 8 warps reading the projector through L1.
 template <typename T, int H>
 cudaError_t eloc_t(scale_ctx* c, double* eloc, const int32_t* list, int n) {
   LowrankArgs a = make_args(c);
   a.out = eloc;
   a.move_count = c->move_count;
   a.list = list;
-  const size_t smem = eloc_smem<T, H>(c->N);
-  cudaError_t e = cudaFuncSetAttribute(k_eloc<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_eloc<T, H><<<n, kWarps * 32, smem, c->stream>>>(a, make_net<T>(c));
-  return cudaGetLastError();
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (sizeof(T) == 4 && eloc_smem<T, H, 16>(c->N, c->Ne, c->h, true) <= (size_t)optin)
+    return eloc_launch<T, H, 16>(c, a, n, true);
+  return eloc_launch<T, H, 8>(c, a, n, false);
 }
 
 template <typename T, int H>

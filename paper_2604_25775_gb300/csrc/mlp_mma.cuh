@@ -130,10 +130,10 @@ __device__ __forceinline__ void mlp_tile(float (&x)[H / 8][4], const WFrag* __re
       }
       const float b0 = bl[8 * j + 2 * t], b1 = bl[8 * j + 2 * t + 1];
       const float z0 = c[0] + b0, z1 = c[1] + b1, z2 = c[2] + b0, z3 = c[3] + b1;
-      x[j][0] = (res ? x[j][0] : 0.f) + act_fn<float>(act, z0);
-      x[j][1] = (res ? x[j][1] : 0.f) + act_fn<float>(act, z1);
-      x[j][2] = (res ? x[j][2] : 0.f) + act_fn<float>(act, z2);
-      x[j][3] = (res ? x[j][3] : 0.f) + act_fn<float>(act, z3);
+      x[j][0] = (res ? x[j][0] : 0.f) + act_fast(act, z0);
+      x[j][1] = (res ? x[j][1] : 0.f) + act_fast(act, z1);
+      x[j][2] = (res ? x[j][2] : 0.f) + act_fast(act, z2);
+      x[j][3] = (res ? x[j][3] : 0.f) + act_fast(act, z3);
     }
   }
 }

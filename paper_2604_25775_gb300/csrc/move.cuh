@@ -31,7 +31,7 @@ struct MoveScratch {
   int nold[kSMax], nnew[kSMax];
   int pair_s[2 * 9];  // S index of each (touched site, offset) pair, -1 if none
   int slot[kRMax], orb[kRMax], sidx[kRMax], moved[kRMax];
-  T feat[32][H];      // new features H'(L) on S (rows padded to two 16-row tiles)
+  T feat[kSMax][H];   // new features H'(L) on S (tile loads/stores stop at nS)
   T hl[kSMax][H];     // cached features H(L) on S
   T R[kRMax][kRMax + 1];
 };
@@ -217,42 +217,45 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   const int lane = threadIdx.x & 31;
   const int N = lat.N, Ne = lat.Ne, h = net.h;
   const int nS = ms.nS;
-  // electrons (s, spin) in S-major order, compacted with ballots
-  int r = 0;
+  // electrons on S after the move: spin-up ones first, then spin-down, each group in S
+  // order, compacted with ballots (the determinant does not depend on the row order
+  // because rows and columns of R follow the same list)
+  int r = 0, r_up = 0;
   bool bad = false;
-  for (int base = 0; base < 2 * nS; base += 32) {
-    const int q = base + lane;
-    int slot = -1, mv = 0, s = 0, sp = 0;
-    bool occ = false;
-    if (q < 2 * nS) {
-      s = q >> 1;
-      sp = q & 1;
-      occ = (ms.nnew[s] >> sp) & 1;
-      if (occ) {
-        const int site = ms.site[s];
-        if ((ms.nold[s] >> sp) & 1) {
-          slot = sv.slot_of_orb[sp * N + site];  // same electron, same orbital
-        } else if (ms.kind == 0) {
-          slot = sv.slot_of_orb[sp * N + ms.src];  // the hopping electron
-          mv = 1;
-        } else {
-          slot = sv.slot_of_orb[sp * N + (site == ms.src ? ms.dst : ms.src)];  // exchanged spin
-          mv = 1;
+  for (int sp = 0; sp < 2; ++sp) {
+    if (sp == 1) r_up = r;
+    for (int base = 0; base < nS; base += 32) {
+      const int s = base + lane;
+      int slot = -1, mv = 0;
+      bool occ = false;
+      if (s < nS) {
+        occ = (ms.nnew[s] >> sp) & 1;
+        if (occ) {
+          const int site = ms.site[s];
+          if ((ms.nold[s] >> sp) & 1) {
+            slot = sv.slot_of_orb[sp * N + site];  // same electron, same orbital
+          } else if (ms.kind == 0) {
+            slot = sv.slot_of_orb[sp * N + ms.src];  // the hopping electron
+            mv = 1;
+          } else {
+            slot = sv.slot_of_orb[sp * N + (site == ms.src ? ms.dst : ms.src)];  // exchanged spin
+            mv = 1;
+          }
         }
       }
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, occ);
-    if (occ) {
-      const int pos = r + __popc(bal & ((1u << lane) - 1u));
-      if (slot < 0) bad = true;
-      if (pos < kRMax) {
-        ms.slot[pos] = slot;
-        ms.orb[pos] = sp * N + ms.site[s];
-        ms.sidx[pos] = s;
-        ms.moved[pos] = mv;
+      const unsigned bal = __ballot_sync(0xffffffffu, occ);
+      if (occ) {
+        const int pos = r + __popc(bal & ((1u << lane) - 1u));
+        if (slot < 0) bad = true;
+        if (pos < kRMax) {
+          ms.slot[pos] = slot;
+          ms.orb[pos] = sp * N + ms.site[s];
+          ms.sidx[pos] = s;
+          ms.moved[pos] = mv;
+        }
       }
+      r += __popc(bal);
     }
-    r += __popc(bal);
   }
   bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) ms.r = r;
@@ -264,26 +267,29 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   __syncwarp();
   const int cb = ms.slot[lane < r ? lane : 0];
   // Pt terms, column b = lane: the Pt[spin][c_b] row in registers (16 channels at a time),
-  // each electron of that spin dotted against its feature row (H' if it moved, Delta H if not)
-  T acc_own = T(0);  // unused lanes keep zero
+  // each electron of that spin dotted against its feature row (H' if it moved, Delta H if
+  // not); identity for the electrons that kept their orbital
+  if (lane < r)
+    for (int a = 0; a < r; ++a) ms.R[a][lane] = (!ms.moved[a] && a == lane) ? T(1) : T(0);
+  __syncwarp();
   for (int sp = 0; sp < 2; ++sp) {
+    const int a0 = sp ? r_up : 0, a1 = sp ? r : r_up;
+    if (a0 == a1) continue;
     const T* pt = sv.Pt + ((size_t)sp * Ne + cb) * h;
     for (int c0 = 0; c0 < h; c0 += 16) {
       T pv[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) pv[u] = (c0 + u < h) ? pt[c0 + u] : T(0);
-      for (int a = 0; a < r; ++a) {
-        if (ms.orb[a] / N != sp) continue;
-        const T* row = ms.moved[a] ? ms.feat[ms.sidx[a]] : ms.hl[ms.sidx[a]];
+      for (int a = a0; a < a1; ++a) {
+        const T* row = (ms.moved[a] ? ms.feat[ms.sidx[a]] : ms.hl[ms.sidx[a]]) + c0;
         T v = T(0);
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-          if (c0 + u < h) v += row[c0 + u] * pv[u];
-        if (lane < r) ms.R[a][lane] = (c0 == 0 ? ((!ms.moved[a] && a == lane) ? T(1) : T(0)) : ms.R[a][lane]) + v;
+          if (c0 + u < h) v += row[u] * pv[u];
+        if (lane < r) ms.R[a][lane] += v;
       }
     }
   }
-  (void)acc_own;
   __syncwarp();
   // moved rows: + (M0[o'] + proj_b[s]) . Binv[c_b], lanes split k, one warp reduction per b
   for (int a = 0; a < r; ++a) {
@@ -319,15 +325,24 @@ __device__ T warp_det(MoveScratch<T, H>& ms, int r) {
   const int lane = threadIdx.x & 31;
   T det = T(1);
   for (int k = 0; k < r; ++k) {
-    T best = (lane >= k && lane < r) ? fabs(ms.R[lane][k]) : T(-1);
-    int p = lane;
+    int p;
+    const bool mine = lane >= k && lane < r;
+    if constexpr (sizeof(T) == 4) {
+      // |x| of non-negative floats orders like its bit pattern: one warp max + ballot
+      const unsigned key = mine ? __float_as_uint(fabsf((float)ms.R[lane][k])) : 0u;
+      const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+      p = __ffs(__ballot_sync(0xffffffffu, mine && key == mx)) - 1;
+    } else {
+      T best = mine ? fabs(ms.R[lane][k]) : T(-1);
+      p = lane;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const T ob = __shfl_xor_sync(0xffffffffu, best, off);
-      const int op = __shfl_xor_sync(0xffffffffu, p, off);
-      if (ob > best || (ob == best && op < p)) {
-        best = ob;
-        p = op;
+      for (int off = 16; off > 0; off >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int op = __shfl_xor_sync(0xffffffffu, p, off);
+        if (ob > best || (ob == best && op < p)) {
+          best = ob;
+          p = op;
+        }
       }
     }
     if (p != k) {

@@ -65,10 +65,37 @@ struct Net {
   const T* KE;                   // [Ns][4][k0*k0][h]
 };
 
+// FP32 tanh for the tensor-core layers, from the odd Taylor series
+//   tanh z = z - z^3/3 + 2z^5/15 - 17z^7/315 + 62z^9/2835 - 1382z^11/155925
+//            + 21844z^13/6081075 - 929569z^15/638512875 + ...
+// for |z| < 0.5 (the first omitted term is below 1e-8 relative there), and from
+// tanh|z| = (1 - e^{-2|z|}) / (1 + e^{-2|z|}) above (no cancellation once |z| >= 0.5).
+__device__ __forceinline__ float tanh_f32(float z) {
+  const float a = fabsf(z);
+  const float s = z * z;
+  float p = -929569.f / 638512875.f;
+  p = fmaf(p, s, 21844.f / 6081075.f);
+  p = fmaf(p, s, -1382.f / 155925.f);
+  p = fmaf(p, s, 62.f / 2835.f);
+  p = fmaf(p, s, -17.f / 315.f);
+  p = fmaf(p, s, 2.f / 15.f);
+  p = fmaf(p, s, -1.f / 3.f);
+  const float small = fmaf(z * s, p, z);
+  const float e = __expf(-2.f * a);
+  const float big = copysignf(__fdividef(1.f - e, 1.f + e), z);
+  return a < 0.5f ? small : big;
+}
+
 template <typename T>
 __device__ __forceinline__ T act_fn(int act, T z) {
   if (act == SCALE_ACT_TANH) return tanh(z);
   return z / (T(1) + exp(-z));
+}
+
+// Activation of the tensor-core layers (FP32): own tanh, SiLU through the FP32 exp.
+__device__ __forceinline__ float act_fast(int act, float z) {
+  if (act == SCALE_ACT_TANH) return tanh_f32(z);
+  return z / (1.f + __expf(-z));
 }
 
 template <typename T>

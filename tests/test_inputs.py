@@ -32,3 +32,17 @@ def test_moves_are_allowed():
     assert ((after & 1).sum(1) == pb.n_up).all()
     assert not (after == 3).any()
     assert (mv[:, 0] == I.MOVE_HOP).sum() >= 28
+
+
+def test_tanh_series_and_identity_bound():
+    """The FP32 tanh of the tensor-core layers uses the odd Taylor series through z^15 for
+    |z| < 0.5 and (1 - e^{-2|z|})/(1 + e^{-2|z|}) above; in exact arithmetic the series'
+    truncation error is below 1e-8 relative (FP32 rounding is checked by the GPU parity)."""
+    import numpy as np
+    c = [1.0, -1 / 3, 2 / 15, -17 / 315, 62 / 2835, -1382 / 155925, 21844 / 6081075, -929569 / 638512875]
+    z = np.linspace(-0.5, 0.5, 20001)
+    series = sum(ck * z ** (2 * k + 1) for k, ck in enumerate(c))
+    assert np.max(np.abs(series - np.tanh(z)) / np.maximum(np.abs(np.tanh(z)), 1e-300)) < 1e-8
+    z2 = np.linspace(0.5, 20, 20001)
+    e = np.exp(-2 * z2)
+    assert np.max(np.abs((1 - e) / (1 + e) - np.tanh(z2))) < 1e-15
