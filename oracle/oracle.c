@@ -21,7 +21,8 @@
  *     space;
  *   * E_loc(n) = sum_n' <n|H|n'> psi(n')/psi(n) (Sec. II.A) with EVERY psi(n') from a
  *     full network forward plus a fresh LU (the O(N^4) route of Sec. III.A);
- *   * d log|psi| / d theta by a hand-written FP64 backward pass.
+ *   * d log|psi| / d theta by a hand-written FP64 backward pass;
+ *   * Metropolis steps n -> n' with acceptance min(1, |psi(n')/psi(n)|^2) (Sec. II.A).
  *
  * Parity status: every function here is pinned by CPU tests (closed-form U=0 energy,
  * library convolution and slogdet, dense-Hamiltonian enumeration, finite differences,
@@ -501,6 +502,72 @@ int ora_ratio(const ora_model *m, int B, const int8_t *occ, const int32_t *moves
       amplitude(m, x, &w, &la, &sg);
       amplitude(m, x2, &w, &la2, &sg2);
       ratio[b] = (sg == 0 || sg2 == 0) ? 0.0 : (double)(sg * sg2) * exp(la2 - la);
+    }
+    free(x2);
+    ws_free(&w);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Metropolis sampling of P(n) ~ |psi(n)|^2 by local updates (Sec. II.A; the optimisation
+ * settings give 2.5 N steps per sample). The paper does not spell out the proposal; this
+ * is the symmetric single-electron hop:
+ *   electron  = the pick-th occupied orbital in ascending orbital order (o = s*N + i),
+ *   direction = +x, -x, +y, -y for dir = 0..3 (nearest neighbour of its site);
+ *   a target off an open edge, or already holding an electron of that spin (t-J: any
+ *   electron), is rejected; otherwise the move is accepted when u < |psi(n')/psi(n)|^2.
+ * A current amplitude of zero accepts any move to a non-zero amplitude. Every random
+ * number is an input: pick [S][B] in [0, Ne), dir [S][B] in [0, 4), u [S][B] in [0, 1).
+ * occ [B][N] is advanced in place; accepted[b] counts the accepted steps.
+ * ------------------------------------------------------------------------------------ */
+int ora_metropolis(const ora_model *m, int B, int S, int8_t *occ, const int32_t *pick, const int32_t *dir,
+                   const double *u, int32_t *accepted) {
+  const int N = m->Lx * m->Ly, Ne = m->n_up + m->n_dn;
+#pragma omp parallel
+  {
+    ora_ws w = ws_alloc(m);
+    int8_t *x2 = (int8_t *)malloc(N);
+#pragma omp for schedule(dynamic)
+    for (int b = 0; b < B; ++b) {
+      int8_t *x = occ + (int64_t)b * N;
+      double la;
+      int sg;
+      amplitude(m, x, &w, &la, &sg);
+      accepted[b] = 0;
+      for (int st = 0; st < S; ++st) {
+        const int64_t q = (int64_t)st * B + b;
+        /* the pick-th occupied orbital, ascending */
+        int k = pick[q], o_src = -1;
+        if (k < 0 || k >= Ne) continue;
+        for (int o = 0; o < 2 * N; ++o)
+          if ((x[o % N] >> (o / N)) & 1) {
+            if (k == 0) { o_src = o; break; }
+            --k;
+          }
+        const int s = o_src / N, i = o_src % N;
+        static const int dx[4] = {1, -1, 0, 0}, dy[4] = {0, 0, 1, -1};
+        if (dir[q] < 0 || dir[q] > 3) continue;
+        const int j = site_offset(m, i, dx[dir[q]], dy[dir[q]]);
+        if (j < 0) continue;
+        if (m->model == 1 ? x[j] != 0 : ((x[j] >> s) & 1)) continue;
+        memcpy(x2, x, N);
+        x2[i] &= (int8_t)~(1 << s);
+        x2[j] |= (int8_t)(1 << s);
+        double la2;
+        int sg2;
+        amplitude(m, x2, &w, &la2, &sg2);
+        int acc;
+        if (sg2 == 0) acc = 0;
+        else if (sg == 0) acc = 1;
+        else acc = u[q] < exp(2.0 * (la2 - la));
+        if (acc) {
+          memcpy(x, x2, N);
+          la = la2;
+          sg = sg2;
+          accepted[b] += 1;
+        }
+      }
     }
     free(x2);
     ws_free(&w);

@@ -77,6 +77,8 @@ def _load():
             lib.ora_diag.restype = ctypes.c_double
             lib.ora_diag.argtypes = [P(_Model), ctypes.c_void_p]
             lib.ora_num_threads.restype = ctypes.c_int
+            lib.ora_metropolis.restype = ctypes.c_int
+            lib.ora_metropolis.argtypes = [P(_Model), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 5
             _lib = lib
     return _lib
 
@@ -177,6 +179,20 @@ class Model:
     def diag(self, occ1: np.ndarray) -> float:
         occ1 = np.ascontiguousarray(occ1, dtype=np.int8)
         return float(_load().ora_diag(ctypes.byref(self.s), occ1.ctypes.data))
+
+    def metropolis(self, occ: np.ndarray, pick: np.ndarray, direction: np.ndarray, u: np.ndarray):
+        """Metropolis steps (hop proposals, acceptance min(1, |psi'/psi|^2)); pick, direction
+        and u are [S][B]. Returns (final occ [B][N], accepted [B])."""
+        x = np.array(occ, dtype=np.int8, order="C", copy=True)
+        pick = np.ascontiguousarray(pick, dtype=np.int32)
+        direction = np.ascontiguousarray(direction, dtype=np.int32)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        S, B = u.shape
+        assert x.shape[0] == B and pick.shape == (S, B) and direction.shape == (S, B)
+        acc = np.zeros(B, dtype=np.int32)
+        _load().ora_metropolis(ctypes.byref(self.s), B, S, x.ctypes.data, pick.ctypes.data,
+                               direction.ctypes.data, u.ctypes.data, acc.ctypes.data)
+        return x, acc
 
     def with_params(self, params: np.ndarray) -> "Model":
         return Model(self.d, params, self.M0)

@@ -211,6 +211,17 @@ def plane_wave_M0(pb: Problem) -> np.ndarray:
     return M0
 
 
+def metropolis_randoms(pb: Problem, B: int, S: int, seed: int):
+    """Random inputs of S Metropolis steps for B chains: the electron pick [S][B] int32 in
+    [0, Ne) (rank of the electron in ascending orbital order), the hop direction [S][B]
+    int32 in [0, 4) (+x, -x, +y, -y) and the acceptance uniform [S][B] float64 in [0, 1)."""
+    rng = np.random.default_rng(seed)
+    pick = rng.integers(0, pb.Ne, size=(S, B), dtype=np.int32)
+    direction = rng.integers(0, 4, size=(S, B), dtype=np.int32)
+    u = rng.random((S, B))
+    return pick, direction, u
+
+
 def random_hop_moves(pb: Problem, occ: np.ndarray, seed: int) -> np.ndarray:
     """One proposed nearest-neighbour move per sample, int32 [B][4] = (kind, src, dst, spin).
 
