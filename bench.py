@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--full-samples", type=int, default=128)
     ap.add_argument("--cpu-samples", type=int, default=48)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--sweep-steps", type=int, default=64)
     return ap.parse_args()
 
 
@@ -382,6 +384,37 @@ def main():
         line["grad"] = {"walkers": ng, "ms": a.elapsed_time(b2), "params": ctxg.P}
         del g
         ctxg.close()
+        # Metropolis sweep on the same walkers: hop proposal, rank-r ratio, accept, Woodbury
+        # commit of the accepted moves (random numbers generated on the host beforehand)
+        if args.sweep_steps > 0:
+            S = args.sweep_steps
+            ctxs = Bd.make_context(pb, params, M0, B)
+            ctxs.scale_load(occ_d)
+            pk, dr, uu = I.metropolis_randoms(pb, B, 4 + S, 77)
+            pk_d, dr_d, uu_d = (torch.from_numpy(x).cuda() for x in (pk, dr, uu))
+            ctxs.sweep(pk_d[:4].contiguous(), dr_d[:4].contiguous(), uu_d[:4].contiguous())
+            pk_t, dr_t, uu_t = pk_d[4:].contiguous(), dr_d[4:].contiguous(), uu_d[4:].contiguous()
+            torch.cuda.synchronize()
+            a.record()
+            acc_s = ctxs.sweep(pk_t, dr_t, uu_t)
+            b2.record()
+            torch.cuda.synchronize()
+            sw_ms = a.elapsed_time(b2)
+            steps_per_sample = int(2.5 * pb.N)
+            line["sweep"] = {"walkers": B, "steps": S, "ms": sw_ms,
+                             "walker_steps_per_s": B * S / (sw_ms / 1e3),
+                             "acceptance": float(acc_s.double().mean().item() / S),
+                             "ms_per_sweep_2.5N": sw_ms / S * steps_per_sample,
+                             "steps_per_sweep": steps_per_sample}
+            del pk_d, dr_d, uu_d, pk_t, dr_t, uu_t
+            ctxs.close()
+        # serving: open-loop Poisson sweep-step requests over mixed chains, continuous batching
+        if args.serve_seconds > 0:
+            from paper_2604_25775_gb300 import serve_bench
+            sv = serve_bench.run(duration_s=args.serve_seconds)
+            line["serve"] = {k: sv[k] for k in ("p50_ms", "p99_ms", "throughput_eloc_per_s", "capacity_eloc_per_s",
+                                                "offered_load", "requests", "open_p50_ms", "open_p99_ms",
+                                                "resident_max_gb", "classes", "chains")}
         # CPU oracle baseline on a bounded sample
         from oracle import oracle as O
         m = O.Model(pb, params, M0)

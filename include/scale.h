@@ -185,6 +185,21 @@ scale_status scale_local_energy(scale_ctx *ctx, int32_t path, double *eloc);
  * and skips a move whose source is empty or whose target is occupied). */
 scale_status scale_commit(scale_ctx *ctx, const int32_t *moves);
 
+/* n_steps Metropolis steps of every loaded sample, drawing n from P(n) ~ |psi(n)|^2 by local
+ * updates (Sec. II.A; the optimisation settings use 2.5 N steps per sample). Step k of
+ * sample b proposes the hop of the pick[k][b]-th occupied orbital (ascending o = s*N + i,
+ * pick in [0, Ne)) one site along dir[k][b] (0 +x, 1 -x, 2 +y, 3 -y); a target past an open
+ * edge or already holding an electron of that spin (t-J: any electron) is rejected, else
+ * the move is accepted when u[k][b] < |psi(n')/psi(n)|^2, the square of the rank-r
+ * determinant against the cached inverse. An accepted move is committed as by
+ * scale_commit (Woodbury update, refresh schedule, drift check); a sample whose psi is
+ * zero accepts every proposal and is re-factorised. pick, dir: int32 [n_steps][B];
+ * u: float64 [n_steps][B] in [0, 1), all random numbers supplied by the caller;
+ * accepted: int32 [B], set to the number of accepted steps. Needs the SCALE layer layout
+ * (SCALE_EUNSUPPORTED otherwise). */
+scale_status scale_sweep(scale_ctx *ctx, int32_t n_steps, const int32_t *pick, const int32_t *dir,
+                         const double *u, int32_t *accepted);
+
 /* Re-factorise in FP64 every loaded sample (force_all = 1) or only the ones flagged by
  * the drift check or the commit counter (force_all = 0). */
 scale_status scale_refresh(scale_ctx *ctx, int32_t force_all);

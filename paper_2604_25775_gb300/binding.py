@@ -27,6 +27,7 @@ EXPORTED = [
     "scale_param_count", "scale_footprint_bytes", "scale_create", "scale_set_params", "scale_load",
     "scale_log_psi", "scale_get_occ", "scale_ratios", "scale_local_energy", "scale_commit",
     "scale_refresh", "scale_grad_logpsi", "scale_get_stats", "scale_last_error", "scale_destroy",
+    "scale_sweep",
 ]
 
 
@@ -87,7 +88,8 @@ def load_library(build: bool = True):
                                ("scale_local_energy", [V, ctypes.c_int32, V]), ("scale_commit", [V, V]),
                                ("scale_refresh", [V, ctypes.c_int32]),
                                ("scale_grad_logpsi", [V, V, ctypes.c_int32]),
-                               ("scale_get_stats", [V, P(scale_stats)])):
+                               ("scale_get_stats", [V, P(scale_stats)]),
+                               ("scale_sweep", [V, ctypes.c_int32, V, V, V, V])):
                 fn = getattr(lib, name)
                 fn.restype = ctypes.c_int
                 fn.argtypes = args
@@ -210,6 +212,15 @@ class Context:
         import torch
         self._check(self.lib.scale_commit(self.h, _ptr(moves, torch.int32, (self.B, 4), "moves")))
 
+    def scale_sweep(self, pick, direction, u, accepted):
+        """Metropolis steps: pick, direction int32 [S][B], u float64 [S][B], accepted int32 [B]."""
+        import torch
+        S = int(u.shape[0]) if u.dim() == 2 else 0
+        self._check(self.lib.scale_sweep(self.h, S, _ptr(pick, torch.int32, (S, self.B), "pick"),
+                                         _ptr(direction, torch.int32, (S, self.B), "direction"),
+                                         _ptr(u, torch.float64, (S, self.B), "u"),
+                                         _ptr(accepted, torch.int32, (self.B,), "accepted")))
+
     def scale_refresh(self, force_all=True):
         self._check(self.lib.scale_refresh(self.h, 1 if force_all else 0))
 
@@ -230,6 +241,13 @@ class Context:
         sg = torch.empty(self.B, dtype=torch.int32, device="cuda")
         self.scale_log_psi(la, sg)
         return la, sg
+
+    def sweep(self, pick, direction, u):
+        """Run the Metropolis steps; returns the number of accepted steps per sample."""
+        import torch
+        acc = torch.empty(self.B, dtype=torch.int32, device="cuda")
+        self.scale_sweep(pick, direction, u, acc)
+        return acc
 
     def local_energy(self, path=PATH_LOWRANK):
         import torch

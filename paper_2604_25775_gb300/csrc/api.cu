@@ -400,6 +400,21 @@ scale_status scale_commit(scale_ctx* c, const int32_t* moves) {
   return SCALE_OK;
 }
 
+scale_status scale_sweep(scale_ctx* c, int32_t n_steps, const int32_t* pick, const int32_t* dir, const double* u,
+                         int32_t* accepted) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  if (n_steps < 0 || (n_steps > 0 && (!pick || !dir || !u)) || !accepted) return SCALE_EINVAL;
+  if ((s = require_lowrank(c)) != SCALE_OK) return s;
+  SCALE_TRY(c, cudaMemsetAsync(accepted, 0, sizeof(int32_t) * (size_t)c->B, c->stream));
+  for (int32_t k = 0; k < n_steps; ++k) {
+    const size_t off = (size_t)k * c->B;
+    SCALE_TRY(c, launch_metropolis(c, pick + off, dir + off, u + off, accepted));
+    SCALE_TRY(c, refresh_samples(c, false));
+  }
+  return SCALE_OK;
+}
+
 scale_status scale_refresh(scale_ctx* c, int32_t force_all) {
   scale_status s = check_loaded(c);
   if (s != SCALE_OK) return s;

@@ -165,27 +165,71 @@ __device__ void move_features(const Lattice& lat, const Net<T>& net, int k0, con
   if (lane == 0) ms.nS = nS;
   __syncwarp();
   const int ts_src = net.per_site ? ms.src : 0, ts_dst = net.per_site ? ms.dst : 0;
-  // stage z0 and H(L) rows of S, add the layer-0 table deltas, activation + residual
+  // stage z0 and H(L) rows of S, add the layer-0 table deltas, activation + residual.
+  // Loads are issued kG at a time into registers before any is used (groups predicated on
+  // the actual counts): a handful of memory round trips instead of one per row, at a
+  // register cost the 128-register budget of a 16-warp CTA still holds.
+  constexpr int kG = 6;
   for (int c = lane; c < h; c += 32) {
-    for (int s = 0; s < nS; ++s) {
-      ms.feat[s][c] = sv.z0[(size_t)ms.site[s] * h + c];
-      ms.hl[s][c] = sv.HL[(size_t)ms.site[s] * h + c];
+    // (a) z0 and H(L) rows of S
+#pragma unroll 1
+    for (int s0 = 0; s0 < nS; s0 += kG) {
+      T z[kG], hv[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        const bool on = s0 + g < nS;
+        const int site = on ? ms.site[s0 + g] : 0;
+        z[g] = on ? sv.z0[(size_t)site * h + c] : T(0);
+        hv[g] = on ? sv.HL[(size_t)site * h + c] : T(0);
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g)
+        if (s0 + g < nS) {
+          ms.feat[s0 + g][c] = z[g];
+          ms.hl[s0 + g][c] = hv[g];
+        }
     }
-    for (int p = 0; p < npairs; ++p) {
-      const int s = ms.pair_s[p];
-      if (s < 0) continue;
-      const int d = p % kk;
-      const bool from_src = p < kk;
-      const int ts = from_src ? ts_src : ts_dst;
-      const int nn = from_src ? n_src_new : n_dst_new;
-      const int no = from_src ? n_src_old : n_dst_old;
-      ms.feat[s][c] += net.KE[(((size_t)ts * 4 + nn) * kk + d) * h + c] - net.KE[(((size_t)ts * 4 + no) * kk + d) * h + c];
+    // (b) layer-0 table deltas of the touched (site, offset) pairs
+#pragma unroll 1
+    for (int p0 = 0; p0 < npairs; p0 += kG) {
+      T kn[kG], ko[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        const int p = p0 + g;
+        kn[g] = ko[g] = T(0);
+        if (p < npairs && ms.pair_s[p] >= 0) {
+          const int d = p % kk;
+          const bool from_src = p < kk;
+          const int ts = from_src ? ts_src : ts_dst;
+          const int nn = from_src ? n_src_new : n_dst_new;
+          const int no = from_src ? n_src_old : n_dst_old;
+          kn[g] = net.KE[(((size_t)ts * 4 + nn) * kk + d) * h + c];
+          ko[g] = net.KE[(((size_t)ts * 4 + no) * kk + d) * h + c];
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        const int p = p0 + g;
+        if (p < npairs && ms.pair_s[p] >= 0) ms.feat[ms.pair_s[p]][c] += kn[g] - ko[g];
+      }
     }
-    for (int s = 0; s < nS; ++s) {
-      const int site = ms.site[s];
-      if (z0_new) z0_new[s][c] = ms.feat[s][c];
-      const T e = net.resid[0] ? net.embed[((size_t)(net.per_site ? site * 4 : 0) + ms.nnew[s]) * h + c] : T(0);
-      ms.feat[s][c] = e + act_fn<T>(net.act, ms.feat[s][c]);
+    // (c) activation + residual embedding
+#pragma unroll 1
+    for (int s0 = 0; s0 < nS; s0 += kG) {
+      T ev[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        const bool on = s0 + g < nS && net.resid[0];
+        const int site = on ? ms.site[s0 + g] : 0;
+        ev[g] = on ? net.embed[((size_t)(net.per_site ? site * 4 : 0) + ms.nnew[s0 + g]) * h + c] : T(0);
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g)
+        if (s0 + g < nS) {
+          const T zz = ms.feat[s0 + g][c];
+          if (z0_new) z0_new[s0 + g][c] = zz;
+          ms.feat[s0 + g][c] = ev[g] + act_fn<T>(net.act, zz);
+        }
     }
   }
   __syncwarp();
@@ -282,11 +326,13 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
       for (int u = 0; u < 16; ++u) pv[u] = (c0 + u < h) ? pt[c0 + u] : T(0);
       for (int a = a0; a < a1; ++a) {
         const T* row = (ms.moved[a] ? ms.feat[ms.sidx[a]] : ms.hl[ms.sidx[a]]) + c0;
-        T v = T(0);
+        T v0 = T(0), v1 = T(0);
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (c0 + u < h) v += row[u] * pv[u];
-        if (lane < r) ms.R[a][lane] += v;
+        for (int u = 0; u < 16; u += 2) {
+          if (c0 + u < h) v0 += row[u] * pv[u];
+          if (c0 + u + 1 < h) v1 += row[u + 1] * pv[u + 1];
+        }
+        if (lane < r) ms.R[a][lane] += v0 + v1;
       }
     }
   }
@@ -295,15 +341,26 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   for (int a = 0; a < r; ++a) {
     if (!ms.moved[a]) continue;
     const T* m0b = net.M0b + (size_t)ms.orb[a] * Ne;
+    constexpr int KK = 4;  // k values per lane held in registers per pass
     for (int b0 = 0; b0 < r; b0 += 4) {
       T g[4] = {T(0), T(0), T(0), T(0)};
       const T* br[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) br[q] = sv.Binv + (size_t)ms.slot[min(b0 + q, r - 1)] * Ne;
-      for (int k = lane; k < Ne; k += 32) {
-        const T v = m0b[k];
+      for (int k0 = 0; k0 < Ne; k0 += 32 * KK) {
+        T v[KK], bv[4][KK];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) g[q] += v * br[q][k];
+        for (int u = 0; u < KK; ++u) {
+          const int k = k0 + lane + 32 * u;
+          const bool on = k < Ne;
+          v[u] = on ? m0b[k] : T(0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) bv[q][u] = on ? br[q][k] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < KK; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) g[q] += v[u] * bv[q][u];
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -317,6 +374,33 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   return r;
 }
 
+// Pivot row of column k among rows [k, r) of R (lane i holds row i): the largest |R[i][k]|,
+// ties to the lowest row. Same value in every lane.
+template <typename T>
+__device__ __forceinline__ int warp_pivot(const T (*R)[kRMax + 1], int k, int r) {
+  const int lane = threadIdx.x & 31;
+  const bool mine = lane >= k && lane < r;
+  if constexpr (sizeof(T) == 4) {
+    // |x| of non-negative floats orders like its bit pattern: one warp max + ballot
+    const unsigned key = mine ? __float_as_uint(fabsf((float)R[lane][k])) : 0u;
+    const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+    return __ffs(__ballot_sync(0xffffffffu, mine && key == mx)) - 1;
+  } else {
+    T best = mine ? fabs(R[lane][k]) : T(-1);
+    int p = lane;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int op = __shfl_xor_sync(0xffffffffu, p, off);
+      if (ob > best || (ob == best && op < p)) {
+        best = ob;
+        p = op;
+      }
+    }
+    return p;
+  }
+}
+
 // Step 5: det of ms.R (r x r) by LU with partial pivoting, lane j owning column j; the
 // pivot search is a warp argmax over the rows, one reciprocal per column.
 // R is destroyed. Returns the determinant (same value in all lanes).
@@ -325,26 +409,7 @@ __device__ T warp_det(MoveScratch<T, H>& ms, int r) {
   const int lane = threadIdx.x & 31;
   T det = T(1);
   for (int k = 0; k < r; ++k) {
-    int p;
-    const bool mine = lane >= k && lane < r;
-    if constexpr (sizeof(T) == 4) {
-      // |x| of non-negative floats orders like its bit pattern: one warp max + ballot
-      const unsigned key = mine ? __float_as_uint(fabsf((float)ms.R[lane][k])) : 0u;
-      const unsigned mx = __reduce_max_sync(0xffffffffu, key);
-      p = __ffs(__ballot_sync(0xffffffffu, mine && key == mx)) - 1;
-    } else {
-      T best = mine ? fabs(ms.R[lane][k]) : T(-1);
-      p = lane;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const int op = __shfl_xor_sync(0xffffffffu, p, off);
-        if (ob > best || (ob == best && op < p)) {
-          best = ob;
-          p = op;
-        }
-      }
-    }
+    const int p = warp_pivot<T>(ms.R, k, r);
     if (p != k) {
       if (lane < r) {
         const T t = ms.R[k][lane];
