@@ -203,6 +203,8 @@ cudaError_t launch_logpsi_out(scale_ctx* c, double* logabs, int32_t* sign);
 cudaError_t launch_eloc_lowrank(scale_ctx* c, double* eloc);
 cudaError_t launch_ratios(scale_ctx* c, const int32_t* moves, int M, double* ratio);
 cudaError_t launch_commit(scale_ctx* c, const int32_t* moves);
+cudaError_t launch_metropolis(scale_ctx* c, const int32_t* pick, const int32_t* dir, const double* u,
+                              int32_t* accepted);
 cudaError_t launch_eloc_full(scale_ctx* c, double* eloc);
 cudaError_t launch_grad(scale_ctx* c, double* grad, int recompute);
 cudaError_t refresh_samples(scale_ctx* c, bool force_all);
