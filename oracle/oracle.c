@@ -40,7 +40,7 @@
 #define ORA_MAX_LAYERS 32
 
 typedef struct {
-  int32_t Lx, Ly, pbc_x, pbc_y, n_up, n_dn, model; /* model: 0 Hubbard, 1 t-J */
+  int32_t Lx, Ly, pbc_x, pbc_y, n_up, n_dn, model; /* model: 0 Hubbard, 1 t-J, 2 Hubbard after PHT */
   double t, tp, U, J;
   int32_t n_layers, h, act, per_site_embed; /* act: 0 tanh, 1 SiLU */
   int32_t ksize[ORA_MAX_LAYERS];
@@ -359,12 +359,19 @@ static void from_orbitals(int N, const int8_t *oo, int8_t *occ) {
 }
 
 /* Diagonal part: Hubbard U sum_i n_up n_dn; t-J J sum_<ij> Sz_i Sz_j (Eq. ham-tj carries
- * no -n_i n_j / 4 term). */
+ * no -n_i n_j / 4 term); the particle-hole transformed Hubbard model of the attractive-U
+ * benchmarks (App. "particle-hole transformation": c_dn -> (-1)^i c_dn^+, so n_dn -> 1 - n_dn)
+ * U sum_i n_up (1 - n_dn). */
 double ora_diag(const ora_model *m, const int8_t *occ) {
   const int N = m->Lx * m->Ly;
   if (m->model == 0) {
     int d = 0;
     for (int i = 0; i < N; ++i) d += (occ[i] == 3);
+    return m->U * d;
+  }
+  if (m->model == 2) {
+    int d = 0;
+    for (int i = 0; i < N; ++i) d += (occ[i] & 1) * (1 - ((occ[i] >> 1) & 1));
     return m->U * d;
   }
   int32_t *pr = (int32_t *)malloc(sizeof(int32_t) * 4 * N);

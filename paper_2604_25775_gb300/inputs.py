@@ -27,6 +27,7 @@ import numpy as np
 
 MODEL_HUBBARD = 0
 MODEL_TJ = 1
+MODEL_HUBBARD_PH = 2  # Hubbard after the particle-hole transformation of the down spins
 ACT_TANH = 0
 ACT_SILU = 1
 PREC_FP64 = 0
@@ -297,6 +298,10 @@ def workload(name: str) -> Problem:
         ks, rs = scale_layout(4)
         return Problem(8, 8, 1, 1, 28, 28, MODEL_TJ, 1.0, 0.0, 0.0, 0.4, 4, 16, ks, rs,
                        ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+    if name == "hubbard_ph8x8":  # attractive U=-4 at 28+28, after the particle-hole transformation: 28 + (64-28)
+        ks, rs = scale_layout(4)
+        return Problem(8, 8, 1, 1, 28, 36, MODEL_HUBBARD_PH, 1.0, 0.0, -4.0, 0.0, 4, 16, ks, rs,
+                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
     if name == "tj16x16":
         ks, rs = scale_layout(6)
         return Problem(16, 16, 1, 1, 112, 112, MODEL_TJ, 1.0, 0.0, 0.0, 0.4, 6, 32, ks, rs,
@@ -313,7 +318,8 @@ def workload(name: str) -> Problem:
 
 
 WORKLOAD_INDEX = {"hubbard4x4": 0, "hubbard8x8": 1, "hubbard16x16": 2, "cylinder16x4": 3,
-                  "tj8x8": 4, "tj16x16": 4, "hubbard32x32": 4, "tj32x32": 4}
+                  "tj8x8": 4, "tj16x16": 4, "hubbard32x32": 4, "tj32x32": 4,
+                  "hubbard_ph8x8": 5}
 
 
 def workload_seeds(name: str):

@@ -88,6 +88,8 @@ def dense_h(d):
         dn = [(s >> (N + i)) & 1 for i in range(N)]
         if d["model"] == 0:
             H[k, k] += d["U"] * sum(u * v for u, v in zip(up, dn))
+        elif d["model"] == 2:  # particle-hole transformed Hubbard: n_dn -> 1 - n_dn
+            H[k, k] += d["U"] * sum(u * (1 - v) for u, v in zip(up, dn))
         else:
             for i, j in nn:
                 H[k, k] += d["J"] * 0.25 * (up[i] - dn[i]) * (up[j] - dn[j])

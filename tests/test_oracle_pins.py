@@ -157,6 +157,7 @@ TINY = [
     I.Problem(3, 2, 1, 0, 2, 1, I.MODEL_HUBBARD, 1.0, -0.3, 6.0, 0.0, 2, 3, [3, 1], [1, 0], I.ACT_SILU),
     I.Problem(3, 3, 1, 1, 2, 2, I.MODEL_TJ, 1.0, 0.0, 0.0, 0.4, 2, 4, [3, 1], [1, 0]),
     I.Problem(4, 2, 0, 0, 2, 2, I.MODEL_TJ, 1.0, 0.2, 0.0, 1.0 / 3.0, 3, 3, [3, 3, 1], [1, 1, 0]),
+    I.Problem(3, 2, 0, 0, 2, 4, I.MODEL_HUBBARD_PH, 1.0, 0.0, -4.0, 0.0, 2, 4, [3, 1], [1, 0]),
 ]
 
 
@@ -175,6 +176,23 @@ def test_enumeration_matches_dense_hamiltonian(k):
     E_dense = psi @ H @ psi / (psi @ psi)
     assert abs(E - E_dense) <= 1e-10 * max(1.0, abs(E_dense))
     assert E >= np.linalg.eigvalsh(H)[0] - 1e-10
+
+
+@pytest.mark.parametrize("Lx,Ly,n_up,n_dn", [(3, 2, 2, 2), (4, 2, 2, 3), (4, 2, 3, 3)])
+def test_particle_hole_transformation_spectrum(Lx, Ly, n_up, n_dn):
+    """App. "particle-hole transformation": c_dn -> (-1)^i c_dn^+ maps the attractive Hubbard
+    model with (n_up, n_dn) onto -t sum hops + U sum n_up (1 - n_dn) with (n_up, N - n_dn) on a
+    bipartite lattice, a unitary map: the two dense Hamiltonians (the PH diagonal written
+    independently in the dense builder) have the same spectrum."""
+    U = -4.0
+    base = dict(Lx=Lx, Ly=Ly, pbc_x=0, pbc_y=0, t=1.0, tp=0.0, U=U, J=0.0)
+    H_attr, _ = dense_h(dict(base, n_up=n_up, n_dn=n_dn, model=I.MODEL_HUBBARD))
+    H_ph, _ = dense_h(dict(base, n_up=n_up, n_dn=Lx * Ly - n_dn, model=I.MODEL_HUBBARD_PH))
+    assert H_attr.shape == H_ph.shape
+    np.testing.assert_allclose(np.linalg.eigvalsh(H_ph), np.linalg.eigvalsh(H_attr), atol=1e-10)
+    # and the transformed model is not trivially the repulsive one
+    H_rep, _ = dense_h(dict(base, n_up=n_up, n_dn=Lx * Ly - n_dn, model=I.MODEL_HUBBARD))
+    assert abs(np.linalg.eigvalsh(H_rep)[0] - np.linalg.eigvalsh(H_ph)[0]) > 0.1
 
 
 def test_dense_builder_two_site_closed_form():
