@@ -55,6 +55,37 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM traffic of the local-energy kernel per walker, from the ncu capture summarised in
+# this file; used only while the kernel sources still hash to the value recorded there.
+ELOC_PROFILE = os.path.join(ROOT, "profiles", "k_eloc_hubbard16x16.md")
+ELOC_SOURCES = ["lowrank.cu", "move.cuh", "mlp_mma.cuh", "scale_internal.cuh"]
+
+
+def eloc_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in ELOC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_25775_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic_per_walker():
+    """(bytes per walker, note) from the profile summary, or (None, reason)."""
+    try:
+        fields = {}
+        with open(ELOC_PROFILE) as f:
+            for line in f:
+                if ":" in line and line.split(":", 1)[0].strip() in ("dram_bytes_per_walker", "sources_sha256"):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        if fields.get("sources_sha256") != eloc_sources_sha256():
+            return None, "kernel sources changed since the capture"
+        return float(fields["dram_bytes_per_walker"]), "ncu capture at 512 walkers, scaled per walker"
+    except (OSError, KeyError, ValueError):
+        return None, "no capture summary"
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -327,9 +358,11 @@ def main():
     if rank == 0 and not args.no_extras:
         flops = lowrank_flops_per_sample(pb, occ)
         achieved = flops * B / (eloc_ms / 1e3) / 1e12
+        tpw, tnote = profiled_traffic_per_walker()
         line["roofline"] = {"kernel": "k_eloc (low-rank E_loc)", "bound": "alu", "achieved": achieved,
                             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                            "traffic": None, "flops_per_walker": flops,
+                            "traffic": None if tpw is None else tpw * B, "traffic_note": tnote,
+                            "flops_per_walker": flops,
                             "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived)"}
         # cold path: load (forward, FP64 Gauss-Jordan inverse, projector) + E_loc
         ctx2 = Bd.make_context(pb, params, M0, B)

@@ -64,7 +64,13 @@ typedef enum {
   SCALE_EUNSUPPORTED = 6  /* valid but not supported by this build (see text) */
 } scale_status;
 
-enum { SCALE_MODEL_HUBBARD = 0, SCALE_MODEL_TJ = 1 };
+/* SCALE_MODEL_HUBBARD_PH: the Hubbard model after the particle-hole transformation of the
+ * down spins used for the attractive-U benchmarks (App. "particle-hole transformation",
+ * c_dn -> (-1)^i c_dn^+): the same nearest-neighbour hopping and the diagonal
+ * U sum_i n_up (1 - n_dn); n_dn counts the transformed down particles (N minus the down
+ * electrons of the attractive model). The transformation keeps the hopping form only for
+ * nearest-neighbour bonds, so t' must be 0. */
+enum { SCALE_MODEL_HUBBARD = 0, SCALE_MODEL_TJ = 1, SCALE_MODEL_HUBBARD_PH = 2 };
 enum { SCALE_ACT_TANH = 0, SCALE_ACT_SILU = 1 };
 enum { SCALE_PREC_FP64 = 0, SCALE_PREC_MIXED = 1, SCALE_PREC_MIXED_BF16 = 2 };
 enum { SCALE_PATH_LOWRANK = 0, SCALE_PATH_FULL = 1 };

@@ -33,7 +33,11 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
   if (N > 4096) return fail("at most 4096 sites");
   if (s->n_up < 0 || s->n_dn < 0 || s->n_up > N || s->n_dn > N || s->n_up + s->n_dn < 1)
     return fail("particle numbers out of range");
-  if (s->model != SCALE_MODEL_HUBBARD && s->model != SCALE_MODEL_TJ) return fail("unknown model");
+  if (s->model != SCALE_MODEL_HUBBARD && s->model != SCALE_MODEL_TJ && s->model != SCALE_MODEL_HUBBARD_PH)
+    return fail("unknown model");
+  if (s->model == SCALE_MODEL_HUBBARD_PH && s->tp != 0.0)
+    return fail("particle-hole transformed model: t' must be 0 (the transformation keeps the hopping form "
+                "on nearest-neighbour bonds only)");
   if (s->model == SCALE_MODEL_TJ && s->n_up + s->n_dn > N) return fail("t-J: more electrons than sites");
   if (a->n_layers < 1 || a->n_layers > SCALE_MAX_LAYERS) return fail("n_layers must be in [1, 32]");
   if (a->h < 1 || a->h > kMaxH) return fail("h must be in [1, 64]");

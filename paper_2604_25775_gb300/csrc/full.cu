@@ -46,6 +46,10 @@ __global__ void k_enum(Lattice lat, const int8_t* __restrict__ occ, const int32_
     int nd = 0;
     for (int i = 0; i < N; ++i) nd += x[i] == 3;
     d = lat.U * nd;
+  } else if (lat.model == SCALE_MODEL_HUBBARD_PH) {
+    int nu = 0;  // U sum_i n_up (1 - n_dn)
+    for (int i = 0; i < N; ++i) nu += x[i] == 1;
+    d = lat.U * nu;
   } else {
     for (int q = 0; q < nb_nn; ++q) {
       const int i = bonds[2 * q], j = bonds[2 * q + 1];

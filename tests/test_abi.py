@@ -42,6 +42,8 @@ def test_invalid_descriptors_rejected_on_host():
         I.workload("hubbard4x4").replace(n_up=17),       # more electrons than sites
         I.workload("tj8x8").replace(n_up=40, n_dn=40),   # t-J overfilled
         I.workload("hubbard4x4").replace(refresh_every=0),
+        I.workload("hubbard_ph8x8").replace(tp=-0.2),    # PHT keeps its form on NN bonds only
+        I.workload("hubbard4x4").replace(model=3),       # unknown model
     ]
     for pb in bad:
         assert Bd.scale_param_count(pb) == -1

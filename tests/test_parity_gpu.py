@@ -87,7 +87,7 @@ def test_lowrank_equals_full_fp64(fp64_4x4):
     assert rel_err(e1[good], e2[good]).max() <= FP64_TOL
 
 
-@pytest.mark.parametrize("variant", ["tp", "tj", "tj_tp", "open_silu", "shared_embed"])
+@pytest.mark.parametrize("variant", ["tp", "tj", "tj_tp", "open_silu", "shared_embed", "ph"])
 def test_local_energy_variants_fp64(variant):
     """Hamiltonian and network variants at FP64: NNN hopping, t-J exchange and projection,
     open boundaries with SiLU, a shared embedding table."""
@@ -99,6 +99,7 @@ def test_local_energy_variants_fp64(variant):
         "tj_tp": base.replace(model=I.MODEL_TJ, U=0.0, J=1 / 3, tp=0.2, pbc_y=0),
         "open_silu": base.replace(pbc_x=0, pbc_y=0, act=I.ACT_SILU, tp=0.1),
         "shared_embed": base.replace(per_site_embed=0, tp=-0.1),
+        "ph": base.replace(model=I.MODEL_HUBBARD_PH, U=-4.0, n_dn=30 - 8),
     }[variant]
     ctx, ora, occ, st, = setup(pb, 48, 31, 41, scale=0.2)
     cond = conditioning(ora, occ)
@@ -133,7 +134,7 @@ def test_ratios_fp64():
     assert (rb[:, 0] == 0).all() and (rb[:, 1] == 1).all()
 
 
-@pytest.mark.parametrize("name", ["hubbard8x8", "tj8x8"])
+@pytest.mark.parametrize("name", ["hubbard8x8", "tj8x8", "hubbard_ph8x8"])
 def test_local_energy_mixed_8x8(name):
     pb = I.workload(name)
     ctx, ora, occ, st = setup(pb, 256, 1235, 5679)
