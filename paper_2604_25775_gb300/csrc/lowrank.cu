@@ -12,7 +12,8 @@
 //           permutation sign of the ascending convention cancel),
 //   exchange (J/2)(S+_i S-_j + h.c.) = -(J/2) (c+_{i up} c_{j up})(c+_{j dn} c_{i dn}):
 //           -J/2 times det R.
-// Diagonal: Hubbard U * (doubly occupied sites); t-J J sum_<ij> Sz_i Sz_j.
+// Diagonal: Hubbard U * (doubly occupied sites); t-J J sum_<ij> Sz_i Sz_j; the
+// particle-hole transformed Hubbard model U sum_i n_up (1 - n_dn).
 #include <algorithm>
 
 #include "move.cuh"
@@ -114,6 +115,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net, 
       int nd = 0;
       for (int i = 0; i < N; ++i) nd += occ_s[i] == 3;
       d = a.lat.U * nd;
+    } else if (a.lat.model == SCALE_MODEL_HUBBARD_PH) {
+      int nu = 0;  // sites with an up particle and no (transformed) down particle
+      for (int i = 0; i < N; ++i) nu += occ_s[i] == 1;
+      d = a.lat.U * nu;
     } else {
       for (int q = 0; q < a.nb_nn; ++q) {
         const int i = a.bonds[2 * q], j = a.bonds[2 * q + 1];
