@@ -48,8 +48,9 @@ struct LowrankArgs {
   const int32_t* list;   // optional: CTA i handles sample list[i]
 };
 
-// Candidate id -> move (kind -1 when not allowed in the current configuration).
-__device__ __forceinline__ MoveDesc candidate(const LowrankArgs& a, const int8_t* occ, int id, double* coeff) {
+// Candidate id -> move (kind -1 when not allowed in the current configuration) and its
+// coefficient class: 0 NN hop (-t), 1 NNN hop (-t'), 2 exchange (-J/2).
+__device__ __forceinline__ MoveDesc candidate(const LowrankArgs& a, const int8_t* occ, int id, int* cls) {
   MoveDesc m{-1, 0, 0, 0};
   const int nb = a.nb_nn + a.nb_nnn;
   if (id < 2 * nb) {
@@ -64,7 +65,7 @@ __device__ __forceinline__ MoveDesc candidate(const LowrankArgs& a, const int8_t
     m.src = src;
     m.dst = dst;
     m.spin = s;
-    *coeff = (q < a.nb_nn) ? -a.lat.t : -a.lat.tp;
+    *cls = (q < a.nb_nn) ? 0 : 1;
     return m;
   }
   const int q = id - 2 * nb;
@@ -75,9 +76,17 @@ __device__ __forceinline__ MoveDesc candidate(const LowrankArgs& a, const int8_t
     m.src = i;
     m.dst = j;
     m.spin = 0;
-    *coeff = -0.5 * a.lat.J;
+    *cls = 2;
   }
   return m;
+}
+
+// Moves of one chunk are kept packed in shared memory: bits 0-11 src, 12-23 dst (N <= 4096),
+// 24 spin, 25 kind, 26-27 coefficient class.
+constexpr int kMoveChunk = 1024;
+__device__ __forceinline__ uint32_t pack_move(const MoveDesc& m, int cls) {
+  return (uint32_t)m.src | ((uint32_t)m.dst << 12) | ((uint32_t)m.spin << 24) | ((uint32_t)m.kind << 25) |
+         ((uint32_t)cls << 26);
 }
 
 // WARPS warps per sample; with stage_pt the sample's projector rows (2 x Ne x h) are copied
@@ -88,13 +97,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net, 
   const int N = a.lat.N, Ne = a.lat.Ne, h = net.h;
   MoveScratch<T, H>* ms_all = reinterpret_cast<MoveScratch<T, H>*>(smem);
   T* pt_s = reinterpret_cast<T*>(ms_all + WARPS);                  // [2][Ne][h] when staged
-  MoveDesc* moves = reinterpret_cast<MoveDesc*>(pt_s + (stage_pt ? (size_t)2 * Ne * h : 0));
-  double* contrib = reinterpret_cast<double*>(moves + WARPS * 32);
-  double* coeffs = contrib + WARPS * 32;
-  int32_t* slot_s = reinterpret_cast<int32_t*>(coeffs + WARPS * 32);
+  uint32_t* mlist = reinterpret_cast<uint32_t*>(pt_s + (stage_pt ? (size_t)2 * Ne * h : 0));  // [kMoveChunk]
+  double* contrib = reinterpret_cast<double*>(mlist + kMoveChunk);   // [kMoveChunk]
+  int32_t* slot_s = reinterpret_cast<int32_t*>(contrib + kMoveChunk);
   int8_t* occ_s = reinterpret_cast<int8_t*>(slot_s + 2 * N);
   __shared__ int warp_cnt[WARPS];
   __shared__ double s_diag;
+  __shared__ int s_next;
 
   const int b = a.list ? a.list[blockIdx.x] : blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -148,44 +157,66 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net, 
   const int ncand = 2 * nb + ((a.lat.model == SCALE_MODEL_TJ && a.lat.J != 0.0) ? a.nb_nn : 0);
   double total = 0.0;  // thread 0
   int nmoves = 0;
-  for (int cs = 0; cs < ncand; cs += WARPS * 32) {
-    const int id = cs + tid;
-    double cf = 0.0;
-    MoveDesc m{-1, 0, 0, 0};
-    if (id < ncand) m = candidate(a, occ_s, id, &cf);
-    const bool valid = m.kind >= 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, valid);
-    if (lane == 0) warp_cnt[warp] = __popc(bal);
-    __syncthreads();
-    int off = 0, nm = 0;
-    for (int w = 0; w < WARPS; ++w) {
-      if (w < warp) off += warp_cnt[w];
-      nm += warp_cnt[w];
+  for (int cs = 0; cs < ncand; cs += kMoveChunk) {
+    const int ce = min(ncand, cs + kMoveChunk);
+    // enumerate and compact the allowed moves of this chunk (enumeration order)
+    int nm = 0;
+    for (int sub = cs; sub < ce; sub += WARPS * 32) {
+      const int id = sub + tid;
+      int cls = 0;
+      MoveDesc m{-1, 0, 0, 0};
+      if (id < ce) m = candidate(a, occ_s, id, &cls);
+      const bool valid = m.kind >= 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, valid);
+      if (lane == 0) warp_cnt[warp] = __popc(bal);
+      __syncthreads();
+      int off = 0, tot = 0;
+      for (int w = 0; w < WARPS; ++w) {
+        if (w < warp) off += warp_cnt[w];
+        tot += warp_cnt[w];
+      }
+      if (valid) mlist[nm + off + __popc(bal & ((1u << lane) - 1u))] = pack_move(m, cls);
+      nm += tot;
+      __syncthreads();
     }
-    if (valid) {
-      const int pos = off + __popc(bal & ((1u << lane) - 1u));
-      moves[pos] = m;
-      coeffs[pos] = cf;
-    }
+    if (tid == 0) s_next = 0;
     __syncthreads();
-    for (int mi = warp; mi < nm; mi += WARPS) {
+    // warps take the next move as they finish the previous one
+    for (;;) {
+      int mi = 0;
+      if (lane == 0) mi = atomicAdd(&s_next, 1);
+      mi = __shfl_sync(0xffffffffu, mi, 0);
+      if (mi >= nm) break;
+      const uint32_t pm = mlist[mi];
       if (lane == 0) {
-        ms.kind = moves[mi].kind;
-        ms.src = moves[mi].src;
-        ms.dst = moves[mi].dst;
-        ms.spin = moves[mi].spin;
+        ms.src = (int)(pm & 0xfffu);
+        ms.dst = (int)((pm >> 12) & 0xfffu);
+        ms.spin = (int)((pm >> 24) & 1u);
+        ms.kind = (int)((pm >> 25) & 1u);
       }
       __syncwarp();
       move_features<T, H>(a.lat, net, a.k0, sv, a.mf, ms);
       const int r = move_matrix<T, H>(a.lat, net, sv, ms);
       const T det = (r < 0) ? T(CUDART_NAN) : warp_det<T, H>(ms, r);
-      if (lane == 0) contrib[mi] = coeffs[mi] * (double)det;
+      if (lane == 0) {
+        const uint32_t cls = (pm >> 26) & 3u;
+        const double cf = cls == 0 ? -a.lat.t : (cls == 1 ? -a.lat.tp : -0.5 * a.lat.J);
+        contrib[mi] = cf * (double)det;
+      }
       __syncwarp();
     }
     __syncthreads();
-    if (tid == 0) {
-      for (int q = 0; q < nm; ++q) total += contrib[q];
-      nmoves += nm;
+    // fixed-order sum of the chunk: lane l adds contributions l, l+32, ..., then an xor tree
+    // (both orders independent of which warp evaluated which move)
+    if (warp == 0) {
+      double s = 0.0;
+      for (int q = lane; q < nm; q += 32) s += contrib[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) {
+        total += s;
+        nmoves += nm;
+      }
     }
     __syncthreads();
   }
@@ -310,7 +341,7 @@ __global__ void __launch_bounds__(256) k_project(int Ne, int h, const T* __restr
 template <typename T, int H, int WARPS>
 size_t eloc_smem(int N, int Ne, int h, bool stage_pt) {
   return sizeof(MoveScratch<T, H>) * WARPS + (stage_pt ? sizeof(T) * 2 * Ne * h : 0) +
-         (sizeof(MoveDesc) + sizeof(double) * 2) * WARPS * 32 + sizeof(int32_t) * 2 * N + N + 16;
+         (sizeof(uint32_t) + sizeof(double)) * kMoveChunk + sizeof(int32_t) * 2 * N + N + 16;
 }
 
 template <typename T, int H>

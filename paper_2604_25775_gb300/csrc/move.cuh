@@ -313,6 +313,27 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   // Pt terms, column b = lane: the Pt[spin][c_b] row in registers (16 channels at a time),
   // each electron of that spin dotted against its feature row (H' if it moved, Delta H if
   // not); identity for the electrons that kept their orbital
+  if constexpr (H <= 32) {
+    // the whole Pt row of the lane's column in registers; every row of R written once
+    for (int sp = 0; sp < 2; ++sp) {
+      const int a0 = sp ? r_up : 0, a1 = sp ? r : r_up;
+      if (a0 == a1) continue;
+      const T* pt = sv.Pt + ((size_t)sp * Ne + cb) * h;
+      T pv[H];
+#pragma unroll
+      for (int u = 0; u < H; ++u) pv[u] = (u < h) ? pt[u] : T(0);
+      for (int a = a0; a < a1; ++a) {
+        const T* row = ms.moved[a] ? ms.feat[ms.sidx[a]] : ms.hl[ms.sidx[a]];
+        T v[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int u = 0; u < H; ++u)
+          if (u < h) v[u & 3] += row[u] * pv[u];
+        const T init = (!ms.moved[a] && a == lane) ? T(1) : T(0);
+        if (lane < r) ms.R[a][lane] = init + ((v[0] + v[1]) + (v[2] + v[3]));
+      }
+    }
+    __syncwarp();
+  } else {
   if (lane < r)
     for (int a = 0; a < r; ++a) ms.R[a][lane] = (!ms.moved[a] && a == lane) ? T(1) : T(0);
   __syncwarp();
@@ -337,6 +358,7 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
     }
   }
   __syncwarp();
+  }
   // moved rows: + (M0[o'] + proj_b[s]) . Binv[c_b], lanes split k, one warp reduction per b
   for (int a = 0; a < r; ++a) {
     if (!ms.moved[a]) continue;
