@@ -198,8 +198,10 @@ scale_status scale_commit(scale_ctx *ctx, const int32_t *moves);
  * edge or already holding an electron of that spin (t-J: any electron) is rejected, else
  * the move is accepted when u[k][b] < |psi(n')/psi(n)|^2, the square of the rank-r
  * determinant against the cached inverse. An accepted move is committed as by
- * scale_commit (Woodbury update, refresh schedule, drift check); a sample whose psi is
- * zero accepts every proposal and is re-factorised. pick, dir: int32 [n_steps][B];
+ * scale_commit (Woodbury update, drift check); a sample whose psi is zero accepts every
+ * proposal and is re-factorised. Samples whose commit counter reaches refresh_every are
+ * re-factorised in FP64 at the next multiple of 8 steps and at the end of the call (drift-
+ * flagged ones after the step that flagged them). pick, dir: int32 [n_steps][B];
  * u: float64 [n_steps][B] in [0, 1), all random numbers supplied by the caller;
  * accepted: int32 [B], set to the number of accepted steps. Needs the SCALE layer layout
  * (SCALE_EUNSUPPORTED otherwise). */

@@ -180,9 +180,9 @@ namespace scale {
 
 // FP64 re-factorisation of the samples selected by the commit counter / drift flag (or
 // all of them): network forward, ascending slot maps, Phi, Gauss-Jordan inverse, projector.
-cudaError_t refresh_samples(scale_ctx* c, bool force_all) {
+cudaError_t refresh_samples(scale_ctx* c, bool force_all, bool counters_due) {
   cudaError_t e;
-  if ((e = launch_mark_refresh(c, force_all)) != cudaSuccess) return e;
+  if ((e = launch_mark_refresh(c, force_all, counters_due)) != cudaSuccess) return e;
   if ((e = launch_forward(c, c->occ, c->B, c->list, true, c->Phi64)) != cudaSuccess) return e;
   if ((e = launch_slots_list(c, c->list, c->B)) != cudaSuccess) return e;
   if ((e = launch_gj(c, c->Phi64, c->Ne, c->B, c->list, true, c->fp64, c->Binv, c->logabs, c->sign_slot,
@@ -411,10 +411,17 @@ scale_status scale_sweep(scale_ctx* c, int32_t n_steps, const int32_t* pick, con
   if (n_steps < 0 || (n_steps > 0 && (!pick || !dir || !u)) || !accepted) return SCALE_EINVAL;
   if ((s = require_lowrank(c)) != SCALE_OK) return s;
   SCALE_TRY(c, cudaMemsetAsync(accepted, 0, sizeof(int32_t) * (size_t)c->B, c->stream));
+  // Samples whose drift check fired, or whose step fell back to the occupations alone, are
+  // re-factorised after the step that flagged them. Samples whose commit counter came due
+  // wait for the next multiple of kSweepRefreshStride steps (and the end of the call), so
+  // the FP64 refreshes of a sweep run as a few full launches instead of one thin launch
+  // per step: one 224 x 224 FP64 inverse occupies an SM for milliseconds.
+  constexpr int32_t kSweepRefreshStride = 8;
   for (int32_t k = 0; k < n_steps; ++k) {
     const size_t off = (size_t)k * c->B;
     SCALE_TRY(c, launch_metropolis(c, pick + off, dir + off, u + off, accepted));
-    SCALE_TRY(c, refresh_samples(c, false));
+    const bool due = (k % kSweepRefreshStride) == kSweepRefreshStride - 1 || k == n_steps - 1;
+    SCALE_TRY(c, refresh_samples(c, false, due));
   }
   return SCALE_OK;
 }

@@ -675,16 +675,19 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
   }
 }
 
-// list[b] = b when sample b needs an FP64 re-factorisation, else -1.
-__global__ void k_mark_refresh(int B, int refresh_every, bool force_all, const int32_t* __restrict__ commits,
-                               const int32_t* __restrict__ status, int32_t* __restrict__ list,
-                               int32_t* __restrict__ n_refresh, int32_t* __restrict__ n_drift) {
+// list[b] = b when sample b needs an FP64 re-factorisation, else -1: all samples
+// (force_all), a sample whose drift check fired or whose Woodbury step was skipped, and
+// (when counters_due) a sample whose commit counter reached refresh_every.
+__global__ void k_mark_refresh(int B, int refresh_every, bool force_all, bool counters_due,
+                               const int32_t* __restrict__ commits, const int32_t* __restrict__ status,
+                               int32_t* __restrict__ list, int32_t* __restrict__ n_refresh,
+                               int32_t* __restrict__ n_drift) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const int st = status[b];
   const bool bad = st & (SCALE_SAMPLE_BAD_COUNT | SCALE_SAMPLE_DOUBLE_OCC);
   const bool drift = st & SCALE_SAMPLE_DRIFT;
-  const bool need = !bad && (force_all || drift || commits[b] >= refresh_every);
+  const bool need = !bad && (force_all || drift || (counters_due && commits[b] >= refresh_every));
   list[b] = need ? b : -1;
   if (need) {
     atomicAdd(n_refresh, 1);
@@ -757,10 +760,11 @@ cudaError_t launch_metropolis(scale_ctx* c, const int32_t* pick, const int32_t* 
   return commit_dispatch(c, nullptr, pick, dir, u, accepted);
 }
 
-cudaError_t launch_mark_refresh(scale_ctx* c, bool force_all) {
+cudaError_t launch_mark_refresh(scale_ctx* c, bool force_all, bool counters_due) {
   int32_t* counters = reinterpret_cast<int32_t*>(c->stat_dev + 1);
-  k_mark_refresh<<<(c->B + 255) / 256, 256, 0, c->stream>>>(c->B, c->arch.refresh_every, force_all, c->commits,
-                                                            c->status, c->list, counters + 1, counters + 2);
+  k_mark_refresh<<<(c->B + 255) / 256, 256, 0, c->stream>>>(c->B, c->arch.refresh_every, force_all, counters_due,
+                                                            c->commits, c->status, c->list, counters + 1,
+                                                            counters + 2);
   return cudaGetLastError();
 }
 

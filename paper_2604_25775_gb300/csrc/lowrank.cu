@@ -89,15 +89,14 @@ __device__ __forceinline__ uint32_t pack_move(const MoveDesc& m, int cls) {
          ((uint32_t)cls << 26);
 }
 
-// WARPS warps per sample; with stage_pt the sample's projector rows (2 x Ne x h) are copied
-// to shared memory once and every move reads them from there.
+// WARPS warps per sample; the sample's cached rows (Binv, Pt, z0, H(L)) are read through
+// L1/L2, shared memory holds the per-warp move scratch and the move list.
 template <typename T, int H, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net, int stage_pt) {
+__global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.lat.N, Ne = a.lat.Ne, h = net.h;
   MoveScratch<T, H>* ms_all = reinterpret_cast<MoveScratch<T, H>*>(smem);
-  T* pt_s = reinterpret_cast<T*>(ms_all + WARPS);                  // [2][Ne][h] when staged
-  uint32_t* mlist = reinterpret_cast<uint32_t*>(pt_s + (stage_pt ? (size_t)2 * Ne * h : 0));  // [kMoveChunk]
+  uint32_t* mlist = reinterpret_cast<uint32_t*>(ms_all + WARPS);     // [kMoveChunk]
   double* contrib = reinterpret_cast<double*>(mlist + kMoveChunk);   // [kMoveChunk]
   int32_t* slot_s = reinterpret_cast<int32_t*>(contrib + kMoveChunk);
   int8_t* occ_s = reinterpret_cast<int8_t*>(slot_s + 2 * N);
@@ -145,12 +144,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net, 
   sv.HL = (const T*)a.HL + (size_t)b * N * h;
   sv.Binv = (const T*)a.Binv + (size_t)b * Ne * Ne;
   sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
-  if (stage_pt) {
-    const T* src = sv.Pt;
-    for (int q = tid; q < 2 * Ne * h; q += blockDim.x) pt_s[q] = src[q];
-    sv.Pt = pt_s;
-    __syncthreads();
-  }
   MoveScratch<T, H>& ms = ms_all[warp];
 
   const int nb = a.nb_nn + a.nb_nnn;
@@ -339,9 +332,9 @@ __global__ void __launch_bounds__(256) k_project(int Ne, int h, const T* __restr
 }
 
 template <typename T, int H, int WARPS>
-size_t eloc_smem(int N, int Ne, int h, bool stage_pt) {
-  return sizeof(MoveScratch<T, H>) * WARPS + (stage_pt ? sizeof(T) * 2 * Ne * h : 0) +
-         (sizeof(uint32_t) + sizeof(double)) * kMoveChunk + sizeof(int32_t) * 2 * N + N + 16;
+size_t eloc_smem(int N) {
+  return sizeof(MoveScratch<T, H>) * WARPS + (sizeof(uint32_t) + sizeof(double)) * kMoveChunk +
+         sizeof(int32_t) * 2 * N + N + 16;
 }
 
 template <typename T, int H>
@@ -369,16 +362,18 @@ LowrankArgs make_args(scale_ctx* c) {
 }
 
 template <typename T, int H, int WARPS>
-cudaError_t eloc_launch(scale_ctx* c, const LowrankArgs& a, int n, bool stage) {
-  const size_t smem = eloc_smem<T, H, WARPS>(c->N, c->Ne, c->h, stage);
+cudaError_t eloc_launch(scale_ctx* c, const LowrankArgs& a, int n) {
+  const size_t smem = eloc_smem<T, H, WARPS>(c->N);
   cudaError_t e = cudaFuncSetAttribute(k_eloc<T, H, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_eloc<T, H, WARPS><<<n, WARPS * 32, smem, c->stream>>>(a, make_net<T>(c), stage ? 1 : 0);
+  k_eloc<T, H, WARPS><<<n, WARPS * 32, smem, c->stream>>>(a, make_net<T>(c));
   return cudaGetLastError();
 }
 
-// Launch shape: 16 warps with the projector staged in shared memory when it fits (one CTA
-// per SM, 512 threads), otherwise 8 warps reading the projector through L1.
+// Launch shape: the most warps per CTA (one CTA per SM) whose move scratch fits, up to 20.
+// Measured at 16x16, 8192 walkers: 20 warps 65.7 ms, 22 warps 68.8 ms (too little L1 left
+// for the cached rows), 16 warps 77.7 ms, 12 warps 88.0 ms; staging the projector in shared
+// memory instead (16 warps) took 80.1 ms.
 template <typename T, int H>
 cudaError_t eloc_t(scale_ctx* c, double* eloc, const int32_t* list, int n) {
   LowrankArgs a = make_args(c);
@@ -388,9 +383,10 @@ cudaError_t eloc_t(scale_ctx* c, double* eloc, const int32_t* list, int n) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (sizeof(T) == 4 && eloc_smem<T, H, 16>(c->N, c->Ne, c->h, true) <= (size_t)optin)
-    return eloc_launch<T, H, 16>(c, a, n, true);
-  return eloc_launch<T, H, 8>(c, a, n, false);
+  if (eloc_smem<T, H, 20>(c->N) <= (size_t)optin) return eloc_launch<T, H, 20>(c, a, n);
+  if (eloc_smem<T, H, 16>(c->N) <= (size_t)optin) return eloc_launch<T, H, 16>(c, a, n);
+  if (eloc_smem<T, H, 12>(c->N) <= (size_t)optin) return eloc_launch<T, H, 12>(c, a, n);
+  return eloc_launch<T, H, 8>(c, a, n);
 }
 
 template <typename T, int H>

@@ -207,8 +207,8 @@ cudaError_t launch_metropolis(scale_ctx* c, const int32_t* pick, const int32_t* 
                               int32_t* accepted);
 cudaError_t launch_eloc_full(scale_ctx* c, double* eloc);
 cudaError_t launch_grad(scale_ctx* c, double* grad, int recompute);
-cudaError_t refresh_samples(scale_ctx* c, bool force_all);
-cudaError_t launch_mark_refresh(scale_ctx* c, bool force_all);
+cudaError_t refresh_samples(scale_ctx* c, bool force_all, bool counters_due = true);
+cudaError_t launch_mark_refresh(scale_ctx* c, bool force_all, bool counters_due);
 cudaError_t launch_slots_list(scale_ctx* c, const int32_t* list, int B);
 cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, void* phi);
 cudaError_t launch_det_f32(scale_ctx* c, float* mats, int n, int B, double* logabs, int32_t* sign);
