@@ -31,10 +31,19 @@ struct MoveScratch {
   int nold[kSMax], nnew[kSMax];
   int pair_s[2 * 9];  // S index of each (touched site, offset) pair, -1 if none
   int slot[kRMax], orb[kRMax], sidx[kRMax], moved[kRMax];
-  T feat[kSMax][H];   // new features H'(L) on S (tile loads/stores stop at nS)
-  T hl[kSMax][H];     // cached features H(L) on S
-  T R[kRMax][kRMax + 1];
+  alignas(16) T feat[kSMax][H];   // new features H'(L) on S (tile loads/stores stop at nS)
+  alignas(16) T hl[kSMax][H];     // cached features H(L) on S
+  alignas(16) T R[kRMax][kRMax + 1];  // also the embedding rows of S while the features are built
 };
+
+// 16-byte asynchronous global -> shared copies (the warp waits for its own copies and then
+// synchronises, after which every lane sees every row).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Per-sample views used by the move routines.
 template <typename T>
@@ -166,9 +175,72 @@ __device__ void move_features(const Lattice& lat, const Net<T>& net, int k0, con
   __syncwarp();
   const int ts_src = net.per_site ? ms.src : 0, ts_dst = net.per_site ? ms.dst : 0;
   // stage z0 and H(L) rows of S, add the layer-0 table deltas, activation + residual.
+  constexpr bool kCopyRows = H <= 32 && kSMax * H <= kRMax * (kRMax + 1);
+  if (kCopyRows && (h * (int)sizeof(T)) % 16 == 0) {
+    // z0 -> feat, H(L) -> hl and the residual embedding rows -> the R area by asynchronous
+    // 16-byte copies; the table-delta loads go out while they travel (two rounds of nine
+    // touched pairs), so the staging costs about two memory round trips
+    constexpr int E = 16 / (int)sizeof(T);
+    const int cpr = h / E;  // chunks per row
+    T* emb = &ms.R[0][0];   // [nS][h]
+    const int nrows = nS * (net.resid[0] ? 3 : 2);
+    for (int q = lane; q < nrows * cpr; q += 32) {
+      const int row = q / cpr, v = q - row * cpr;
+      const int part = row / nS, s = row - part * nS;
+      const int site = ms.site[s];
+      const T* src;
+      T* dst;
+      if (part == 0) {
+        src = sv.z0 + (size_t)site * h;
+        dst = ms.feat[s];
+      } else if (part == 1) {
+        src = sv.HL + (size_t)site * h;
+        dst = ms.hl[s];
+      } else {
+        src = net.embed + ((size_t)(net.per_site ? site * 4 : 0) + ms.nnew[s]) * h;
+        dst = emb + (size_t)s * h;
+      }
+      cp_async16(dst + v * E, src + v * E);
+    }
+    cp_async_commit();
+    const int c = lane;
+    const bool on_c = c < h;
+#pragma unroll
+    for (int p0 = 0; p0 < 2 * 9; p0 += 9) {
+      T kn[9], ko[9];
+#pragma unroll
+      for (int g = 0; g < 9; ++g) {
+        const int p = p0 + g;
+        kn[g] = ko[g] = T(0);
+        if (on_c && p < npairs && ms.pair_s[p] >= 0) {
+          const int d = p % kk;
+          const bool from_src = p < kk;
+          const int ts = from_src ? ts_src : ts_dst;
+          const int nn = from_src ? n_src_new : n_dst_new;
+          const int no = from_src ? n_src_old : n_dst_old;
+          kn[g] = net.KE[(((size_t)ts * 4 + nn) * kk + d) * h + c];
+          ko[g] = net.KE[(((size_t)ts * 4 + no) * kk + d) * h + c];
+        }
+      }
+      if (p0 == 0) {
+        cp_async_wait_all();
+        __syncwarp();
+      }
+#pragma unroll
+      for (int g = 0; g < 9; ++g) {
+        const int p = p0 + g;
+        if (on_c && p < npairs && ms.pair_s[p] >= 0) ms.feat[ms.pair_s[p]][c] += kn[g] - ko[g];
+      }
+    }
+    if (on_c)
+      for (int s = 0; s < nS; ++s) {
+        const T zz = ms.feat[s][c];
+        if (z0_new) z0_new[s][c] = zz;
+        ms.feat[s][c] = (net.resid[0] ? emb[(size_t)s * h + c] : T(0)) + act_fn<T>(net.act, zz);
+      }
+  } else {
   // Loads are issued kG at a time into registers before any is used (groups predicated on
-  // the actual counts): a handful of memory round trips instead of one per row, at a
-  // register cost the 128-register budget of a 16-warp CTA still holds.
+  // the actual counts): a handful of memory round trips instead of one per row.
   constexpr int kG = 6;
   for (int c = lane; c < h; c += 32) {
     // (a) z0 and H(L) rows of S
@@ -231,6 +303,7 @@ __device__ void move_features(const Lattice& lat, const Net<T>& net, int k0, con
           ms.feat[s0 + g][c] = ev[g] + act_fn<T>(net.act, zz);
         }
     }
+  }
   }
   __syncwarp();
   if (net.L > 1) {
