@@ -386,7 +386,8 @@ cudaError_t eloc_t(scale_ctx* c, double* eloc, const int32_t* list, int n) {
   if (eloc_smem<T, H, 20>(c->N) <= (size_t)optin) return eloc_launch<T, H, 20>(c, a, n);
   if (eloc_smem<T, H, 16>(c->N) <= (size_t)optin) return eloc_launch<T, H, 16>(c, a, n);
   if (eloc_smem<T, H, 12>(c->N) <= (size_t)optin) return eloc_launch<T, H, 12>(c, a, n);
-  return eloc_launch<T, H, 8>(c, a, n);
+  if (eloc_smem<T, H, 8>(c->N) <= (size_t)optin) return eloc_launch<T, H, 8>(c, a, n);
+  return eloc_launch<T, H, 4>(c, a, n);  // FP64 with 64 channels: 28 KB of move scratch per warp
 }
 
 template <typename T, int H>

@@ -41,3 +41,19 @@ def conditioning(ora, occ):
             continue
         out[b] = np.linalg.cond(M[b][orbs])
     return out
+
+
+def eloc_term_scale(ora, occ):
+    """|diag| + sum over connected n' of |<n|H|n'> psi(n')/psi(n)| per sample (oracle): the
+    scale of the absolute error of E_loc when every ratio carries the same relative error,
+    |dE| <= delta * scale. Where E_loc is a cancelling sum this exceeds |E_loc| by far."""
+    la, sg = ora.log_psi(occ)
+    out = np.zeros(occ.shape[0])
+    for b in range(occ.shape[0]):
+        xp, cf = ora.connected(occ[b])
+        s = abs(ora.diag(occ[b]))
+        if len(cf):
+            la2, sg2 = ora.log_psi(xp)
+            s += float(np.sum(np.abs(cf) * np.exp(la2 - la[b]) * (sg2 != 0)))
+        out[b] = s
+    return out
