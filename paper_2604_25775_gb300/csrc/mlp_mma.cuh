@@ -114,7 +114,8 @@ __device__ __forceinline__ void mlp_tile(float (&x)[H / 8][4], const WFrag* __re
     const int res = resid[l];
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      const float b0 = bl[8 * j + 2 * t], b1 = bl[8 * j + 2 * t + 1];
+      float c[4] = {b0, b1, b0, b1};  // the accumulators start at the bias
 #pragma unroll
       for (int kk = 0; kk < KT; ++kk) {
         const WFrag w = wl[(kk * NT + j) * 32 + lane];
@@ -128,12 +129,13 @@ __device__ __forceinline__ void mlp_tile(float (&x)[H / 8][4], const WFrag* __re
           mma_bf16(c, ah[kk], w.v[2], w.v[3]);
         }
       }
-      const float b0 = bl[8 * j + 2 * t], b1 = bl[8 * j + 2 * t + 1];
-      const float z0 = c[0] + b0, z1 = c[1] + b1, z2 = c[2] + b0, z3 = c[3] + b1;
-      x[j][0] = (res ? x[j][0] : 0.f) + act_fast(act, z0);
-      x[j][1] = (res ? x[j][1] : 0.f) + act_fast(act, z1);
-      x[j][2] = (res ? x[j][2] : 0.f) + act_fast(act, z2);
-      x[j][3] = (res ? x[j][3] : 0.f) + act_fast(act, z3);
+      if (res) {  // uniform
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[j][q] += act_fast(act, c[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[j][q] = act_fast(act, c[q]);
+      }
     }
   }
 }

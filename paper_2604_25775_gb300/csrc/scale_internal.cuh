@@ -81,7 +81,8 @@ __device__ __forceinline__ float tanh_f32(float z) {
   p = fmaf(p, s, 2.f / 15.f);
   p = fmaf(p, s, -1.f / 3.f);
   const float small = fmaf(z * s, p, z);
-  const float e = __expf(-2.f * a);
+  float e;  // e^{-2|z|} = 2^{|z| (-2 log2 e)}, one multiply into the hardware base-2 exponential
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(a * -2.8853900817779268f));
   const float big = copysignf(__fdividef(1.f - e, 1.f + e), z);
   return a < 0.5f ? small : big;
 }
