@@ -73,7 +73,7 @@ __device__ T warp_inverse(T (*R)[kRMax + 1], T (*Ri)[kRMax + 1], int r) {
     const T pv = R[k][k];
     det *= pv;
     if (pv == T(0)) return T(0);
-    const T inv = T(1) / pv;
+    const T inv = recip(pv);
     T rk = T(0), rik = T(0), f = T(0);
     if (lane < r) {
       rk = R[k][lane] * inv;

@@ -436,7 +436,7 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   for (int a = 0; a < r; ++a) {
     if (!ms.moved[a]) continue;
     const T* m0b = net.M0b + (size_t)ms.orb[a] * Ne;
-    constexpr int KK = 4;  // k values per lane held in registers per pass
+    constexpr int KK = 7;  // k values per lane per pass (224 per warp: one pass at 16x16)
     for (int b0 = 0; b0 < r; b0 += 4) {
       T g[4] = {T(0), T(0), T(0), T(0)};
       const T* br[4];
@@ -468,6 +468,10 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   __syncwarp();
   return r;
 }
+
+// 1/x rounded to nearest: the same value as the division 1/x, without its general path.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 
 // Pivot row of column k among rows [k, r) of R (lane i holds row i): the largest |R[i][k]|,
 // ties to the lowest row. Same value in every lane.
@@ -517,7 +521,7 @@ __device__ T warp_det(MoveScratch<T, H>& ms, int r) {
     const T pv = ms.R[k][k];
     det *= pv;
     if (pv == T(0)) return T(0);
-    const T inv = T(1) / pv;
+    const T inv = recip(pv);
     // multipliers in column k (lane i > k), then the trailing update (lane j > k)
     if (lane > k && lane < r) ms.R[lane][k] *= inv;
     __syncwarp();
