@@ -183,12 +183,12 @@ namespace scale {
 cudaError_t refresh_samples(scale_ctx* c, bool force_all, bool counters_due) {
   cudaError_t e;
   if ((e = launch_mark_refresh(c, force_all, counters_due)) != cudaSuccess) return e;
-  if ((e = launch_forward(c, c->occ, c->B, c->list, true, c->Phi64)) != cudaSuccess) return e;
+  if ((e = launch_forward(c, c->occ, c->B, c->list, true, c->Phi64, c->list_count)) != cudaSuccess) return e;
   if ((e = launch_slots_list(c, c->list, c->B)) != cudaSuccess) return e;
   if ((e = launch_gj(c, c->Phi64, c->Ne, c->B, c->list, true, c->fp64, c->Binv, c->logabs, c->sign_slot,
                      c->status)) != cudaSuccess)
     return e;
-  return launch_projector(c, c->B, c->list);
+  return launch_projector(c, c->B, c->list, c->list_count);
 }
 
 }  // namespace scale

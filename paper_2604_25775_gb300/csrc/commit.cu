@@ -675,20 +675,22 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
   }
 }
 
-// list[b] = b when sample b needs an FP64 re-factorisation, else -1: all samples
-// (force_all), a sample whose drift check fired or whose Woodbury step was skipped, and
-// (when counters_due) a sample whose commit counter reached refresh_every.
+// The samples that need an FP64 re-factorisation -- all of them (force_all), a sample whose
+// drift check fired or whose Woodbury step was skipped, and (when counters_due) a sample
+// whose commit counter reached refresh_every -- compacted into list[0, *count); the rest
+// of list is -1 (set before the launch). The order of the entries is arbitrary; every
+// sample is re-factorised on its own.
 __global__ void k_mark_refresh(int B, int refresh_every, bool force_all, bool counters_due,
                                const int32_t* __restrict__ commits, const int32_t* __restrict__ status,
-                               int32_t* __restrict__ list, int32_t* __restrict__ n_refresh,
-                               int32_t* __restrict__ n_drift) {
+                               int32_t* __restrict__ list, int32_t* __restrict__ count,
+                               int32_t* __restrict__ n_refresh, int32_t* __restrict__ n_drift) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const int st = status[b];
   const bool bad = st & (SCALE_SAMPLE_BAD_COUNT | SCALE_SAMPLE_DOUBLE_OCC);
   const bool drift = st & SCALE_SAMPLE_DRIFT;
   const bool need = !bad && (force_all || drift || (counters_due && commits[b] >= refresh_every));
-  list[b] = need ? b : -1;
+  if (need) list[atomicAdd(count, 1)] = b;
   if (need) {
     atomicAdd(n_refresh, 1);
     if (drift && !force_all) atomicAdd(n_drift, 1);
@@ -762,9 +764,12 @@ cudaError_t launch_metropolis(scale_ctx* c, const int32_t* pick, const int32_t* 
 
 cudaError_t launch_mark_refresh(scale_ctx* c, bool force_all, bool counters_due) {
   int32_t* counters = reinterpret_cast<int32_t*>(c->stat_dev + 1);
+  cudaError_t e = cudaMemsetAsync(c->list, 0xff, sizeof(int32_t) * (size_t)c->B, c->stream);  // all -1
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->list_count, 0, sizeof(int32_t), c->stream);
+  if (e != cudaSuccess) return e;
   k_mark_refresh<<<(c->B + 255) / 256, 256, 0, c->stream>>>(c->B, c->arch.refresh_every, force_all, counters_due,
-                                                            c->commits, c->status, c->list, counters + 1,
-                                                            counters + 2);
+                                                            c->commits, c->status, c->list, c->list_count,
+                                                            counters + 1, counters + 2);
   return cudaGetLastError();
 }
 

@@ -17,16 +17,18 @@ namespace {
 template <typename T>
 __global__ void k_layer(Lattice lat, Net<T> net, int l, const int8_t* __restrict__ occ,
                         const int32_t* __restrict__ list, const T* __restrict__ in, T* __restrict__ out,
-                        T* __restrict__ zout, int B) {
+                        T* __restrict__ zout, int B, const int32_t* __restrict__ count) {
   const int h = net.h, N = lat.N;
-  const int row = blockIdx.y;  // position in the launch
-  const int b = list ? list[row] : row;
-  if (b < 0) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * h) return;
   const int i = idx / h, c = idx - i * h;
   const int k = net.ksize[l], r = (k - 1) / 2;
   const T* K = net.kernel[l];
+  // positions in the launch: all B, or the first *count entries of a compacted list
+  const int nrows = count ? min(*count, B) : B;
+  for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+  const int b = list ? list[row] : row;
+  if (b < 0) continue;
   T z = net.bias[l][c];
   const int8_t* ob = occ + (size_t)b * N;
   const T* ib = in ? in + (size_t)b * N * h : nullptr;
@@ -47,6 +49,7 @@ __global__ void k_layer(Lattice lat, Net<T> net, int l, const int8_t* __restrict
   }
   out[(size_t)b * N * h + idx] = self + act_fn<T>(net.act, z);
   if (zout) zout[(size_t)b * N * h + idx] = z;
+  }
 }
 
 // Block-wide exclusive scan of 0/1 flags over 2N orbitals; writes the ascending list of
@@ -134,10 +137,13 @@ __global__ void k_slots(Lattice lat, const int8_t* __restrict__ occ, const int32
 // o_a = s*N + i the a-th occupied orbital. Computed in T, stored as TO.
 template <typename T, typename TO>
 __global__ void k_phi(Lattice lat, Net<T> net, const int8_t* __restrict__ occ, const int32_t* __restrict__ list,
-                      const T* __restrict__ HL, TO* __restrict__ phi) {
+                      const T* __restrict__ HL, TO* __restrict__ phi, int B, const int32_t* __restrict__ count) {
   extern __shared__ int sm[];
-  const int b = list ? list[blockIdx.x] : blockIdx.x;
-  if (b < 0) return;
+  const int nrows = count ? min(*count, B) : B;
+  for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+  __syncthreads();  // the previous sample's use of shared memory is over
+  const int b = list ? list[row] : row;
+  if (b < 0) continue;
   const int N = lat.N, Ne = lat.Ne, h = net.h;
   int* olist = sm;
   int* tmp = sm + 2 * N;
@@ -145,7 +151,7 @@ __global__ void k_phi(Lattice lat, Net<T> net, const int8_t* __restrict__ occ, c
   TO* P = phi + (size_t)b * Ne * Ne;
   if (n != Ne) {  // invalid sample: leave a zero matrix (singular)
     for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = TO(0);
-    return;
+    continue;
   }
   const T* Hb = HL + (size_t)b * N * h;
   for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) {
@@ -156,6 +162,7 @@ __global__ void k_phi(Lattice lat, Net<T> net, const int8_t* __restrict__ occ, c
     const T* x = Hb + (size_t)i * h;
     for (int c = 0; c < h; ++c) v += x[c] * w[(size_t)c * 2 * Ne];
     P[q] = (TO)v;
+  }
   }
 }
 
@@ -209,10 +216,11 @@ __global__ void k_logpsi_out(int Ne, const int32_t* __restrict__ orb_of_slot, co
 template <int H, int KIND>
 __global__ void __launch_bounds__(256) k_mlp_fwd(Net<float> net, const WFrag* __restrict__ wf, int N, int B,
                                                  const int32_t* __restrict__ list, const float* __restrict__ in,
-                                                 float* __restrict__ out) {
+                                                 float* __restrict__ out, const int32_t* __restrict__ count) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long row0 = (long long)warp * 16;
-  const long long rows = (long long)B * N;  // B = entries of the launch (list length)
+  // entries of the launch: B, or the first *count entries of a compacted list
+  const long long rows = (long long)(count ? min(*count, B) : B) * N;
   if (row0 >= rows) return;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   float x[H / 8][4];
@@ -343,17 +351,20 @@ template Net<float> make_net<float>(scale_ctx*);
 namespace {
 template <typename T>
 cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, bool keep_cache,
-                      double* phi_out, void* phi_f32) {
+                      double* phi_out, void* phi_f32, const int32_t* count) {
   const Net<T> net = make_net<T>(c);
   const int N = c->N, h = c->h;
-  dim3 grid((N * h + 127) / 128, B);
+  // with a compacted list (count on the device) the kernels loop over its entries from a
+  // capped grid instead of launching a CTA per sample of the batch
+  const int Bgrid = count ? std::min(B, 256) : B;
+  dim3 grid((N * h + 127) / 128, Bgrid);
   T* bufs[2] = {(T*)c->act_a, (T*)c->act_b};
   const T* in = nullptr;
   const bool mma = c->use_mma && c->L > 1;
   for (int l = 0; l < (mma ? 1 : c->L); ++l) {
     T* out = (l == c->L - 1 && keep_cache) ? (T*)c->HL : bufs[l & 1];
     T* zo = (l == 0 && keep_cache) ? (T*)c->z0 : nullptr;
-    k_layer<T><<<grid, 128, 0, c->stream>>>(c->lat, net, l, occ, list, in, out, zo, B);
+    k_layer<T><<<grid, 128, 0, c->stream>>>(c->lat, net, l, occ, list, in, out, zo, B, count);
     in = out;
   }
   if constexpr (sizeof(T) == 4) {
@@ -365,38 +376,39 @@ cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* lis
       const WFrag* wf = (const WFrag*)c->wfrag;
       const float* fin = (const float*)in;
       if (c->arch.precision == SCALE_PREC_MIXED_BF16) {
-        if (c->hpad == 16) k_mlp_fwd<16, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
-        else if (c->hpad == 32) k_mlp_fwd<32, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
-        else k_mlp_fwd<64, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
+        if (c->hpad == 16) k_mlp_fwd<16, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
+        else if (c->hpad == 32) k_mlp_fwd<32, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
+        else k_mlp_fwd<64, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
       } else {
-        if (c->hpad == 16) k_mlp_fwd<16, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
-        else if (c->hpad == 32) k_mlp_fwd<32, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
-        else k_mlp_fwd<64, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out);
+        if (c->hpad == 16) k_mlp_fwd<16, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
+        else if (c->hpad == 32) k_mlp_fwd<32, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
+        else k_mlp_fwd<64, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
       }
       in = (const T*)out;
     }
   }
   const size_t smem = sizeof(int) * (2 * N + 257);
+  const int Bphi = count ? std::min(B, 1024) : B;
   if (phi_out)
-    k_phi<T, double><<<B, 256, smem, c->stream>>>(c->lat, net, occ, list, in, phi_out);
+    k_phi<T, double><<<Bphi, 256, smem, c->stream>>>(c->lat, net, occ, list, in, phi_out, B, count);
   if (phi_f32)
-    k_phi<T, float><<<B, 256, smem, c->stream>>>(c->lat, net, occ, list, in, (float*)phi_f32);
+    k_phi<T, float><<<Bphi, 256, smem, c->stream>>>(c->lat, net, occ, list, in, (float*)phi_f32, B, count);
   return cudaGetLastError();
 }
 }  // namespace
 
 // Forward every listed sample of occ; keep_cache writes z0 / HL of the context.
 cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, bool keep_cache,
-                           double* phi_out) {
-  if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, nullptr);
-  return forward_t<float>(c, occ, B, list, keep_cache, phi_out, nullptr);
+                           double* phi_out, const int32_t* count) {
+  if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, nullptr, count);
+  return forward_t<float>(c, occ, B, list, keep_cache, phi_out, nullptr, count);
 }
 
 // Forward for the full-recompute path: Slater matrices of B configurations into phi
 // (double in FP64 mode, float in mixed mode); features go to the scratch buffers.
 cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, void* phi) {
-  if (c->fp64) return forward_t<double>(c, occ, B, nullptr, false, (double*)phi, nullptr);
-  return forward_t<float>(c, occ, B, nullptr, false, nullptr, phi);
+  if (c->fp64) return forward_t<double>(c, occ, B, nullptr, false, (double*)phi, nullptr, nullptr);
+  return forward_t<float>(c, occ, B, nullptr, false, nullptr, phi, nullptr);
 }
 
 cudaError_t launch_slots(scale_ctx* c, const int8_t* occ, int B) {

@@ -284,11 +284,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_ratios(LowrankArgs a, Net<T> ne
 template <typename T>
 __global__ void __launch_bounds__(256) k_project(int Ne, int h, const T* __restrict__ proj_w,
                                                  const T* __restrict__ Binv, T* __restrict__ Pt,
-                                                 const int32_t* __restrict__ list) {
+                                                 const int32_t* __restrict__ list, int B,
+                                                 const int32_t* __restrict__ count) {
   __shared__ T Bs[32][33];
   __shared__ T Ws[32][2 * kMaxH + 1];
-  const int b = list ? list[blockIdx.y] : blockIdx.y;
-  if (b < 0) return;
+  const int nrows = count ? min(*count, B) : B;  // a compacted list: its first *count entries
+  for (int lrow = blockIdx.y; lrow < nrows; lrow += gridDim.y) {
+  __syncthreads();  // the previous sample's tiles are consumed
+  const int b = list ? list[lrow] : lrow;
+  if (b < 0) continue;
   const int c0 = blockIdx.x * 32;
   const int tid = threadIdx.x;
   const int row = tid >> 3, grp = tid & 7;
@@ -320,14 +324,16 @@ __global__ void __launch_bounds__(256) k_project(int Ne, int h, const T* __restr
     __syncthreads();
   }
   const int c = c0 + row;
-  if (c >= Ne) return;
+  if (c < Ne) {
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int col = grp + 8 * u;
-    if (col < ncol) {
-      const int s = col / h, cc = col - s * h;
-      Pt[(((size_t)b * 2 + s) * Ne + c) * h + cc] = acc[u];
+    for (int u = 0; u < 16; ++u) {
+      const int col = grp + 8 * u;
+      if (col < ncol) {
+        const int s = col / h, cc = col - s * h;
+        Pt[(((size_t)b * 2 + s) * Ne + c) * h + cc] = acc[u];
+      }
     }
+  }
   }
 }
 
@@ -404,9 +410,10 @@ cudaError_t ratios_t(scale_ctx* c, const int32_t* moves, int M, double* ratio) {
 }
 
 template <typename T>
-cudaError_t project_t(scale_ctx* c, int B, const int32_t* list) {
-  dim3 grid((c->Ne + 31) / 32, B);
-  k_project<T><<<grid, 256, 0, c->stream>>>(c->Ne, c->h, make_net<T>(c).proj_w, (const T*)c->Binv, (T*)c->Pt, list);
+cudaError_t project_t(scale_ctx* c, int B, const int32_t* list, const int32_t* count) {
+  dim3 grid((c->Ne + 31) / 32, count ? std::min(B, 1024) : B);
+  k_project<T><<<grid, 256, 0, c->stream>>>(c->Ne, c->h, make_net<T>(c).proj_w, (const T*)c->Binv, (T*)c->Pt, list,
+                                            B, count);
   return cudaGetLastError();
 }
 
@@ -430,8 +437,8 @@ cudaError_t launch_ratios(scale_ctx* c, const int32_t* moves, int M, double* rat
   return SCALE_DISPATCH_H(c, ratios_t, c, moves, M, ratio);
 }
 
-cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list) {
-  return c->fp64 ? project_t<double>(c, B, list) : project_t<float>(c, B, list);
+cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list, const int32_t* count) {
+  return c->fp64 ? project_t<double>(c, B, list, count) : project_t<float>(c, B, list, count);
 }
 
 }  // namespace scale

@@ -188,13 +188,14 @@ struct scale_ctx {
 namespace scale {
 
 // kernels (launch wrappers), each enqueued on ctx->stream
+// count (optional, device): sample_list is compacted, its first *count entries are used
 cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t* sample_list,
-                           bool keep_cache, double* phi_out);
+                           bool keep_cache, double* phi_out, const int32_t* count = nullptr);
 cudaError_t launch_slots(scale_ctx* c, const int8_t* occ, int B);
 cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32_t* list,
                       bool inverse, bool out_fp64, void* Binv, double* logabs, int32_t* sign,
                       int32_t* status);
-cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list);
+cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list, const int32_t* count = nullptr);
 cudaError_t launch_build_ke(scale_ctx* c);
 cudaError_t launch_build_wfrag(scale_ctx* c);
 cudaError_t launch_eloc_lowrank_list(scale_ctx* c, const int32_t* list, int n, double* eloc);
