@@ -22,7 +22,9 @@
  *   * E_loc(n) = sum_n' <n|H|n'> psi(n')/psi(n) (Sec. II.A) with EVERY psi(n') from a
  *     full network forward plus a fresh LU (the O(N^4) route of Sec. III.A);
  *   * d log|psi| / d theta by a hand-written FP64 backward pass;
- *   * Metropolis steps n -> n' with acceptance min(1, |psi(n')/psi(n)|^2) (Sec. II.A).
+ *   * Metropolis steps n -> n' with acceptance min(1, |psi(n')/psi(n)|^2) (Sec. II.A);
+ *   * the symmetry-projected amplitude sum_g Pi(n, g) chi_g psi(g n) (App. "Symmetry
+ *     Projection").
  *
  * Parity status: every function here is pinned by CPU tests (closed-form U=0 energy,
  * library convolution and slogdet, dense-Hamiltonian enumeration, finite differences,
@@ -510,6 +512,67 @@ int ora_ratio(const ora_model *m, int B, const int8_t *occ, const int32_t *moves
       amplitude(m, x2, &w, &la2, &sg2);
       ratio[b] = (sg == 0 || sg2 == 0) ? 0.0 : (double)(sg * sg2) * exp(la2 - la);
     }
+    free(x2);
+    ws_free(&w);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Symmetry-projected amplitude (App. "Symmetry Projection"):
+ *   psi_sym(n) = sum_g Pi(n, g) chi_g psi(g n).
+ * Each group element is an orbital permutation perm[g][o] (o = s*N + i; a lattice symmetry
+ * moves the site of both spins, spin inversion exchanges s); g n occupies perm[g][o] for
+ * every orbital o occupied in n. Pi(n, g) is the fermionic sign of that relabelling: with
+ * o_1 < ... < o_Ne the occupied orbitals of n, the parity of the permutation that sorts
+ * (perm[g][o_1], ..., perm[g][o_Ne]) ascending. The characters chi_g are real (one-
+ * dimensional real representations, e.g. the fully symmetric one). A g n outside the
+ * model's space (wrong particle numbers, double occupancy in t-J) has psi = 0. The sum is
+ * accumulated in FP64 as s * exp(m) (largest log|psi| first) and returned as log|psi_sym|
+ * and its sign (0 for a vanishing sum).
+ * ------------------------------------------------------------------------------------ */
+int ora_log_psi_sym(const ora_model *m, int B, const int8_t *occ, int G, const int32_t *perm, const double *chi,
+                    double *logabs, int32_t *sign) {
+  const int N = m->Lx * m->Ly;
+#pragma omp parallel
+  {
+    ora_ws w = ws_alloc(m);
+    int8_t *x2 = (int8_t *)malloc(N);
+    int *orbs = (int *)malloc(sizeof(int) * 2 * N);
+    int *img = (int *)malloc(sizeof(int) * 2 * N);
+#pragma omp for schedule(dynamic)
+    for (int b = 0; b < B; ++b) {
+      const int8_t *x = occ + (int64_t)b * N;
+      const int n = occupied(m, x, orbs);
+      double mx = -INFINITY, s = 0.0;
+      for (int g = 0; g < G; ++g) {
+        const int32_t *pg = perm + (int64_t)g * 2 * N;
+        memset(x2, 0, N);
+        for (int a = 0; a < n; ++a) {
+          img[a] = pg[orbs[a]];
+          x2[img[a] % N] |= (int8_t)(1 << (img[a] / N));
+        }
+        int inv = 0;
+        for (int a = 0; a < n; ++a)
+          for (int c = a + 1; c < n; ++c) inv += img[a] > img[c];
+        double la;
+        int sg;
+        amplitude(m, x2, &w, &la, &sg);
+        if (sg == 0) continue;
+        const double c = chi[g] * ((inv & 1) ? -1.0 : 1.0) * sg;
+        if (c == 0.0) continue;
+        if (la > mx) {
+          s = s * exp(mx - la) + c;
+          mx = la;
+        } else {
+          s += c * exp(la - mx);
+        }
+      }
+      logabs[b] = (s == 0.0) ? -INFINITY : mx + log(fabs(s));
+      sign[b] = s > 0.0 ? 1 : (s < 0.0 ? -1 : 0);
+    }
+    free(img);
+    free(orbs);
     free(x2);
     ws_free(&w);
   }

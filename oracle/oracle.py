@@ -78,6 +78,8 @@ def _load():
             lib.ora_diag.argtypes = [P(_Model), ctypes.c_void_p]
             lib.ora_num_threads.restype = ctypes.c_int
             lib.ora_metropolis.restype = ctypes.c_int
+            lib.ora_log_psi_sym.restype = ctypes.c_int
+            lib.ora_log_psi_sym.argtypes = [P(_Model), ctypes.c_int, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4
             lib.ora_metropolis.argtypes = [P(_Model), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 5
             _lib = lib
     return _lib
@@ -179,6 +181,20 @@ class Model:
     def diag(self, occ1: np.ndarray) -> float:
         occ1 = np.ascontiguousarray(occ1, dtype=np.int8)
         return float(_load().ora_diag(ctypes.byref(self.s), occ1.ctypes.data))
+
+    def log_psi_sym(self, occ: np.ndarray, perms: np.ndarray, chi: np.ndarray):
+        """log|psi_sym| and sign of sum_g Pi(n, g) chi_g psi(g n); perms [G][2N] orbital
+        permutations, chi [G] real characters."""
+        occ = np.ascontiguousarray(occ, dtype=np.int8)
+        perms = np.ascontiguousarray(perms, dtype=np.int32)
+        chi = np.ascontiguousarray(chi, dtype=np.float64)
+        B, G = occ.shape[0], perms.shape[0]
+        assert perms.shape == (G, 2 * self.N) and chi.shape == (G,)
+        la = np.zeros(B)
+        sg = np.zeros(B, dtype=np.int32)
+        _load().ora_log_psi_sym(ctypes.byref(self.s), B, occ.ctypes.data, G, perms.ctypes.data, chi.ctypes.data,
+                                la.ctypes.data, sg.ctypes.data)
+        return la, sg
 
     def metropolis(self, occ: np.ndarray, pick: np.ndarray, direction: np.ndarray, u: np.ndarray):
         """Metropolis steps (hop proposals, acceptance min(1, |psi'/psi|^2)); pick, direction

@@ -223,6 +223,42 @@ def metropolis_randoms(pb: Problem, B: int, S: int, seed: int):
     return pick, direction, u
 
 
+def symmetry_group(pb: Problem, translations: bool = True, reflections: bool = False,
+                   spin_inversion: bool = False):
+    """Orbital permutations [G][2N] int32 of a lattice symmetry group (o = s*N + i): the
+    translations of the periodic axes, the reflections x -> -x and y -> -y (about the
+    lattice centre on open axes), and the exchange of the two spins, all products of the
+    chosen generators. Row 0 is the identity."""
+    N, Lx, Ly = pb.N, pb.Lx, pb.Ly
+    site_maps = []
+    txs = range(Lx) if (translations and pb.pbc_x) else [0]
+    tys = range(Ly) if (translations and pb.pbc_y) else [0]
+    rxs = (False, True) if reflections else (False,)
+    rys = (False, True) if reflections else (False,)
+    for rx in rxs:
+        for ry in rys:
+            for tx in txs:
+                for ty in tys:
+                    m = np.zeros(N, dtype=np.int64)
+                    for i in range(N):
+                        x, y = i % Lx, i // Lx
+                        if rx:
+                            x = (-x) % Lx if pb.pbc_x else Lx - 1 - x
+                        if ry:
+                            y = (-y) % Ly if pb.pbc_y else Ly - 1 - y
+                        m[i] = ((y + ty) % Ly) * Lx + (x + tx) % Lx
+                    site_maps.append(m)
+    perms = []
+    for m in site_maps:
+        for flip in ((False, True) if spin_inversion else (False,)):
+            p = np.zeros(2 * N, dtype=np.int32)
+            for s in range(2):
+                for i in range(N):
+                    p[s * N + i] = ((1 - s) if flip else s) * N + m[i]
+            perms.append(p)
+    return np.array(perms, dtype=np.int32)
+
+
 def random_hop_moves(pb: Problem, occ: np.ndarray, seed: int) -> np.ndarray:
     """One proposed nearest-neighbour move per sample, int32 [B][4] = (kind, src, dst, spin).
 
