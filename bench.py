@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--sweep-steps", type=int, default=64)
+    ap.add_argument("--sym-walkers", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -61,12 +62,21 @@ ELOC_PROFILE = os.path.join(ROOT, "profiles", "k_eloc_hubbard16x16.md")
 ELOC_SOURCES = ["lowrank.cu", "move.cuh", "mlp_mma.cuh", "scale_internal.cuh"]
 
 
+# The shared header contributes only its device part (geometry, parameter view, activation
+# functions); the context struct and launch declarations below the marker do not reach the
+# kernel's code.
+HEADER_DEVICE_END = b"\n// The context (opaque to callers)."
+
+
 def eloc_sources_sha256() -> str:
     import hashlib
     h = hashlib.sha256()
     for name in ELOC_SOURCES:
         with open(os.path.join(ROOT, "paper_2604_25775_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+            data = f.read()
+        if name == "scale_internal.cuh":
+            data = data.split(HEADER_DEVICE_END, 1)[0]
+        h.update(data)
     return h.hexdigest()
 
 
@@ -441,6 +451,24 @@ def main():
                              "steps_per_sweep": steps_per_sample}
             del pk_d, dr_d, uu_d, pk_t, dr_t, uu_t
             ctxs.close()
+        # symmetry projection over the lattice translations: |G| fresh amplitudes per walker
+        if args.sym_walkers > 0:
+            ns = args.sym_walkers
+            perms = torch.from_numpy(I.symmetry_group(pb, translations=True)).cuda()
+            chi = torch.ones(perms.shape[0], dtype=torch.float64, device="cuda")
+            ctxy = Bd.make_context(pb, params, M0, ns)
+            ctxy.scale_load(occ_d[:ns].contiguous())
+            ctxy.log_psi_sym(perms[:4].contiguous(), chi[:4].contiguous())
+            torch.cuda.synchronize()
+            a.record()
+            ctxy.log_psi_sym(perms, chi)
+            b2.record()
+            torch.cuda.synchronize()
+            sy_ms = a.elapsed_time(b2)
+            line["symmetry"] = {"walkers": ns, "group": int(perms.shape[0]), "ms": sy_ms,
+                                "amplitudes_per_s": ns * perms.shape[0] / (sy_ms / 1e3),
+                                "walkers_per_s": ns / (sy_ms / 1e3)}
+            ctxy.close()
         # serving: open-loop Poisson sweep-step requests over mixed chains, continuous batching
         if args.serve_seconds > 0:
             from paper_2604_25775_gb300 import serve_bench

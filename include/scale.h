@@ -208,6 +208,23 @@ scale_status scale_commit(scale_ctx *ctx, const int32_t *moves);
 scale_status scale_sweep(scale_ctx *ctx, int32_t n_steps, const int32_t *pick, const int32_t *dir,
                          const double *u, int32_t *accepted);
 
+/* Symmetry-projected amplitude of the loaded samples (App. "Symmetry Projection"):
+ *   psi_sym(n) = sum_g Pi(n, g) chi_g psi(g n).
+ * perms: device int32 [G][2N] orbital permutations (o = s*N + i; g n occupies perms[g][o]
+ * for each orbital o occupied in n; lattice symmetries move the site of both spins, spin
+ * inversion exchanges s, and with n_up != n_dn its images leave the sector and give no
+ * term). chi: device float64 [G] real characters (1 for the fully symmetric projection). Pi(n, g) is the parity of the permutation sorting the images
+ * of n's occupied orbitals (ascending), the fermionic sign of the relabelling. Every psi(g n)
+ * is a fresh network forward and FP64 LU (G evaluations per sample); the cached inverses and
+ * features are left untouched. Outputs: logabs float64 [B] (log|psi_sym|, -inf when the sum
+ * vanishes) and sign int32 [B]. An image outside the model's space (other particle numbers, a
+ * t-J double occupancy, two occupied orbitals sent to one, or an occupied orbital sent outside
+ * [0, 2N)) contributes 0. All pointers are device memory owned by the caller; the call is
+ * asynchronous on the context's stream. SCALE_EINVAL: G < 1, a null pointer, or no parameters
+ * or samples loaded. */
+scale_status scale_log_psi_sym(scale_ctx *ctx, int32_t G, const int32_t *perms, const double *chi,
+                               double *logabs, int32_t *sign);
+
 /* Re-factorise in FP64 every loaded sample (force_all = 1) or only the ones flagged by
  * the drift check or the commit counter (force_all = 0). */
 scale_status scale_refresh(scale_ctx *ctx, int32_t force_all);

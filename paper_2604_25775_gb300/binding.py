@@ -27,7 +27,7 @@ EXPORTED = [
     "scale_param_count", "scale_footprint_bytes", "scale_create", "scale_set_params", "scale_load",
     "scale_log_psi", "scale_get_occ", "scale_ratios", "scale_local_energy", "scale_commit",
     "scale_refresh", "scale_grad_logpsi", "scale_get_stats", "scale_last_error", "scale_destroy",
-    "scale_sweep",
+    "scale_sweep", "scale_log_psi_sym",
 ]
 
 
@@ -89,7 +89,8 @@ def load_library(build: bool = True):
                                ("scale_refresh", [V, ctypes.c_int32]),
                                ("scale_grad_logpsi", [V, V, ctypes.c_int32]),
                                ("scale_get_stats", [V, P(scale_stats)]),
-                               ("scale_sweep", [V, ctypes.c_int32, V, V, V, V])):
+                               ("scale_sweep", [V, ctypes.c_int32, V, V, V, V]),
+                               ("scale_log_psi_sym", [V, ctypes.c_int32, V, V, V, V])):
                 fn = getattr(lib, name)
                 fn.restype = ctypes.c_int
                 fn.argtypes = args
@@ -220,6 +221,22 @@ class Context:
                                          _ptr(direction, torch.int32, (S, self.B), "direction"),
                                          _ptr(u, torch.float64, (S, self.B), "u"),
                                          _ptr(accepted, torch.int32, (self.B,), "accepted")))
+
+    def scale_log_psi_sym(self, perms, chi, logabs, sign):
+        """perms int32 [G][2N], chi float64 [G], logabs float64 [B], sign int32 [B]."""
+        import torch
+        G = int(perms.shape[0])
+        self._check(self.lib.scale_log_psi_sym(self.h, G, _ptr(perms, torch.int32, (G, 2 * self.N), "perms"),
+                                               _ptr(chi, torch.float64, (G,), "chi"),
+                                               _ptr(logabs, torch.float64, (self.B,), "logabs"),
+                                               _ptr(sign, torch.int32, (self.B,), "sign")))
+
+    def log_psi_sym(self, perms, chi):
+        import torch
+        la = torch.empty(self.B, dtype=torch.float64, device="cuda")
+        sg = torch.empty(self.B, dtype=torch.int32, device="cuda")
+        self.scale_log_psi_sym(perms, chi, la, sg)
+        return la, sg
 
     def scale_refresh(self, force_all=True):
         self._check(self.lib.scale_refresh(self.h, 1 if force_all else 0))

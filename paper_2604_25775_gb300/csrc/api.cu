@@ -426,6 +426,15 @@ scale_status scale_sweep(scale_ctx* c, int32_t n_steps, const int32_t* pick, con
   return SCALE_OK;
 }
 
+scale_status scale_log_psi_sym(scale_ctx* c, int32_t G, const int32_t* perms, const double* chi, double* logabs,
+                               int32_t* sign) {
+  scale_status s = check_loaded(c);
+  if (s != SCALE_OK) return s;
+  if (G < 1 || !perms || !chi || !logabs || !sign) return SCALE_EINVAL;
+  SCALE_TRY(c, launch_log_psi_sym(c, G, perms, chi, logabs, sign));
+  return SCALE_OK;
+}
+
 scale_status scale_refresh(scale_ctx* c, int32_t force_all) {
   scale_status s = check_loaded(c);
   if (s != SCALE_OK) return s;

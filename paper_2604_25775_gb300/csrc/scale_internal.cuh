@@ -207,6 +207,8 @@ cudaError_t launch_ratios(scale_ctx* c, const int32_t* moves, int M, double* rat
 cudaError_t launch_commit(scale_ctx* c, const int32_t* moves);
 cudaError_t launch_metropolis(scale_ctx* c, const int32_t* pick, const int32_t* dir, const double* u,
                               int32_t* accepted);
+cudaError_t launch_log_psi_sym(scale_ctx* c, int G, const int32_t* perms, const double* chi, double* logabs,
+                               int32_t* sign);
 cudaError_t launch_eloc_full(scale_ctx* c, double* eloc);
 cudaError_t launch_grad(scale_ctx* c, double* grad, int recompute);
 cudaError_t refresh_samples(scale_ctx* c, bool force_all, bool counters_due = true);
