@@ -24,7 +24,15 @@
  *   * d log|psi| / d theta by a hand-written FP64 backward pass;
  *   * Metropolis steps n -> n' with acceptance min(1, |psi(n')/psi(n)|^2) (Sec. II.A);
  *   * the symmetry-projected amplitude sum_g Pi(n, g) chi_g psi(g n) (App. "Symmetry
- *     Projection").
+ *     Projection");
+ *   * the ACE network (Sec. II "ACE", Eq. ACE): the embedding, then n_conv blocks
+ *       H(l+1) = LN( H(l) + SiLU(Conv_l(H(l))) )
+ *     with LN the layer normalisation of each site's channel vector (mean and biased
+ *     variance over the channels, (x - mean) / sqrt(var + eps) * gamma + beta), then the
+ *     site-wise layers of Eq. MLP at width h_mlp and the orbital projection. Every psi
+ *     that the functions above take goes through the same amplitude routine, so the ACE
+ *     log psi, local energy (full recompute of every psi(n')) and symmetry projection
+ *     follow from it.
  *
  * Parity status: every function here is pinned by CPU tests (closed-form U=0 energy,
  * library convolution and slogdet, dense-Hamiltonian enumeration, finite differences,
@@ -47,6 +55,10 @@ typedef struct {
   int32_t n_layers, h, act, per_site_embed; /* act: 0 tanh, 1 SiLU */
   int32_t ksize[ORA_MAX_LAYERS];
   int32_t residual[ORA_MAX_LAYERS];
+  int32_t family;       /* 0 SCALE, 1 ACE */
+  int32_t n_conv;       /* ACE: layers [0, n_conv) are conv blocks with layer normalisation */
+  int32_t h_mlp;        /* ACE: width of the site-wise layers after the conv blocks */
+  double ln_eps;        /* ACE: epsilon of the layer normalisation */
   const double *params; /* flat parameter vector (layout in the Python wrapper) */
   const double *M0;     /* [2N][Ne] reference orbitals */
 } ora_model;
@@ -90,29 +102,54 @@ int ora_bonds(const ora_model *m, int which, int32_t *pairs) {
   return nb;
 }
 
+/* Channel widths. SCALE: every layer has h channels. ACE: the conv blocks keep h, the
+ * site-wise layers after them have h_mlp (the first one maps h -> h_mlp). */
+static int width_out(const ora_model *m, int l) {
+  return (m->family == 1 && l >= m->n_conv) ? m->h_mlp : m->h;
+}
+static int width_in(const ora_model *m, int l) { return l == 0 ? m->h : width_out(m, l - 1); }
+static int width_last(const ora_model *m) { return m->n_layers ? width_out(m, m->n_layers - 1) : m->h; }
+static int width_max(const ora_model *m) {
+  return (m->family == 1 && m->h_mlp > m->h && m->n_layers > m->n_conv) ? m->h_mlp : m->h;
+}
+static int has_ln(const ora_model *m, int l) { return m->family == 1 && l < m->n_conv; }
+
 int64_t ora_param_count(const ora_model *m) {
   int64_t N = (int64_t)m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn;
   int64_t n = (m->per_site_embed ? N : 1) * 4 * h;
-  for (int l = 0; l < m->n_layers; ++l) n += (int64_t)m->ksize[l] * m->ksize[l] * h * h + h;
-  n += h * 2 * Ne + 2 * Ne;
+  for (int l = 0; l < m->n_layers; ++l) {
+    const int64_t ci = width_in(m, l), co = width_out(m, l);
+    n += (int64_t)m->ksize[l] * m->ksize[l] * ci * co + co;
+    if (has_ln(m, l)) n += 2 * co;
+  }
+  n += (int64_t)width_last(m) * 2 * Ne + 2 * Ne;
   return n;
 }
 
 /* Offsets of the parameter tensors inside the flat vector. */
 typedef struct {
-  int64_t embed, kernel[ORA_MAX_LAYERS], bias[ORA_MAX_LAYERS], proj_w, proj_b, total;
+  int64_t embed, kernel[ORA_MAX_LAYERS], bias[ORA_MAX_LAYERS], ln_g[ORA_MAX_LAYERS], ln_b[ORA_MAX_LAYERS];
+  int64_t proj_w, proj_b, total;
 } ora_offsets;
 
+/* Layer l: kernel [k][k][c_in][c_out], bias [c_out], then (ACE conv blocks) gamma and beta
+ * [c_out] of the layer normalisation; then proj_w [c_last][2Ne], proj_b [2Ne]. */
 static ora_offsets offsets_of(const ora_model *m) {
   ora_offsets o;
   int64_t N = (int64_t)m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn;
   int64_t p = 0;
   o.embed = p; p += (m->per_site_embed ? N : 1) * 4 * h;
   for (int l = 0; l < m->n_layers; ++l) {
-    o.kernel[l] = p; p += (int64_t)m->ksize[l] * m->ksize[l] * h * h;
-    o.bias[l] = p; p += h;
+    const int64_t ci = width_in(m, l), co = width_out(m, l);
+    o.kernel[l] = p; p += (int64_t)m->ksize[l] * m->ksize[l] * ci * co;
+    o.bias[l] = p; p += co;
+    o.ln_g[l] = o.ln_b[l] = -1;
+    if (has_ln(m, l)) {
+      o.ln_g[l] = p; p += co;
+      o.ln_b[l] = p; p += co;
+    }
   }
-  o.proj_w = p; p += h * 2 * Ne;
+  o.proj_w = p; p += (int64_t)width_last(m) * 2 * Ne;
   o.proj_b = p; p += 2 * Ne;
   o.total = p;
   return o;
@@ -133,38 +170,53 @@ static double act_df(int act, double z) {
 }
 
 /* ------------------------------------------------------------------------------------
- * Network forward (Sec. II.B). H has (L+1) layers of [N][h]; Z (optional) holds the
- * pre-activation of every layer [L][N][h].
+ * Network forward (Sec. II.B; ACE blocks of Eq. ACE). H holds L+1 layers of [N][hmax]
+ * (row stride hmax = width_max, layer l using its first width entries); Z (optional, SCALE
+ * only) holds the pre-activation of every layer [L][N][h].
  *   H0_i = E_i[n_i]
- *   H(l+1)_i = res_l * H(l)_i + act( b_l + sum_{offset d} sum_c' H(l)_{i+d}[c'] K_l[d][c'][.] )
+ *   u_i = res_l * H(l)_i + act( b_l + sum_{offset d} sum_c' H(l)_{i+d}[c'] K_l[d][c'][.] )
+ *   H(l+1)_i = u_i, or LN(u_i) for an ACE conv block:
+ *     mean = sum_c u_i[c] / C, var = sum_c (u_i[c] - mean)^2 / C,
+ *     H(l+1)_i[c] = (u_i[c] - mean) / sqrt(var + eps) * gamma_l[c] + beta_l[c].
  * A site-wise layer is the k = 1 case.
  * ------------------------------------------------------------------------------------ */
 static void forward(const ora_model *m, const int8_t *occ, double *H, double *Z) {
-  const int N = m->Lx * m->Ly, h = m->h;
+  const int N = m->Lx * m->Ly, h = m->h, hs = width_max(m);
   const ora_offsets off = offsets_of(m);
   const double *P = m->params;
   for (int i = 0; i < N; ++i) {
     const double *e = P + off.embed + ((m->per_site_embed ? (int64_t)i * 4 : 0) + occ[i]) * h;
-    for (int c = 0; c < h; ++c) H[(int64_t)i * h + c] = e[c];
+    for (int c = 0; c < h; ++c) H[(int64_t)i * hs + c] = e[c];
   }
   for (int l = 0; l < m->n_layers; ++l) {
-    const double *in = H + (int64_t)l * N * h;
-    double *out = H + (int64_t)(l + 1) * N * h;
-    const int k = m->ksize[l], r = (k - 1) / 2;
+    const double *in = H + (int64_t)l * N * hs;
+    double *out = H + (int64_t)(l + 1) * N * hs;
+    const int k = m->ksize[l], r = (k - 1) / 2, ci_n = width_in(m, l), co_n = width_out(m, l);
     const double *K = P + off.kernel[l];
     const double *b = P + off.bias[l];
     for (int i = 0; i < N; ++i) {
-      for (int co = 0; co < h; ++co) {
+      for (int co = 0; co < co_n; ++co) {
         double z = b[co];
         for (int ky = 0; ky < k; ++ky)
           for (int kx = 0; kx < k; ++kx) {
             int j = site_offset(m, i, kx - r, ky - r);
             if (j < 0) continue; /* zero padding on open edges */
-            const double *w = K + ((int64_t)(ky * k + kx) * h) * h;
-            for (int ci = 0; ci < h; ++ci) z += in[(int64_t)j * h + ci] * w[(int64_t)ci * h + co];
+            const double *w = K + ((int64_t)(ky * k + kx) * ci_n) * co_n;
+            for (int ci = 0; ci < ci_n; ++ci) z += in[(int64_t)j * hs + ci] * w[(int64_t)ci * co_n + co];
           }
         if (Z) Z[((int64_t)l * N + i) * h + co] = z;
-        out[(int64_t)i * h + co] = (m->residual[l] ? in[(int64_t)i * h + co] : 0.0) + act_f(m->act, z);
+        out[(int64_t)i * hs + co] = (m->residual[l] ? in[(int64_t)i * hs + co] : 0.0) + act_f(m->act, z);
+      }
+      if (has_ln(m, l)) {
+        double *u = out + (int64_t)i * hs;
+        double mean = 0.0, var = 0.0;
+        for (int c = 0; c < co_n; ++c) mean += u[c];
+        mean /= co_n;
+        for (int c = 0; c < co_n; ++c) var += (u[c] - mean) * (u[c] - mean);
+        var /= co_n;
+        const double inv = 1.0 / sqrt(var + m->ln_eps);
+        const double *g = P + off.ln_g[l], *be = P + off.ln_b[l];
+        for (int c = 0; c < co_n; ++c) u[c] = (u[c] - mean) * inv * g[c] + be[c];
       }
     }
   }
@@ -172,7 +224,7 @@ static void forward(const ora_model *m, const int8_t *occ, double *H, double *Z)
 
 /* Orbital matrix M [2N][Ne] from the last-layer features (Sec. II.B "Orbital Projection"). */
 static void orbitals(const ora_model *m, const double *HL, double *M) {
-  const int N = m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn;
+  const int N = m->Lx * m->Ly, h = width_last(m), hs = width_max(m), Ne = m->n_up + m->n_dn;
   const ora_offsets off = offsets_of(m);
   const double *W = m->params + off.proj_w, *bp = m->params + off.proj_b;
   for (int s = 0; s < 2; ++s)
@@ -180,7 +232,7 @@ static void orbitals(const ora_model *m, const double *HL, double *M) {
       const int o = s * N + i;
       for (int k = 0; k < Ne; ++k) {
         double v = m->M0[(int64_t)o * Ne + k] + bp[s * Ne + k];
-        for (int c = 0; c < h; ++c) v += HL[(int64_t)i * h + c] * W[(int64_t)c * 2 * Ne + s * Ne + k];
+        for (int c = 0; c < h; ++c) v += HL[(int64_t)i * hs + c] * W[(int64_t)c * 2 * Ne + s * Ne + k];
         M[(int64_t)o * Ne + k] = v;
       }
     }
@@ -248,9 +300,9 @@ typedef struct {
 } ora_ws;
 
 static ora_ws ws_alloc(const ora_model *m) {
-  const int N = m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn;
+  const int N = m->Lx * m->Ly, hs = width_max(m), Ne = m->n_up + m->n_dn;
   ora_ws w;
-  w.H = (double *)malloc(sizeof(double) * (int64_t)(m->n_layers + 1) * N * h);
+  w.H = (double *)malloc(sizeof(double) * (int64_t)(m->n_layers + 1) * N * hs);
   w.M = (double *)malloc(sizeof(double) * (int64_t)2 * N * Ne);
   w.Phi = (double *)malloc(sizeof(double) * (int64_t)Ne * Ne);
   w.orbs = (int *)malloc(sizeof(int) * 2 * N);
@@ -271,7 +323,7 @@ static int has_double(const ora_model *m, const int8_t *occ) {
  * sets sign = 0 for configurations outside the model's space (wrong particle numbers, or
  * double occupancy under the Gutzwiller projection of the t-J model). */
 static int amplitude(const ora_model *m, const int8_t *occ, ora_ws *w, double *logabs, int *sign) {
-  const int N = m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn;
+  const int N = m->Lx * m->Ly, hs = width_max(m), Ne = m->n_up + m->n_dn;
   int nu = 0, nd = 0;
   for (int i = 0; i < N; ++i) { nu += occ[i] & 1; nd += (occ[i] >> 1) & 1; }
   if (nu != m->n_up || nd != m->n_dn || (m->model == 1 && has_double(m, occ))) {
@@ -279,7 +331,7 @@ static int amplitude(const ora_model *m, const int8_t *occ, ora_ws *w, double *l
     return 0;
   }
   forward(m, occ, w->H, NULL);
-  orbitals(m, w->H + (int64_t)m->n_layers * N * h, w->M);
+  orbitals(m, w->H + (int64_t)m->n_layers * N * hs, w->M);
   int n = occupied(m, occ, w->orbs);
   for (int a = 0; a < n; ++a)
     memcpy(w->Phi + (int64_t)a * Ne, w->M + (int64_t)w->orbs[a] * Ne, sizeof(double) * Ne);
@@ -303,17 +355,19 @@ int ora_log_psi(const ora_model *m, int B, const int8_t *occ, double *logabs, in
   return 0;
 }
 
-/* Features of the last layer [B][N][h] and orbital matrices [B][2N][Ne]. */
+/* Features of the last layer [B][N][c_last] and orbital matrices [B][2N][Ne]. */
 int ora_orbitals(const ora_model *m, int B, const int8_t *occ, double *HL_out, double *M_out) {
-  const int N = m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn;
+  const int N = m->Lx * m->Ly, h = width_last(m), hs = width_max(m), Ne = m->n_up + m->n_dn;
 #pragma omp parallel
   {
     ora_ws w = ws_alloc(m);
 #pragma omp for schedule(dynamic)
     for (int b = 0; b < B; ++b) {
       forward(m, occ + (int64_t)b * N, w.H, NULL);
-      const double *HL = w.H + (int64_t)m->n_layers * N * h;
-      if (HL_out) memcpy(HL_out + (int64_t)b * N * h, HL, sizeof(double) * N * h);
+      const double *HL = w.H + (int64_t)m->n_layers * N * hs;
+      if (HL_out)
+        for (int i = 0; i < N; ++i)
+          memcpy(HL_out + ((int64_t)b * N + i) * h, HL + (int64_t)i * hs, sizeof(double) * h);
       if (M_out) orbitals(m, HL, M_out + (int64_t)b * 2 * N * Ne);
     }
     ws_free(&w);
@@ -321,7 +375,8 @@ int ora_orbitals(const ora_model *m, int B, const int8_t *occ, double *HL_out, d
   return 0;
 }
 
-/* All layers of the forward pass for one configuration: [(L+1)][N][h]. */
+/* All layers of the forward pass for one configuration: [(L+1)][N][hmax], layer l in the
+ * first entries of each row (hmax = the widest layer). */
 int ora_features(const ora_model *m, const int8_t *occ, double *H_out) {
   forward(m, occ, H_out, NULL);
   return 0;
@@ -761,6 +816,7 @@ static void grad_one(const ora_model *m, const int8_t *occ, double *g, double *H
 int ora_grad_logpsi(const ora_model *m, int B, const int8_t *occ, double *grad) {
   const int N = m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn, L = m->n_layers;
   const int64_t P = ora_param_count(m);
+  if (m->family != 0) return -1; /* the backward pass covers the SCALE family */
 #pragma omp parallel
   {
     double *H = (double *)malloc(sizeof(double) * (int64_t)(L + 1) * N * h);

@@ -33,6 +33,8 @@ class _Model(ctypes.Structure):
         ("n_layers", ctypes.c_int32), ("h", ctypes.c_int32), ("act", ctypes.c_int32),
         ("per_site_embed", ctypes.c_int32),
         ("ksize", ctypes.c_int32 * MAX_LAYERS), ("residual", ctypes.c_int32 * MAX_LAYERS),
+        ("family", ctypes.c_int32), ("n_conv", ctypes.c_int32), ("h_mlp", ctypes.c_int32),
+        ("ln_eps", ctypes.c_double),
         ("params", ctypes.POINTER(ctypes.c_double)), ("M0", ctypes.POINTER(ctypes.c_double)),
     ]
 
@@ -111,6 +113,13 @@ class Model:
         for l in range(self.L):
             s.ksize[l] = int(d["ksize"][l])
             s.residual[l] = int(d["residual"][l])
+        s.family = int(d.get("family", 0))
+        s.n_conv = int(d.get("n_conv", 0))
+        s.h_mlp = int(d.get("h_mlp", 0)) or self.h
+        s.ln_eps = float(d.get("ln_eps", 1e-5))
+        ace = s.family == 1 and self.L > s.n_conv
+        self.h_last = s.h_mlp if ace else self.h
+        self.h_max = max(self.h, self.h_last)
         s.params = self.params.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         s.M0 = self.M0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.s = s
@@ -136,14 +145,14 @@ class Model:
     def orbitals(self, occ: np.ndarray):
         occ = np.ascontiguousarray(occ, dtype=np.int8)
         B = occ.shape[0]
-        HL = np.zeros((B, self.N, self.h))
+        HL = np.zeros((B, self.N, self.h_last))
         M = np.zeros((B, 2 * self.N, self.Ne))
         _load().ora_orbitals(ctypes.byref(self.s), B, occ.ctypes.data, HL.ctypes.data, M.ctypes.data)
         return HL, M
 
     def features(self, occ1: np.ndarray) -> np.ndarray:
         occ1 = np.ascontiguousarray(occ1, dtype=np.int8)
-        H = np.zeros((self.L + 1, self.N, self.h))
+        H = np.zeros((self.L + 1, self.N, self.h_max))
         _load().ora_features(ctypes.byref(self.s), occ1.ctypes.data, H.ctypes.data)
         return H
 
@@ -167,7 +176,8 @@ class Model:
         occ = np.ascontiguousarray(occ, dtype=np.int8)
         B = occ.shape[0]
         g = np.zeros((B, self.P))
-        _load().ora_grad_logpsi(ctypes.byref(self.s), B, occ.ctypes.data, g.ctypes.data)
+        if _load().ora_grad_logpsi(ctypes.byref(self.s), B, occ.ctypes.data, g.ctypes.data) != 0:
+            raise NotImplementedError("the oracle's backward pass covers the SCALE family")
         return g
 
     def connected(self, occ1: np.ndarray):

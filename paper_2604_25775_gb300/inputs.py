@@ -16,6 +16,10 @@ Parameter layout (flat, float64, in this order; the C header documents the same 
   for each layer l:  kernel [k_l][k_l][h][h] (ky, kx, c_in, c_out), bias [h]
   proj_w  [h][2*Ne]   columns [0,Ne) build rows (i, up), [Ne, 2Ne) rows (i, down)
   proj_b  [2*Ne]
+The ACE family (Eq. ACE) uses the same order with per-layer widths: layers [0, n_conv) are
+conv blocks h -> h followed by ln_gamma [h] and ln_beta [h] of the layer normalisation;
+the site-wise layers after them map h -> h_mlp, then h_mlp -> h_mlp; proj_w is
+[h_mlp][2*Ne]. The layer-normalisation gains are drawn as 1 + N(0, scale^2).
 """
 from __future__ import annotations
 
@@ -30,6 +34,8 @@ MODEL_TJ = 1
 MODEL_HUBBARD_PH = 2  # Hubbard after the particle-hole transformation of the down spins
 ACT_TANH = 0
 ACT_SILU = 1
+FAMILY_SCALE = 0
+FAMILY_ACE = 1
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_MIXED_BF16 = 2
@@ -63,6 +69,10 @@ class Problem:
     precision: int = PREC_FP64
     refresh_every: int = 64
     drift_tol: float = 1e-4
+    family: int = FAMILY_SCALE
+    n_conv: int = 0       # ACE: number of conv blocks with layer normalisation
+    h_mlp: int = 0        # ACE: width of the site-wise layers (0 = h)
+    ln_eps: float = 1e-5  # ACE: layer-normalisation epsilon
 
     @property
     def N(self) -> int:
@@ -91,15 +101,37 @@ def scale_layout(L: int, ksize_first: int = 3, conv_residual: int = 1):
     return ks, rs
 
 
+def ace_layout(n_conv: int, n_mlp: int, ksize: int = 3):
+    """Kernel sizes / residual flags of the ACE layout (Eq. ACE): n_conv residual k x k
+    conv blocks (each followed by a layer normalisation), then n_mlp site-wise layers."""
+    return [ksize] * n_conv + [1] * n_mlp, [1] * n_conv + [0] * n_mlp
+
+
+def layer_widths(pb: Problem, l: int):
+    """(c_in, c_out) of layer l."""
+    hm = pb.h_mlp or pb.h
+    if pb.family != FAMILY_ACE:
+        return pb.h, pb.h
+    c_out = pb.h if l < pb.n_conv else hm
+    c_in = pb.h if l <= pb.n_conv else hm
+    return c_in, c_out
+
+
 def param_shapes(pb: Problem) -> List[tuple]:
     """(name, shape) of every parameter tensor in flat-vector order."""
     N, h, Ne = pb.N, pb.h, pb.Ne
     shapes = [("embed", (N, 4, h) if pb.per_site_embed else (4, h))]
+    c_last = h
     for l in range(pb.n_layers):
         k = int(pb.ksize[l])
-        shapes.append((f"kernel{l}", (k, k, h, h)))
-        shapes.append((f"bias{l}", (h,)))
-    shapes.append(("proj_w", (h, 2 * Ne)))
+        ci, co = layer_widths(pb, l)
+        shapes.append((f"kernel{l}", (k, k, ci, co)))
+        shapes.append((f"bias{l}", (co,)))
+        if pb.family == FAMILY_ACE and l < pb.n_conv:
+            shapes.append((f"ln_gamma{l}", (co,)))
+            shapes.append((f"ln_beta{l}", (co,)))
+        c_last = co
+    shapes.append(("proj_w", (c_last, 2 * Ne)))
     shapes.append(("proj_b", (2 * Ne,)))
     return shapes
 
@@ -120,7 +152,8 @@ def param_offsets(pb: Problem) -> dict:
 def random_params(pb: Problem, seed: int, scale: float = 0.05) -> np.ndarray:
     """Every learnable entry i.i.d. N(0, scale^2) from PCG64(seed), tensors in layout order."""
     rng = np.random.default_rng(seed)
-    parts = [rng.normal(0.0, scale, size=int(np.prod(s))) for _, s in param_shapes(pb)]
+    parts = [rng.normal(0.0, scale, size=int(np.prod(s))) + (1.0 if name.startswith("ln_gamma") else 0.0)
+             for name, s in param_shapes(pb)]
     return np.concatenate(parts).astype(np.float64)
 
 
@@ -338,6 +371,22 @@ def workload(name: str) -> Problem:
         ks, rs = scale_layout(4)
         return Problem(8, 8, 1, 1, 28, 36, MODEL_HUBBARD_PH, 1.0, 0.0, -4.0, 0.0, 4, 16, ks, rs,
                        ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+    if name == "ace4x4":  # 4x4 torus, 7+7, 3 conv blocks + 2 site-wise layers, h 8 -> 12, FP64
+        ks, rs = ace_layout(3, 2)
+        return Problem(4, 4, 1, 1, 7, 7, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 5, 8, ks, rs,
+                       ACT_SILU, 1, PREC_FP64, 64, 1e-10, FAMILY_ACE, 3, 12)
+    if name == "ace8x8":  # 8x8 torus, 28+28, 16 conv blocks h=48, 2 site-wise layers h=64, mixed
+        ks, rs = ace_layout(16, 2)
+        return Problem(8, 8, 1, 1, 28, 28, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 18, 48, ks, rs,
+                       ACT_SILU, 1, PREC_MIXED, 64, 1e-4, FAMILY_ACE, 16, 64)
+    if name == "ace16x16":  # Table tab:model ACE: 16 conv blocks h=144, 2 site-wise layers h=256
+        ks, rs = ace_layout(16, 2)
+        return Problem(16, 16, 1, 1, 112, 112, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 18, 144, ks, rs,
+                       ACT_SILU, 1, PREC_MIXED, 64, 1e-4, FAMILY_ACE, 16, 256)
+    if name == "ace16x4":  # ACE on the periodic 16x4 lattice of the symmetry study, t'=0, 28+28
+        ks, rs = ace_layout(16, 2)
+        return Problem(16, 4, 1, 1, 28, 28, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 18, 144, ks, rs,
+                       ACT_SILU, 1, PREC_MIXED, 64, 1e-4, FAMILY_ACE, 16, 256)
     if name == "tj16x16":
         ks, rs = scale_layout(6)
         return Problem(16, 16, 1, 1, 112, 112, MODEL_TJ, 1.0, 0.0, 0.0, 0.4, 6, 32, ks, rs,
@@ -355,7 +404,7 @@ def workload(name: str) -> Problem:
 
 WORKLOAD_INDEX = {"hubbard4x4": 0, "hubbard8x8": 1, "hubbard16x16": 2, "cylinder16x4": 3,
                   "tj8x8": 4, "tj16x16": 4, "hubbard32x32": 4, "tj32x32": 4,
-                  "hubbard_ph8x8": 5}
+                  "hubbard_ph8x8": 5, "ace4x4": 6, "ace8x8": 6, "ace16x16": 6, "ace16x4": 6}
 
 
 def workload_seeds(name: str):
