@@ -72,6 +72,15 @@ typedef enum {
  * nearest-neighbour bonds, so t' must be 0. */
 enum { SCALE_MODEL_HUBBARD = 0, SCALE_MODEL_TJ = 1, SCALE_MODEL_HUBBARD_PH = 2 };
 enum { SCALE_ACT_TANH = 0, SCALE_ACT_SILU = 1 };
+/* Network family. SCALE (Sec. II.B): one k x k residual conv then site-wise layers, all
+ * at width h; every entry point. ACE (Sec. II "ACE", Eq. ACE): n_conv residual k x k conv
+ * blocks at width h, each followed by a layer normalisation of every site's channel vector
+ * (mean and biased variance over the channels, eps = ln_eps, per-channel gain and shift),
+ * then site-wise layers at width h_mlp. A local change reaches every site through the
+ * stack, so ACE has no cached update: scale_load, scale_log_psi, scale_local_energy with
+ * SCALE_PATH_FULL and scale_log_psi_sym run it; the low-rank entry points, the gradient,
+ * the server and the allocation-free call return SCALE_EUNSUPPORTED. */
+enum { SCALE_FAMILY_SCALE = 0, SCALE_FAMILY_ACE = 1 };
 enum { SCALE_PREC_FP64 = 0, SCALE_PREC_MIXED = 1, SCALE_PREC_MIXED_BF16 = 2 };
 enum { SCALE_PATH_LOWRANK = 0, SCALE_PATH_FULL = 1 };
 
@@ -98,7 +107,7 @@ typedef struct {
 /* Network shape and numerics. */
 typedef struct {
   int32_t n_layers;       /* L >= 1 */
-  int32_t h;              /* channels of every layer, 1..64 */
+  int32_t h;              /* channels of every layer, 1..64 (ACE: of the conv blocks, 1..256) */
   int32_t act;            /* SCALE_ACT_* */
   int32_t per_site_embed; /* 1: tables E_i per site (Sec. II.B); 0: one shared table */
   int32_t precision;      /* SCALE_PREC_FP64: everything FP64.
@@ -120,6 +129,11 @@ typedef struct {
                              the same call */
   int32_t ksize[SCALE_MAX_LAYERS];    /* odd kernel size per layer, 1 = site-wise */
   int32_t residual[SCALE_MAX_LAYERS]; /* 1: add the layer input (Eq. conv residual) */
+  int32_t family;         /* SCALE_FAMILY_* (0 = SCALE) */
+  int32_t n_conv;         /* ACE: layers [0, n_conv) are conv blocks (residual 1, odd ksize);
+                             layers after them are site-wise (ksize 1, residual 0) */
+  int32_t h_mlp;          /* ACE: width of the site-wise layers, 1..512 (0 = h) */
+  double ln_eps;          /* ACE: epsilon of the layer normalisation (>= 0) */
 } scale_arch;
 
 typedef struct {

@@ -48,7 +48,9 @@ class scale_arch(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int32), ("h", ctypes.c_int32), ("act", ctypes.c_int32),
                 ("per_site_embed", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refresh_every", ctypes.c_int32), ("drift_tol", ctypes.c_double),
-                ("ksize", ctypes.c_int32 * MAX_LAYERS), ("residual", ctypes.c_int32 * MAX_LAYERS)]
+                ("ksize", ctypes.c_int32 * MAX_LAYERS), ("residual", ctypes.c_int32 * MAX_LAYERS),
+                ("family", ctypes.c_int32), ("n_conv", ctypes.c_int32), ("h_mlp", ctypes.c_int32),
+                ("ln_eps", ctypes.c_double)]
 
 
 class scale_stats(ctypes.Structure):
@@ -110,6 +112,7 @@ def make_descriptors(pb: I.Problem):
     for l in range(pb.n_layers):
         a.ksize[l] = int(pb.ksize[l])
         a.residual[l] = int(pb.residual[l])
+    a.family, a.n_conv, a.h_mlp, a.ln_eps = pb.family, pb.n_conv, pb.h_mlp, pb.ln_eps
     return s, a
 
 

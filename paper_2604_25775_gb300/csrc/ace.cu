@@ -1,0 +1,482 @@
+// ace.cu -- the ACE network (Sec. II "ACE", Eq. ACE) for batches of configurations:
+//   H0_i     = E_i[n_i]
+//   H(l+1)   = LN( H(l) + SiLU(Conv_l(H(l))) )            l < n_conv (3x3, the Hamiltonian's
+//                                                          boundary conditions)
+//   H(l+1)   = act( H(l) W_l + b_l )                       site-wise layers (Eq. MLP), width h_mlp
+//   Phi[a][k] = M0[o_a][k] + proj_b[s*Ne+k] + H(L)_i . proj_w[:, s*Ne+k]   (o_a = s*N + i
+//                                                          ascending; FP64 for the LU)
+// LN normalises each site's channel vector: mean and biased variance over the channels,
+// (u - mean) / sqrt(var + eps) * gamma + beta.
+//
+// A change at one site moves the features of every site after enough blocks, so every
+// configuration -- each n' of a local energy included -- is a fresh forward (the O(N^4)
+// route of Sec. III.A). The forward is dense work: a conv block is a GEMM of
+// (configurations x sites) rows against 9 stacked h x h weights with the rows gathered
+// by neighbour offset.
+//
+// Two implementations of a layer:
+//   k_ace_mma   (mixed mode, supported widths): tensor cores, every product as three TF32
+//               products of a hi/lo split (x_hi W_hi + x_lo W_hi + x_hi W_lo, FP32
+//               accumulation, about 2^-21 relative per layer). A warp owns 16 rows and
+//               WC warps share a row group's output columns; the A operand is gathered from
+//               the neighbour sites' rows (L1/L2), the weights come as pre-split fragments.
+//               Bias, residual, activation and the layer normalisation run in the epilogue
+//               on the accumulators (a row's channels live in one lane quad when WC = 1).
+//   k_ace_layer (FP64 mode, and other widths in FP32): one warp per row, CUDA cores, the
+//               same sum order as the definition (bias, then offsets, then channels).
+#include <algorithm>
+
+#include "mlp_mma.cuh"
+#include "scale_internal.cuh"
+
+namespace scale {
+
+namespace {
+
+constexpr int kAceRowsGeneric = 8;  // rows (one warp each) per CTA of k_ace_layer
+
+template <typename T>
+struct AceNet {
+  int h, L, n_conv, act, per_site;
+  double eps;
+  int cin[kMaxLayers], cout[kMaxLayers], ks[kMaxLayers];
+  const T* embed;
+  const T* kernel[kMaxLayers];
+  const T* bias[kMaxLayers];
+  const T* ln_g[kMaxLayers];  // nullptr for the site-wise layers
+  const T* ln_b[kMaxLayers];
+  const T* proj_w;            // [c_last][2 Ne]
+  const T* proj_b;            // [2 Ne]
+  const T* M0;                // [2N][Ne]
+};
+
+// Flat layout: embed; per layer kernel [k][k][c_in][c_out], bias [c_out], and for the conv
+// blocks ln gamma [c_out], ln beta [c_out]; proj_w [c_last][2Ne]; proj_b [2Ne].
+template <typename T>
+AceNet<T> make_ace_net(const scale_ctx* c) {
+  AceNet<T> n{};
+  const scale_arch& a = c->arch;
+  n.h = c->h;
+  n.L = c->L;
+  n.n_conv = a.n_conv;
+  n.act = a.act;
+  n.per_site = a.per_site_embed;
+  n.eps = a.ln_eps;
+  const T* base = c->fp64 ? (const T*)c->params64 : (const T*)c->params32;
+  int64_t p = 0;
+  n.embed = base;
+  p += (int64_t)(a.per_site_embed ? c->N : 1) * 4 * c->h;
+  for (int l = 0; l < c->L; ++l) {
+    n.ks[l] = a.ksize[l];
+    n.cin[l] = ace_width_in(a, l);
+    n.cout[l] = ace_width_out(a, l);
+    n.kernel[l] = base + p;
+    p += (int64_t)n.ks[l] * n.ks[l] * n.cin[l] * n.cout[l];
+    n.bias[l] = base + p;
+    p += n.cout[l];
+    n.ln_g[l] = n.ln_b[l] = nullptr;
+    if (l < a.n_conv) {
+      n.ln_g[l] = base + p;
+      p += n.cout[l];
+      n.ln_b[l] = base + p;
+      p += n.cout[l];
+    }
+  }
+  n.proj_w = base + p;
+  p += (int64_t)n.cout[c->L - 1] * 2 * c->Ne;
+  n.proj_b = base + p;
+  n.M0 = c->fp64 ? (const T*)c->M0_64 : (const T*)c->M0_32;
+  return n;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// H0 rows [C][N][h] from the embedding tables.
+template <typename T>
+__global__ void k_ace_embed(int N, int h, int per_site, const T* __restrict__ embed, const int8_t* __restrict__ occ,
+                            long long total, T* __restrict__ out) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long row = q / h;
+    const int c = (int)(q - row * h);
+    const int i = (int)(row % N);
+    const int s = occ[row] & 3;
+    out[q] = embed[((size_t)(per_site ? i : 0) * 4 + s) * h + c];
+  }
+}
+
+// One layer on CUDA cores, one warp per row (configuration, site); up to 512 output
+// channels (16 per lane).
+template <typename T>
+__global__ void __launch_bounds__(32 * kAceRowsGeneric) k_ace_layer(
+    Lattice lat, const T* __restrict__ K, const T* __restrict__ bias, const T* __restrict__ gam,
+    const T* __restrict__ bet, int ks, int cin, int cout, int res, int act, double eps,
+    const T* __restrict__ in, T* __restrict__ out, long long rows) {
+  constexpr int MQ = kAceMaxHMlp / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long R = (long long)blockIdx.x * kAceRowsGeneric + warp;
+  if (R >= rows) return;  // whole warp
+  const int N = lat.N;
+  const long long cfg = R / N;
+  const int i = (int)(R - cfg * N);
+  T acc[MQ];
+#pragma unroll
+  for (int q = 0; q < MQ; ++q) {
+    const int co = lane + 32 * q;
+    acc[q] = co < cout ? bias[co] : T(0);
+  }
+  const int r = (ks - 1) / 2;
+  for (int d = 0; d < ks * ks; ++d) {
+    const int j = site_off(lat, i, d % ks - r, d / ks - r);
+    if (j < 0) continue;  // zero padding past an open edge
+    const T* x = in + ((size_t)cfg * N + j) * cin;
+    const T* w = K + (size_t)d * cin * cout;
+    for (int ci = 0; ci < cin; ++ci) {
+      const T xv = x[ci];
+      const T* wr = w + (size_t)ci * cout;
+#pragma unroll
+      for (int q = 0; q < MQ; ++q) {
+        const int co = lane + 32 * q;
+        if (co < cout) acc[q] += xv * wr[co];
+      }
+    }
+  }
+  const T* self = in + (size_t)R * cin;
+  T s = T(0);
+#pragma unroll
+  for (int q = 0; q < MQ; ++q) {
+    const int co = lane + 32 * q;
+    if (co < cout) {
+      acc[q] = (res ? self[co] : T(0)) + act_fn<T>(act, acc[q]);
+      s += acc[q];
+    }
+  }
+  if (gam) {  // layer normalisation over this site's channels
+    const T mean = warp_sum(s) / T(cout);
+    T v = T(0);
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+      const int co = lane + 32 * q;
+      if (co < cout) v += (acc[q] - mean) * (acc[q] - mean);
+    }
+    v = warp_sum(v) / T(cout);
+    const T inv = T(1) / sqrt(v + T(eps));
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+      const int co = lane + 32 * q;
+      if (co < cout) acc[q] = (acc[q] - mean) * inv * gam[co] + bet[co];
+    }
+  }
+  T* o = out + (size_t)R * cout;
+#pragma unroll
+  for (int q = 0; q < MQ; ++q) {
+    const int co = lane + 32 * q;
+    if (co < cout) o[co] = acc[q];
+  }
+}
+
+// Pre-split weight fragments of one layer, [tap][kk][nt][lane] {b0_hi, b1_hi, b0_lo, b1_lo},
+// with the k index of each 8-wide step permuted (logical t -> channel 2t, logical t+4 ->
+// channel 2t+1) so that a lane's two A entries are adjacent channels (one 8-byte load).
+__global__ void k_ace_build_frag(const float* __restrict__ K, int taps, int cin, int cout, WFrag* __restrict__ out) {
+  const int KT = cin / 8, NT = cout / 8;
+  const size_t total = (size_t)taps * KT * NT * 32;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int lane = (int)(q % 32);
+    size_t r = q / 32;
+    const int nt = (int)(r % NT);
+    r /= NT;
+    const int kk = (int)(r % KT);
+    const int d = (int)(r / KT);
+    const int g = lane >> 2, t = lane & 3;
+    const float* w = K + (size_t)d * cin * cout;
+    const float b0 = w[(size_t)(8 * kk + 2 * t) * cout + 8 * nt + g];
+    const float b1 = w[(size_t)(8 * kk + 2 * t + 1) * cout + 8 * nt + g];
+    WFrag f;
+    split_tf32(b0, f.v[0], f.v[2]);
+    split_tf32(b1, f.v[1], f.v[3]);
+    out[q] = f;
+  }
+}
+
+// One layer on the tensor cores. CTA: 8 warps = (8 / WC) row groups of 16 rows x WC column
+// groups of NTW n-tiles; cout = 8 NTW WC. LN (WC = 1 only): layer normalisation of each row
+// in the epilogue (the row's channels are spread over the 4 lanes of a quad).
+template <int NTW, int WC, bool LN>
+__global__ void __launch_bounds__(256, (NTW > 18 || NTW == 16 ? 1 : 2)) k_ace_mma(
+    Lattice lat, const WFrag* __restrict__ frag, const float* __restrict__ bias, const float* __restrict__ gam,
+    const float* __restrict__ bet, int ks, int cin, int res, int act, float eps, const float* __restrict__ in,
+    float* __restrict__ out, long long rows) {
+  static_assert(!LN || WC == 1, "the epilogue normalisation needs a row's channels in one warp");
+  constexpr int NT = NTW * WC, COUT = 8 * NT, WR = 8 / WC, ROWS = 16 * WR;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int wr = warp / WC, wc = warp % WC;
+  const int N = lat.N;
+  const long long r0 = (long long)blockIdx.x * ROWS + wr * 16 + g, r1 = r0 + 8;
+  const bool v0 = r0 < rows, v1 = r1 < rows;
+  const long long c0 = v0 ? r0 / N : 0, c1 = v1 ? r1 / N : 0;
+  const int i0 = v0 ? (int)(r0 - c0 * N) : 0, i1 = v1 ? (int)(r1 - c1 * N) : 0;
+  const int col0 = 8 * wc * NTW + 2 * t;
+
+  float acc[NTW][4];
+#pragma unroll
+  for (int j = 0; j < NTW; ++j) {
+    const float b0 = bias[col0 + 8 * j], b1 = bias[col0 + 8 * j + 1];
+    acc[j][0] = b0;
+    acc[j][1] = b1;
+    acc[j][2] = b0;
+    acc[j][3] = b1;
+  }
+  const int KT = cin / 8, rad = (ks - 1) / 2;
+  for (int d = 0; d < ks * ks; ++d) {
+    const int dx = d % ks - rad, dy = d / ks - rad;
+    const int j0 = v0 ? site_off(lat, i0, dx, dy) : -1;
+    const int j1 = v1 ? site_off(lat, i1, dx, dy) : -1;
+    const float* p0 = j0 >= 0 ? in + ((size_t)c0 * N + j0) * cin + 2 * t : nullptr;
+    const float* p1 = j1 >= 0 ? in + ((size_t)c1 * N + j1) * cin + 2 * t : nullptr;
+    const WFrag* fd = frag + (size_t)d * KT * NT * 32 + (size_t)wc * NTW * 32 + lane;
+    for (int kk = 0; kk < KT; ++kk) {
+      const float2 x0 = p0 ? __ldg(reinterpret_cast<const float2*>(p0 + 8 * kk)) : make_float2(0.f, 0.f);
+      const float2 x1 = p1 ? __ldg(reinterpret_cast<const float2*>(p1 + 8 * kk)) : make_float2(0.f, 0.f);
+      uint32_t ah[4], al[4];
+      split_tf32(x0.x, ah[0], al[0]);  // (g,   logical t)   = channel 8kk + 2t
+      split_tf32(x1.x, ah[1], al[1]);  // (g+8, logical t)
+      split_tf32(x0.y, ah[2], al[2]);  // (g,   logical t+4) = channel 8kk + 2t + 1
+      split_tf32(x1.y, ah[3], al[3]);  // (g+8, logical t+4)
+      const WFrag* fk = fd + (size_t)kk * NT * 32;
+#pragma unroll
+      for (int j = 0; j < NTW; ++j) {
+        const WFrag w = fk[j * 32];
+        mma_tf32(acc[j], ah, w.v[0], w.v[1]);
+        mma_tf32(acc[j], al, w.v[0], w.v[1]);
+        mma_tf32(acc[j], ah, w.v[2], w.v[3]);
+      }
+    }
+  }
+  // epilogue: residual + activation, then the normalisation of each row
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < NTW; ++j) {
+    const int col = col0 + 8 * j;
+    float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
+    if (res) {
+      if (v0) x0 = *reinterpret_cast<const float2*>(in + (size_t)r0 * cin + col);
+      if (v1) x1 = *reinterpret_cast<const float2*>(in + (size_t)r1 * cin + col);
+    }
+    acc[j][0] = x0.x + act_fast(act, acc[j][0]);
+    acc[j][1] = x0.y + act_fast(act, acc[j][1]);
+    acc[j][2] = x1.x + act_fast(act, acc[j][2]);
+    acc[j][3] = x1.y + act_fast(act, acc[j][3]);
+    s0 += acc[j][0] + acc[j][1];
+    s1 += acc[j][2] + acc[j][3];
+  }
+  if constexpr (LN) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+    const float m0 = s0 * (1.f / COUT), m1 = s1 * (1.f / COUT);
+    float q0 = 0.f, q1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) {
+      q0 += (acc[j][0] - m0) * (acc[j][0] - m0) + (acc[j][1] - m0) * (acc[j][1] - m0);
+      q1 += (acc[j][2] - m1) * (acc[j][2] - m1) + (acc[j][3] - m1) * (acc[j][3] - m1);
+    }
+    q0 += __shfl_xor_sync(0xffffffffu, q0, 1);
+    q0 += __shfl_xor_sync(0xffffffffu, q0, 2);
+    q1 += __shfl_xor_sync(0xffffffffu, q1, 1);
+    q1 += __shfl_xor_sync(0xffffffffu, q1, 2);
+    const float inv0 = 1.f / sqrtf(q0 * (1.f / COUT) + eps), inv1 = 1.f / sqrtf(q1 * (1.f / COUT) + eps);
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) {
+      const int col = col0 + 8 * j;
+      const float ga = gam[col], gb = gam[col + 1], ba = bet[col], bb = bet[col + 1];
+      acc[j][0] = (acc[j][0] - m0) * inv0 * ga + ba;
+      acc[j][1] = (acc[j][1] - m0) * inv0 * gb + bb;
+      acc[j][2] = (acc[j][2] - m1) * inv1 * ga + ba;
+      acc[j][3] = (acc[j][3] - m1) * inv1 * gb + bb;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NTW; ++j) {
+    const int col = col0 + 8 * j;
+    if (v0) *reinterpret_cast<float2*>(out + (size_t)r0 * COUT + col) = make_float2(acc[j][0], acc[j][1]);
+    if (v1) *reinterpret_cast<float2*>(out + (size_t)r1 * COUT + col) = make_float2(acc[j][2], acc[j][3]);
+  }
+}
+
+// Slater matrix rows of the occupied orbitals in ascending order (FP64 output); a
+// configuration with another electron count gets a zero matrix (singular).
+template <typename T>
+__global__ void k_ace_phi(Lattice lat, AceNet<T> net, int hl, const int8_t* __restrict__ occ,
+                          const T* __restrict__ HL, double* __restrict__ phi) {
+  extern __shared__ int olist[];  // [2N]
+  __shared__ int s_n;
+  const int b = blockIdx.x, N = lat.N, Ne = lat.Ne;
+  const int8_t* ob = occ + (size_t)b * N;
+  if (threadIdx.x < 32) {  // one warp lists the occupied orbitals in order
+    int n = 0;
+    for (int base = 0; base < 2 * N; base += 32) {
+      const int o = base + threadIdx.x;
+      const bool on = o < 2 * N && ((ob[o % N] >> (o / N)) & 1);
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      if (on) olist[n + __popc(m & ((1u << threadIdx.x) - 1u))] = o;
+      n += __popc(m);
+    }
+    if (threadIdx.x == 0) s_n = n;
+  }
+  __syncthreads();
+  double* P = phi + (size_t)b * Ne * Ne;
+  if (s_n != Ne) {
+    for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = 0.0;
+    return;
+  }
+  const T* Hb = HL + (size_t)b * N * hl;
+  for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) {
+    const int a = q / Ne, k = q - a * Ne;
+    const int o = olist[a], s = o / N, i = o - s * N;
+    T v = net.M0[(size_t)o * Ne + k] + net.proj_b[s * Ne + k];
+    const T* w = net.proj_w + s * Ne + k;
+    const T* x = Hb + (size_t)i * hl;
+    for (int c = 0; c < hl; ++c) v += x[c] * w[(size_t)c * 2 * Ne];
+    P[q] = (double)v;
+  }
+}
+
+// Tensor-core shape of a layer: n-tiles per warp and warps per row group, or 0.
+struct MmaPlan {
+  int ntw, wc;
+};
+
+MmaPlan plan_of(const scale_arch& a, int l) {
+  const int ci = ace_width_in(a, l), co = ace_width_out(a, l);
+  if (ci % 8 != 0) return {0, 0};
+  if (l < a.n_conv) {  // conv block with the normalisation in the epilogue
+    if (co == 48 || co == 144 || co == 192) return {co / 8, 1};
+    return {0, 0};
+  }
+  if (co == 64) return {8, 1};
+  if (co == 128) return {16, 1};
+  if (co == 256) return {16, 2};
+  return {0, 0};
+}
+
+size_t frag_layer_bytes(const scale_arch& a, int l) {
+  const size_t k = a.ksize[l];
+  return k * k * (size_t)ace_width_in(a, l) * ace_width_out(a, l) * 8;  // (ci/8)(co/8) 32 lanes x 16 B
+}
+
+template <int NTW, int WC, bool LN>
+void run_mma(cudaStream_t st, const Lattice& lat, const WFrag* frag, const float* bias, const float* g,
+             const float* be, int ks, int cin, int res, int act, float eps, const float* in, float* out,
+             long long rows) {
+  constexpr int ROWS = 16 * (8 / WC);
+  const long long blocks = (rows + ROWS - 1) / ROWS;
+  k_ace_mma<NTW, WC, LN><<<(unsigned)blocks, 256, 0, st>>>(lat, frag, bias, g, be, ks, cin, res, act, eps, in, out,
+                                                            rows);
+}
+
+bool launch_mma_layer(cudaStream_t st, const Lattice& lat, const MmaPlan& p, bool conv, const WFrag* frag,
+                      const float* bias, const float* g, const float* be, int ks, int cin, int res, int act,
+                      float eps, const float* in, float* out, long long rows) {
+#define SCALE_ACE_MMA(NTW, WC, LN) \
+  run_mma<NTW, WC, LN>(st, lat, frag, bias, g, be, ks, cin, res, act, eps, in, out, rows)
+  if (conv) {
+    if (p.ntw == 6) SCALE_ACE_MMA(6, 1, true);
+    else if (p.ntw == 18) SCALE_ACE_MMA(18, 1, true);
+    else if (p.ntw == 24) SCALE_ACE_MMA(24, 1, true);
+    else return false;
+  } else {
+    if (p.ntw == 8 && p.wc == 1) SCALE_ACE_MMA(8, 1, false);
+    else if (p.ntw == 16 && p.wc == 1) SCALE_ACE_MMA(16, 1, false);
+    else if (p.ntw == 16 && p.wc == 2) SCALE_ACE_MMA(16, 2, false);
+    else return false;
+  }
+#undef SCALE_ACE_MMA
+  return true;
+}
+
+template <typename T>
+cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64) {
+  const AceNet<T> net = make_ace_net<T>(c);
+  const int N = c->N;
+  const long long rows = (long long)C * N;
+  T* a = (T*)c->act_a;
+  T* b = (T*)c->act_b;
+  {
+    const long long total = rows * c->h;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
+    k_ace_embed<T><<<blocks, 256, 0, c->stream>>>(N, c->h, net.per_site, net.embed, occ, total, a);
+  }
+  size_t frag_off = 0;
+  for (int l = 0; l < c->L; ++l) {
+    const bool conv = l < net.n_conv;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (c->ace_mma) {
+        const MmaPlan p = plan_of(c->arch, l);
+        const WFrag* frag = (const WFrag*)((const char*)c->ace_frag + frag_off);
+        done = launch_mma_layer(c->stream, c->lat, p, conv, frag, net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l],
+                                net.cin[l], conv ? 1 : 0, net.act, (float)net.eps, a, b, rows);
+      }
+    }
+    if (!done) {
+      const long long blocks = (rows + kAceRowsGeneric - 1) / kAceRowsGeneric;
+      k_ace_layer<T><<<(unsigned)blocks, 32 * kAceRowsGeneric, 0, c->stream>>>(
+          c->lat, net.kernel[l], net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l], net.cin[l], net.cout[l],
+          conv ? 1 : 0, net.act, net.eps, a, b, rows);
+    }
+    frag_off += frag_layer_bytes(c->arch, l);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::swap(a, b);
+  }
+  const int hl = net.cout[c->L - 1];
+  k_ace_phi<T><<<C, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, a, phi64);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool ace_mma_shapes(const scale_arch& a) {
+  for (int l = 0; l < a.n_layers; ++l)
+    if (plan_of(a, l).ntw == 0) return false;
+  return true;
+}
+
+size_t ace_frag_bytes(const scale_arch& a) {
+  if (!ace_mma_shapes(a)) return 0;
+  size_t t = 0;
+  for (int l = 0; l < a.n_layers; ++l) t += frag_layer_bytes(a, l);
+  return t;
+}
+
+cudaError_t launch_ace_build(scale_ctx* c) {
+  if (!c->ace_mma) return cudaSuccess;
+  const AceNet<float> net = make_ace_net<float>(c);
+  size_t off = 0;
+  for (int l = 0; l < c->L; ++l) {
+    const int taps = net.ks[l] * net.ks[l];
+    const size_t n = (size_t)taps * (net.cin[l] / 8) * (net.cout[l] / 8) * 32;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_ace_build_frag<<<blocks, 256, 0, c->stream>>>(net.kernel[l], taps, net.cin[l], net.cout[l],
+                                                     (WFrag*)((char*)c->ace_frag + off));
+    off += frag_layer_bytes(c->arch, l);
+  }
+  return cudaGetLastError();
+}
+
+// Slater matrices (FP64) of C configurations occ[C][N] through the ACE network; the
+// activations go to the context's scratch buffers.
+cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64) {
+  if (C <= 0) return cudaSuccess;
+  if (c->fp64) return ace_forward_t<double>(c, occ, C, phi64);
+  return ace_forward_t<float>(c, occ, C, phi64);
+}
+
+}  // namespace scale

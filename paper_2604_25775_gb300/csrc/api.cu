@@ -40,7 +40,22 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
                 "on nearest-neighbour bonds only)");
   if (s->model == SCALE_MODEL_TJ && s->n_up + s->n_dn > N) return fail("t-J: more electrons than sites");
   if (a->n_layers < 1 || a->n_layers > SCALE_MAX_LAYERS) return fail("n_layers must be in [1, 32]");
-  if (a->h < 1 || a->h > kMaxH) return fail("h must be in [1, 64]");
+  if (a->family != SCALE_FAMILY_SCALE && a->family != SCALE_FAMILY_ACE) return fail("unknown network family");
+  if (a->family == SCALE_FAMILY_ACE) {
+    if (a->h < 1 || a->h > kAceMaxH) return fail("ACE: h must be in [1, 256]");
+    if (a->n_conv < 1 || a->n_conv > a->n_layers) return fail("ACE: n_conv must be in [1, n_layers]");
+    if (a->n_layers > a->n_conv && (a->h_mlp < 0 || a->h_mlp > kAceMaxHMlp))
+      return fail("ACE: h_mlp must be in [0, 512]");
+    if (!(a->ln_eps >= 0.0)) return fail("ACE: ln_eps must be >= 0");
+    for (int l = 0; l < a->n_layers; ++l) {
+      const bool conv = l < a->n_conv;
+      if (conv && a->residual[l] != 1) return fail("ACE: conv blocks carry the residual (Eq. ACE)");
+      if (!conv && (a->ksize[l] != 1 || a->residual[l] != 0))
+        return fail("ACE: layers after the conv blocks are site-wise (kernel size 1, no residual)");
+    }
+  } else if (a->h < 1 || a->h > kMaxH) {
+    return fail("h must be in [1, 64]");
+  }
   if (a->act != SCALE_ACT_TANH && a->act != SCALE_ACT_SILU) return fail("unknown activation");
   if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED && a->precision != SCALE_PREC_MIXED_BF16)
     return fail("unknown precision");
@@ -60,6 +75,13 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
 int64_t param_count(const scale_system* s, const scale_arch* a) {
   const int64_t N = (int64_t)s->Lx * s->Ly, h = a->h, Ne = s->n_up + s->n_dn;
   int64_t n = (a->per_site_embed ? N : 1) * 4 * h;
+  if (a->family == SCALE_FAMILY_ACE) {
+    for (int l = 0; l < a->n_layers; ++l) {
+      const int64_t ci = ace_width_in(*a, l), co = ace_width_out(*a, l);
+      n += (int64_t)a->ksize[l] * a->ksize[l] * ci * co + co + (l < a->n_conv ? 2 * co : 0);
+    }
+    return n + (int64_t)ace_width_out(*a, a->n_layers - 1) * 2 * Ne + 2 * Ne;
+  }
   for (int l = 0; l < a->n_layers; ++l) n += (int64_t)a->ksize[l] * a->ksize[l] * h * h + h;
   return n + h * 2 * Ne + 2 * Ne;
 }
@@ -97,18 +119,22 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   z.cap = (int)(2 * (nb_nn + nb_nnn) + (s->model == SCALE_MODEL_TJ ? nb_nn : 0));
   const size_t P = (size_t)param_count(s, a);
   const size_t k0 = a->ksize[0];
+  const bool ace = a->family == SCALE_FAMILY_ACE;
+  const size_t hmax = ace ? std::max<size_t>(h, ace_width_out(*a, a->n_layers - 1)) : h;
   size_t t = 0;
   t += P * 8 + (T == 4 ? P * 4 : 0);
   t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0) + 2 * N * Ne * T;
-  t += (a->per_site_embed ? N : 1) * 4 * k0 * k0 * h * T;
+  t += ace ? 16 : (a->per_site_embed ? N : 1) * 4 * k0 * k0 * h * T;  // KE
   t += (nb_nn + nb_nnn) * 2 * 4;
   t += (size_t)B * (N + Ne * 4 + 2 * N * 4);
-  t += (size_t)B * N * h * T * 4;          // z0, HL, act_a, act_b
-  t += (size_t)B * Ne * Ne * T;            // Binv
-  t += (size_t)B * 2 * Ne * h * T;         // Pt
+  t += ace ? 32 : (size_t)B * N * h * T * 2;  // z0, HL
+  t += (size_t)B * N * hmax * T * 2;          // act_a, act_b
+  t += ace ? 16 : (size_t)B * Ne * Ne * T;    // Binv
+  t += ace ? 16 : (size_t)B * 2 * Ne * h * T; // Pt
   t += (size_t)B * (8 + 4 + 4 + 4 + 8 + 4 + 4 + 8 + 4 + 8);
   t += (size_t)B * Ne * Ne * 8;            // Phi64
-  t += (size_t)B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T;  // commit scratch
+  t += ace ? 16 : (size_t)B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T;  // commit scratch
+  if (ace && T == 4) t += ace_frag_bytes(*a);
   t += (size_t)B * (N + 4 + 8 + 4);        // full-path chunk
   t += (size_t)B * z.cap * (8 + 8 + 16);   // full-path coefficients, terms, moves
   t += (size_t)(B + 1) * 8 + 64;
@@ -147,7 +173,7 @@ void free_all(scale_ctx* c) {
                   c->commits, c->drift, c->Phi64, c->act_a, c->act_b, c->list, c->list_count, c->stat_dev,
                   c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_terms, c->full_moves,
                   c->commit_scratch, c->la_tmp, c->sg_tmp, c->full_la, c->full_sg, c->full_diag,
-                  c->full_offsets, c->grad_scratch, c->wfrag};
+                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -166,6 +192,10 @@ scale_status check_loaded(scale_ctx* c) {
 }
 
 scale_status require_lowrank(scale_ctx* c) {
+  if (c->ace) {
+    c->err = "the ACE network has no cached update (Sec. II \"ACE\"): use the full-recompute path";
+    return SCALE_EUNSUPPORTED;
+  }
   if (!c->lowrank_ok) {
     c->err = "low-rank path needs the SCALE layer layout: layer 0 with kernel size 1 or 3 and "
              "site-wise layers (kernel size 1) after it; use the full-recompute path";
@@ -231,10 +261,13 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   c->budget = hbm_budget_bytes;
   c->lat = Lattice{sys->Lx, sys->Ly, sys->pbc_x, sys->pbc_y, c->N, sys->n_up, sys->n_dn, c->Ne, sys->model,
                    sys->t, sys->tp, sys->U, sys->J};
-  c->lowrank_ok = c->k0 <= 3;
+  c->ace = arch->family == SCALE_FAMILY_ACE;
+  c->lowrank_ok = !c->ace && c->k0 <= 3;
   for (int l = 1; l < c->L; ++l) c->lowrank_ok = c->lowrank_ok && arch->ksize[l] == 1;
   c->hpad = c->h <= 16 ? 16 : (c->h <= 32 ? 32 : 64);
   c->use_mma = !c->fp64 && c->lowrank_ok && c->h == c->hpad;
+  c->hmax = c->ace ? std::max(c->h, ace_width_out(*arch, c->L - 1)) : c->h;
+  c->ace_mma = c->ace && !c->fp64 && ace_mma_shapes(*arch);
   std::vector<int32_t> bonds = make_bonds(c->lat, &c->nb_nn, &c->nb_nnn);
   c->max_moves = 2 * (c->nb_nn + c->nb_nnn) + (sys->model == SCALE_MODEL_TJ ? c->nb_nn : 0);
   c->full_chunk = max_batch;
@@ -250,28 +283,30 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A(&c->M0_64, 2 * N * Ne * 8);
   if (!c->fp64) A(&c->M0_32, 2 * N * Ne * 4);
   A((char**)&c->M0b, 2 * N * Ne * T);
-  A((char**)&c->KE, Ns * 4 * c->k0 * c->k0 * h * T);
+  const bool ace = c->ace;
+  const size_t hmax = c->hmax;
+  A((char**)&c->KE, ace ? 16 : Ns * 4 * c->k0 * c->k0 * h * T);
   A(&c->bonds, std::max<size_t>(bonds.size(), 2) * 4);
   A(&c->occ, B * N);
   A(&c->orb_of_slot, B * Ne * 4);
   A(&c->slot_of_orb, B * 2 * N * 4);
-  A((char**)&c->z0, B * N * h * T);
-  A((char**)&c->HL, B * N * h * T);
-  A((char**)&c->Binv, B * Ne * Ne * T);
-  A((char**)&c->Pt, B * 2 * Ne * h * T);
+  A((char**)&c->z0, ace ? 16 : B * N * h * T);
+  A((char**)&c->HL, ace ? 16 : B * N * h * T);
+  A((char**)&c->Binv, ace ? 16 : B * Ne * Ne * T);
+  A((char**)&c->Pt, ace ? 16 : B * 2 * Ne * h * T);
   A(&c->logabs, B * 8);
   A(&c->sign_slot, B * 4);
   A(&c->status, B * 4);
   A(&c->commits, B * 4);
   A(&c->drift, B * 8);
   A(&c->Phi64, B * Ne * Ne * 8);
-  A((char**)&c->act_a, B * N * h * T);
-  A((char**)&c->act_b, B * N * h * T);
+  A((char**)&c->act_a, B * N * hmax * T);
+  A((char**)&c->act_b, B * N * hmax * T);
   A(&c->list, B * 4);
   A(&c->list_count, 16);
   A(&c->stat_dev, 4 * 8);
   A(&c->move_count, B * 4);
-  A((char**)&c->commit_scratch, B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T);
+  A((char**)&c->commit_scratch, ace ? 16 : B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T);
   A(&c->la_tmp, B * 8);
   A(&c->sg_tmp, B * 4);
   A(&c->full_occ, B * N);
@@ -284,6 +319,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A(&c->full_terms, B * cap * 8);
   A(&c->full_moves, B * cap * 16);
   if (c->use_mma) A((char**)&c->wfrag, (size_t)c->L * (c->hpad / 8) * (c->hpad / 8) * 32 * 16);
+  if (c->ace_mma) A((char**)&c->ace_frag, ace_frag_bytes(*arch));
   if (e != cudaSuccess) {
     free_all(c);
     delete c;
@@ -315,6 +351,12 @@ scale_status scale_set_params(scale_ctx* c, const double* params, const double* 
     k_convert<float, double><<<1024, 256, 0, c->stream>>>(c->M0_64, c->M0_32, 2 * N * Ne);
     SCALE_TRY(c, cudaGetLastError());
   }
+  if (c->ace) {  // the ACE network has no cached update: only its tensor-core fragments
+    SCALE_TRY(c, launch_ace_build(c));
+    c->params_set = true;
+    c->B = 0;
+    return SCALE_OK;
+  }
   SCALE_TRY(c, launch_build_ke(c));
   SCALE_TRY(c, launch_build_wfrag(c));
   if (c->fp64) {
@@ -345,8 +387,12 @@ scale_status scale_load(scale_ctx* c, const int8_t* occ, int32_t B, int32_t* sam
   SCALE_TRY(c, cudaMemsetAsync(c->drift, 0, (size_t)B * 8, c->stream));
   SCALE_TRY(c, launch_slots(c, c->occ, B));
   SCALE_TRY(c, launch_forward(c, c->occ, B, nullptr, true, c->Phi64));
-  SCALE_TRY(c, launch_gj(c, c->Phi64, c->Ne, B, nullptr, true, c->fp64, c->Binv, c->logabs, c->sign_slot, c->status));
-  SCALE_TRY(c, launch_projector(c, B, nullptr));
+  if (c->ace) {  // log|det| and sign only (FP64 LU); nothing is cached for updates
+    SCALE_TRY(c, launch_gj(c, c->Phi64, c->Ne, B, nullptr, false, true, nullptr, c->logabs, c->sign_slot, c->status));
+  } else {
+    SCALE_TRY(c, launch_gj(c, c->Phi64, c->Ne, B, nullptr, true, c->fp64, c->Binv, c->logabs, c->sign_slot, c->status));
+    SCALE_TRY(c, launch_projector(c, B, nullptr));
+  }
   if (sample_status)
     SCALE_TRY(c, cudaMemcpyAsync(sample_status, c->status, (size_t)B * 4, cudaMemcpyDeviceToDevice, c->stream));
   c->stats.batch = B;
@@ -438,6 +484,7 @@ scale_status scale_log_psi_sym(scale_ctx* c, int32_t G, const int32_t* perms, co
 scale_status scale_refresh(scale_ctx* c, int32_t force_all) {
   scale_status s = check_loaded(c);
   if (s != SCALE_OK) return s;
+  if ((s = require_lowrank(c)) != SCALE_OK) return s;
   SCALE_TRY(c, refresh_samples(c, force_all != 0));
   return SCALE_OK;
 }
@@ -446,6 +493,10 @@ scale_status scale_grad_logpsi(scale_ctx* c, double* grad, int32_t recompute) {
   scale_status s = check_loaded(c);
   if (s != SCALE_OK) return s;
   if (!grad) return SCALE_EINVAL;
+  if (c->ace) {
+    c->err = "the per-sample gradient covers the SCALE family";
+    return SCALE_EUNSUPPORTED;
+  }
   SCALE_TRY(c, launch_grad(c, grad, recompute));
   return SCALE_OK;
 }

@@ -400,6 +400,10 @@ cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* lis
 // Forward every listed sample of occ; keep_cache writes z0 / HL of the context.
 cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, bool keep_cache,
                            double* phi_out, const int32_t* count) {
+  if (c->ace) {  // ACE: no cached features; whole batches only (no list)
+    if (list || count || !phi_out) return cudaErrorInvalidValue;
+    return launch_ace_forward(c, occ, B, phi_out);
+  }
   if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, nullptr, count);
   return forward_t<float>(c, occ, B, list, keep_cache, phi_out, nullptr, count);
 }
@@ -407,6 +411,7 @@ cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t
 // Forward for the full-recompute path: Slater matrices of B configurations into phi
 // (double in FP64 mode, float in mixed mode); features go to the scratch buffers.
 cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, void* phi) {
+  if (c->ace) return launch_ace_forward(c, occ, B, (double*)phi);  // FP64 Slater matrices
   if (c->fp64) return forward_t<double>(c, occ, B, nullptr, false, (double*)phi, nullptr, nullptr);
   return forward_t<float>(c, occ, B, nullptr, false, nullptr, phi, nullptr);
 }

@@ -173,7 +173,7 @@ cudaError_t launch_eloc_full(scale_ctx* c, double* eloc) {
                                             c->full_owner);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_forward_phi(c, c->full_occ, G, c->Phi64)) != cudaSuccess) return e;
-    if (c->fp64)
+    if (c->fp64 || c->ace)  // ACE: FP64 determinants in both modes
       e = launch_gj(c, c->Phi64, Ne, G, nullptr, false, true, nullptr, c->full_la, c->full_sg, nullptr);
     else
       e = launch_det_f32(c, reinterpret_cast<float*>(c->Phi64), Ne, G, c->full_la, c->full_sg);

@@ -51,6 +51,7 @@ extern "C" scale_status scale_log_psi_noalloc(const scale_system* sys, const sca
   if (!sys || !arch || !params || !M0 || !occ || !logabs || !sign || B < 1) return SCALE_EINVAL;
   const int64_t P = scale_param_count(sys, arch);
   if (P < 0) return SCALE_EINVAL;
+  if (arch->family != SCALE_FAMILY_SCALE) return SCALE_EUNSUPPORTED;  // no ACE working set here
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SCALE_ECUDA;
   unsigned char* base = nullptr;

@@ -182,10 +182,29 @@ struct scale_ctx {
   double* full_terms = nullptr;    // [B][max_moves]
   int32_t* full_moves = nullptr;   // [B][max_moves][4]
 
+  // ACE family (full-recompute network, no cached update)
+  bool ace = false;
+  bool ace_mma = false;     // mixed mode with tensor-core shapes for every layer
+  int hmax = 0;             // widest layer (activation buffers are [B][N][hmax])
+  void* ace_frag = nullptr; // TF32 hi/lo mma fragments of every ACE layer
+
   scale_stats stats{};
 };
 
 namespace scale {
+
+// ACE widths: the conv blocks keep h, the site-wise layers after them have h_mlp.
+constexpr int kAceMaxH = 256;
+constexpr int kAceMaxHMlp = 512;
+inline int ace_width_out(const scale_arch& a, int l) {
+  return l < a.n_conv ? a.h : (a.h_mlp > 0 ? a.h_mlp : a.h);
+}
+inline int ace_width_in(const scale_arch& a, int l) { return l == 0 ? a.h : ace_width_out(a, l - 1); }
+// Bytes of the tensor-core fragments of every ACE layer (0 when a shape has none).
+size_t ace_frag_bytes(const scale_arch& a);
+bool ace_mma_shapes(const scale_arch& a);
+cudaError_t launch_ace_build(scale_ctx* c);
+cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64);
 
 // kernels (launch wrappers), each enqueued on ctx->stream
 // count (optional, device): sample_list is compacted, its first *count entries are used

@@ -27,7 +27,8 @@ def test_library_exports_every_declared_symbol():
     assert set(syms) == set(Bd.EXPORTED)
 
 
-@pytest.mark.parametrize("name", ["hubbard4x4", "hubbard16x16", "cylinder16x4", "tj8x8", "hubbard32x32"])
+@pytest.mark.parametrize("name", ["hubbard4x4", "hubbard16x16", "cylinder16x4", "tj8x8", "hubbard32x32",
+                                  "ace4x4", "ace8x8", "ace16x16"])
 def test_param_count_matches_layout(name):
     pb = I.workload(name)
     assert Bd.scale_param_count(pb) == I.param_count(pb)
@@ -44,6 +45,12 @@ def test_invalid_descriptors_rejected_on_host():
         I.workload("hubbard4x4").replace(refresh_every=0),
         I.workload("hubbard_ph8x8").replace(tp=-0.2),    # PHT keeps its form on NN bonds only
         I.workload("hubbard4x4").replace(model=3),       # unknown model
+        I.workload("hubbard4x4").replace(family=2),      # unknown network family
+        I.workload("ace4x4").replace(n_conv=0),          # ACE without conv blocks
+        I.workload("ace4x4").replace(h=300),             # ACE conv width above 256
+        I.workload("ace4x4").replace(residual=[1, 1, 0, 0, 0]),  # ACE conv block without residual
+        I.workload("ace4x4").replace(ksize=[3, 3, 3, 3, 1]),     # ACE site-wise layer with a stencil
+        I.workload("ace4x4").replace(ln_eps=-1.0),
     ]
     for pb in bad:
         assert Bd.scale_param_count(pb) == -1

@@ -1,0 +1,129 @@
+"""GPU parity of the ACE network (Sec. II "ACE", Eq. ACE) against the FP64 oracle, through
+the C ABI: log|psi| at load, the full-recompute local energy (every psi(n') a fresh forward
+and FP64 LU) and the symmetry projection.
+
+Tolerances as for SCALE: FP64 <= 1e-10 relative (cond(Phi) < 1e6), mixed (TF32x3 tensor-core
+layers, FP32 activations, FP64 Slater matrices and LU) <= 1e-4 (cond < 1e3, 1e4 at 16x16), and
+every sample within cond * c * u beyond those bands. A mixed local energy is compared against
+its term scale |diag| + sum |<n|H|n'> psi(n')/psi(n)| (oracle): every ratio carries a relative
+error of about 1e-6, and near a node of psi the terms are large and cancel.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_25775_gb300 import binding as Bd
+from paper_2604_25775_gb300 import inputs as I
+from tests.gpu_common import conditioning, eloc_term_scale, rel_err, setup
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(name, gpu, ora, cond, tol, cond_ok, min_good=1):
+    err = rel_err(gpu, ora)
+    good = cond < cond_ok
+    mixed = tol > 1e-8
+    unit, c = (2.0 ** -24, 8.0) if mixed else (2.0 ** -53, 1e3)
+    print(f"{name}: n={len(err)} good={good.sum()} max_err(good)={err[good].max() if good.any() else 0:.3e} "
+          f"max_err={err.max():.3e}")
+    assert good.sum() >= min_good
+    assert err[good].max() <= tol
+    assert np.all(err <= np.maximum(tol, cond * c * unit))
+
+
+def _ace(pb_name, **kw):
+    return I.workload(pb_name).replace(**kw) if kw else I.workload(pb_name)
+
+
+@pytest.mark.parametrize("variant", ["torus", "open_tj", "shared_embed"])
+def test_ace_fp64_log_psi_and_local_energy(variant):
+    pb = I.workload("ace4x4")
+    if variant == "open_tj":
+        pb = pb.replace(pbc_y=0, model=I.MODEL_TJ, U=0.0, J=0.4, n_up=6, n_dn=6)
+    elif variant == "shared_embed":
+        pb = pb.replace(per_site_embed=0, tp=-0.2)
+    ctx, ora, occ, st = setup(pb, 48, 1250, 5700, scale=0.3)
+    cond = conditioning(ora, occ)
+    la, sg = ctx.log_psi()
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    la_o, sg_o = ora.log_psi(occ)
+    good = cond < 1e6
+    assert (sg[good] == sg_o[good]).all()
+    assert np.abs(la[good] - la_o[good]).max() <= 1e-10
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    _check(f"ace fp64 {variant}", e, e_o, cond, 1e-10, 1e6, min_good=24)
+
+
+@pytest.mark.parametrize("name", ["ace8x8", "ace8x8_tj"])
+def test_ace_mixed_8x8(name):
+    """Tensor-core layers (conv h = 48 with the normalisation in the epilogue, site-wise 64)."""
+    pb = I.workload("ace8x8")
+    if name == "ace8x8_tj":
+        pb = pb.replace(model=I.MODEL_TJ, U=0.0, J=0.4)
+    ctx, ora, occ, st = setup(pb, 16, 1251, 5701, scale=0.05)
+    cond = conditioning(ora, occ)
+    la, sg = ctx.log_psi()
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    la_o, sg_o = ora.log_psi(occ)
+    good = cond < 1e3
+    assert (sg[good] == sg_o[good]).all()
+    _check(f"{name} log|psi|", la, la_o, cond, 1e-4, 1e3)
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    scale = np.maximum(eloc_term_scale(ora, occ), 1.0)
+    _check(f"{name} E_loc / term scale", e / scale, e_o / scale, cond, 1e-4, 1e3)
+
+
+def test_ace_mixed_generic_width():
+    """A width without a tensor-core shape (h = 40) runs the FP32 CUDA-core layers."""
+    pb = I.workload("ace8x8").replace(h=40, h_mlp=40, n_conv=4, n_layers=5, ksize=[3] * 4 + [1],
+                                      residual=[1] * 4 + [0])
+    ctx, ora, occ, st = setup(pb, 16, 1252, 5702, scale=0.05)
+    cond = conditioning(ora, occ)
+    la = ctx.log_psi()[0].cpu().numpy()
+    la_o, _ = ora.log_psi(occ)
+    _check("ace generic width log|psi|", la, la_o, cond, 1e-4, 1e3)
+
+
+def test_ace_mixed_16x16_table_shape():
+    """Table tab:model ACE (16 blocks at h = 144, two site-wise layers at 256) on the 16x16
+    torus: log|psi| of 8 samples and the local energy of 1 (the oracle recomputes every
+    psi(n') in full, about a second each)."""
+    pb = I.workload("ace16x16")
+    ctx, ora, occ, st = setup(pb, 8, 1253, 5703, scale=0.02)
+    cond = conditioning(ora, occ)
+    la = ctx.log_psi()[0].cpu().numpy()
+    la_o, _ = ora.log_psi(occ)
+    _check("ace16x16 log|psi|", la, la_o, cond, 1e-4, 1e4, min_good=2)
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ[:1])
+    _check("ace16x16 E_loc", e[:1], e_o, cond[:1], 1e-4, 1e4, min_good=0)
+
+
+def test_ace_symmetry_projection():
+    import torch
+    pb = I.workload("ace4x4")
+    ctx, ora, occ, st = setup(pb, 24, 1254, 5704, scale=0.3)
+    perms = I.symmetry_group(pb, translations=True, reflections=True)
+    chi = np.ones(len(perms))
+    la, sg = ctx.log_psi_sym(torch.from_numpy(perms).cuda(), torch.from_numpy(chi).cuda())
+    la_o, sg_o = ora.log_psi_sym(occ, perms, chi)
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    ok = np.isfinite(la_o)
+    v = sg * np.exp(la - la_o.max())
+    v_o = sg_o * np.exp(la_o - la_o.max())
+    assert np.abs(v - v_o).max() <= 1e-10 * np.abs(v_o).max()
+    assert (sg[ok & (np.abs(v_o) > 1e-6 * np.abs(v_o).max())] == sg_o[ok & (np.abs(v_o) > 1e-6 * np.abs(v_o).max())]).all()
+
+
+def test_ace_rejects_cached_update_entry_points():
+    import torch
+    pb = I.workload("ace4x4")
+    ctx, ora, occ, st = setup(pb, 8, 1255, 5705)
+    with pytest.raises(Bd.ScaleError) as e:
+        ctx.local_energy(Bd.PATH_LOWRANK)
+    assert e.value.status == Bd.EUNSUPPORTED
+    with pytest.raises(Bd.ScaleError):
+        ctx.scale_grad_logpsi(torch.empty((8, ctx.P), dtype=torch.float64, device="cuda"))
+    # the context still answers after the refusals
+    assert np.isfinite(ctx.log_psi()[0].cpu().numpy()).any()
