@@ -14,8 +14,21 @@
 // (configurations x sites) rows against 9 stacked h x h weights with the rows gathered
 // by neighbour offset.
 //
-// Two implementations of a layer:
-//   k_ace_mma   (mixed mode, supported widths): tensor cores, every product as three TF32
+// Implementations of a layer:
+//   k_ace_conv_tc (mixed mode, conv blocks of width 48, 144 or 192): the 5th-generation
+//               tensor cores. One CTA of 128 threads owns 128 rows (TMEM lanes) and all h
+//               output channels (TMEM columns). The K loop runs over (offset d, 16-channel
+//               chunk) stages in a 3-deep shared-memory ring: each thread gathers its own
+//               row's 16 input channels from the neighbour site with 16-byte cp.async (zero
+//               fill past an open edge), the pre-split weight tile arrives by one bulk copy
+//               per half (hi, lo) on an mbarrier, and one thread issues the three TF32
+//               products x_hi W_hi + x_lo W_hi + x_hi W_lo per K=8 step (tcgen05.mma,
+//               FP32 accumulation in TMEM) and commits them to the stage's mbarrier. The
+//               activations between conv blocks are stored already split (hi, lo).
+//               Epilogue per thread = per row: tcgen05.ld of its accumulator row in 16-column
+//               chunks, bias, residual, SiLU, the layer normalisation (sum and sum of
+//               squares over the row), the split for the next block.
+//   k_ace_mma   (mixed mode, site-wise layers): tensor cores, every product as three TF32
 //               products of a hi/lo split (x_hi W_hi + x_lo W_hi + x_hi W_lo, FP32
 //               accumulation, about 2^-21 relative per layer). A warp owns 16 rows and
 //               WC warps share a row group's output columns; the A operand is gathered from
@@ -28,6 +41,7 @@
 
 #include "mlp_mma.cuh"
 #include "scale_internal.cuh"
+#include "tcgen05.cuh"
 
 namespace scale {
 
@@ -310,11 +324,259 @@ __global__ void __launch_bounds__(256, (NTW > 18 || NTW == 16 ? 1 : 2)) k_ace_mm
   }
 }
 
+// ---- conv blocks on tcgen05 ---------------------------------------------------------------
+constexpr int kTcRows = 128;  // M of a tile = TMEM lanes = threads of the CTA
+constexpr int kTcKC = 16;     // input channels per pipeline stage (two K = 8 MMA steps)
+constexpr int kTcStages = 3;
+constexpr uint32_t kTcWaitPolls = 1u << 24;  // bound of every mbarrier wait
+
+// Byte offset of element (r, k) of an [R x 16] tf32 tile in the K-major core-matrix layout:
+// core matrix (r / 8, k / 4) at ((r / 8) * 4 + k / 4) * 128, its row r % 8 at 16 bytes.
+// Neighbours along K are 128 bytes apart (descriptor LBO), along rows 512 (SBO).
+__host__ __device__ constexpr uint32_t tc_off(int r, int k) {
+  return (uint32_t)(((r >> 3) * 4 + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+template <int N>
+struct TcShape {
+  static constexpr uint32_t A_BYTES = kTcRows * kTcKC * 4;  // one half (hi or lo) of the A tile
+  static constexpr uint32_t B_BYTES = N * kTcKC * 4;        // one half of the weight tile
+  static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr uint32_t SMEM = kTcStages * STAGE + 2 * kTcStages * 8 + 16 + 1024;  // + barriers, slot, alignment
+  static constexpr uint32_t TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+};
+
+// Weight tiles of a conv block in the shared-memory image the MMA reads:
+// [tap d][chunk kc][hi, lo][N rows (output channel) x 16 (input channel)] core-matrix layout.
+__global__ void k_ace_build_bimg(const float* __restrict__ K, int N, float* __restrict__ out) {
+  const int KC = N / kTcKC;
+  const size_t total = (size_t)9 * KC * 2 * N * kTcKC;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q % kTcKC);
+    size_t r = q / kTcKC;
+    const int n = (int)(r % N);
+    r /= N;
+    const int part = (int)(r % 2);
+    r /= 2;
+    const int kc = (int)(r % KC);
+    const int d = (int)(r / KC);
+    const float w = K[((size_t)d * N + kc * kTcKC + k) * N + n];
+    uint32_t hi, lo;
+    split_tf32(w, hi, lo);
+    const size_t tile = (((size_t)d * KC + kc) * 2 + part) * N * kTcKC;
+    out[tile + tc_off(n, k) / 4] = __uint_as_float(part ? lo : hi);
+  }
+}
+
+// H0 rows split for the tensor cores: out_hi = tf32(E), out_lo = tf32(E - out_hi).
+__global__ void k_ace_embed_split(int N, int h, int per_site, const float* __restrict__ embed,
+                                  const int8_t* __restrict__ occ, long long total, float* __restrict__ out_hi,
+                                  float* __restrict__ out_lo) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long row = q / h;
+    const int c = (int)(q - row * h);
+    const int i = (int)(row % N);
+    const float e = embed[((size_t)(per_site ? i : 0) * 4 + (occ[row] & 3)) * h + c];
+    uint32_t hi, lo;
+    split_tf32(e, hi, lo);
+    out_hi[q] = __uint_as_float(hi);
+    out_lo[q] = __uint_as_float(lo);
+  }
+}
+
+// One conv block (3x3, N -> N channels, Eq. ACE) on tcgen05; out_lo == nullptr writes plain
+// FP32 rows to out_hi (the input of the site-wise layers). err: set when a wait ran out.
+template <int N>
+__global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
+    Lattice lat, const float* __restrict__ bimg, const float* __restrict__ bias, const float* __restrict__ gam,
+    const float* __restrict__ bet, int act, float eps, const float* __restrict__ in_hi,
+    const float* __restrict__ in_lo, float* __restrict__ out_hi, float* __restrict__ out_lo, long long rows,
+    int* __restrict__ err) {
+  using S = TcShape<N>;
+  constexpr int KC = N / kTcKC;
+  constexpr int STEPS = 9 * KC;
+  constexpr uint32_t IDESC = tc::idesc_tf32<kTcRows, N>();
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte aligned ring (descriptors address 16-byte units; core matrices 128 bytes)
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kTcStages * S::STAGE);
+  uint64_t* done = full + kTcStages;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + kTcStages);
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int Ns = lat.N;
+  const long long R = (long long)blockIdx.x * kTcRows + tid;
+  const bool valid = R < rows;
+  const long long cfg = valid ? R / Ns : 0;
+  const int site = valid ? (int)(R - cfg * Ns) : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&done[s], 1);
+    }
+    tc::mbar_fence_init();
+    s_abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, S::TCOLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  auto issue = [&](int s) {
+    const int b = s % kTcStages, d = s / KC, kc = s % KC;
+    unsigned char* st = smem + b * S::STAGE;
+    const int j = valid ? site_off(lat, site, d % 3 - 1, d / 3 - 1) : -1;
+    const size_t src = j >= 0 ? ((size_t)cfg * Ns + j) * N + kc * kTcKC : 0;
+    const uint32_t nb = j >= 0 ? 16u : 0u;  // zero fill past an open edge or the last row
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t o = tc_off(tid, 4 * q);
+      tc::cp_async16_zfill(st + o, in_hi + src + 4 * q, nb);
+      tc::cp_async16_zfill(st + S::A_BYTES + o, in_lo + src + 4 * q, nb);
+    }
+    tc::cp_async_commit();
+    if (tid == 0) {
+      const float* w = bimg + ((size_t)d * KC + kc) * 2 * N * kTcKC;
+      tc::mbar_arrive_expect_tx(&full[b], 2 * S::B_BYTES);
+      tc::bulk_g2s(st + 2 * S::A_BYTES, w, S::B_BYTES, &full[b]);
+      tc::bulk_g2s(st + 2 * S::A_BYTES + S::B_BYTES, w + N * kTcKC, S::B_BYTES, &full[b]);
+    }
+  };
+
+  issue(0);
+  for (int s = 0; s < STEPS; ++s) {
+    const int b = s % kTcStages;
+    if (s + 1 < STEPS) {
+      const int s1 = s + 1, b1 = s1 % kTcStages;
+      // the ring slot of stage s1 last held stage s1 - kTcStages: its MMAs must be done
+      bool ok = true;
+      if (s1 >= kTcStages) ok = tc::mbar_wait(&done[b1], (uint32_t)((s1 / kTcStages) - 1) & 1u, kTcWaitPolls);
+      if (ok) issue(s1);
+      else s_abort = 1;
+      tc::cp_async_wait<1>();
+    } else {
+      tc::cp_async_wait<0>();
+    }
+    tc::fence_proxy_async();  // this thread's A rows -> visible to the tensor core
+    __syncthreads();
+    if (s_abort) break;
+    if (tid == 0) {
+      if (!tc::mbar_wait(&full[b], (uint32_t)(s / kTcStages) & 1u, kTcWaitPolls)) {
+        s_abort = 1;
+      } else {
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_u32(smem + b * S::STAGE);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {  // K = 8 steps: core-matrix columns 2k and 2k + 1
+          const uint64_t ah = tc::smem_desc_kmajor(a0 + 256 * k, 128, 512);
+          const uint64_t al = tc::smem_desc_kmajor(a0 + S::A_BYTES + 256 * k, 128, 512);
+          const uint64_t bh = tc::smem_desc_kmajor(a0 + 2 * S::A_BYTES + 256 * k, 128, 512);
+          const uint64_t bl = tc::smem_desc_kmajor(a0 + 2 * S::A_BYTES + S::B_BYTES + 256 * k, 128, 512);
+          tc::mma_tf32(tmem, ah, bh, IDESC, (s > 0 || k > 0) ? 1u : 0u);
+          tc::mma_tf32(tmem, al, bh, IDESC, 1u);
+          tc::mma_tf32(tmem, ah, bl, IDESC, 1u);
+        }
+        tc::mma_commit(&done[b]);
+      }
+    }
+  }
+  if (!s_abort) {
+    const int sl = STEPS - 1;
+    if (!tc::mbar_wait(&done[sl % kTcStages], (uint32_t)(sl / kTcStages) & 1u, kTcWaitPolls)) s_abort = 1;
+  }
+  tc::cp_async_wait<0>();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (!s_abort) {
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const float* xh = in_hi + (size_t)(valid ? R : 0) * N;
+    const float* xl = in_lo + (size_t)(valid ? R : 0) * N;
+    float s1 = 0.f, s2 = 0.f;
+#pragma unroll 1
+    for (int cc = 0; cc < N / 16; ++cc) {
+      float z[16];
+      tc::tmem_ld16(trow + cc * 16, z);
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) {
+        const int col = cc * 16 + q;
+        const float4 h4 = *reinterpret_cast<const float4*>(xh + col);
+        const float4 l4 = *reinterpret_cast<const float4*>(xl + col);
+        const float x[4] = {h4.x + l4.x, h4.y + l4.y, h4.z + l4.z, h4.w + l4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float u = x[e] + act_fast(act, z[q + e] + bias[col + e]);
+          s1 += u;
+          s2 += u * u;
+        }
+      }
+    }
+    const float mean = s1 * (1.f / N);
+    const float var = fmaxf(s2 * (1.f / N) - mean * mean, 0.f);
+    const float inv = 1.f / sqrtf(var + eps);
+#pragma unroll 1
+    for (int cc = 0; cc < N / 16; ++cc) {
+      float z[16];
+      tc::tmem_ld16(trow + cc * 16, z);
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) {
+        const int col = cc * 16 + q;
+        const float4 h4 = *reinterpret_cast<const float4*>(xh + col);
+        const float4 l4 = *reinterpret_cast<const float4*>(xl + col);
+        const float x[4] = {h4.x + l4.x, h4.y + l4.y, h4.z + l4.z, h4.w + l4.w};
+        float y[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float u = x[e] + act_fast(act, z[q + e] + bias[col + e]);
+          y[e] = (u - mean) * inv * gam[col + e] + bet[col + e];
+        }
+        if (valid) {
+          if (out_lo) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) split_tf32(y[e], hi[e], lo[e]);
+            *reinterpret_cast<float4*>(out_hi + (size_t)R * N + col) =
+                make_float4(__uint_as_float(hi[0]), __uint_as_float(hi[1]), __uint_as_float(hi[2]),
+                            __uint_as_float(hi[3]));
+            *reinterpret_cast<float4*>(out_lo + (size_t)R * N + col) =
+                make_float4(__uint_as_float(lo[0]), __uint_as_float(lo[1]), __uint_as_float(lo[2]),
+                            __uint_as_float(lo[3]));
+          } else {
+            *reinterpret_cast<float4*>(out_hi + (size_t)R * N + col) = make_float4(y[0], y[1], y[2], y[3]);
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, S::TCOLS);
+}
+
+template <int N>
+cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, const float* bias, const float* g,
+                        const float* be, int act, float eps, const float* in_hi, const float* in_lo, float* out_hi,
+                        float* out_lo, long long rows, int* err) {
+  using S = TcShape<N>;
+  cudaError_t e = cudaFuncSetAttribute(k_ace_conv_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (rows + kTcRows - 1) / kTcRows;
+  k_ace_conv_tc<N><<<(unsigned)blocks, kTcRows, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, in_hi, in_lo,
+                                                                 out_hi, out_lo, rows, err);
+  return cudaGetLastError();
+}
+
+bool tc_width(int h) { return h == 48 || h == 144 || h == 192; }
+
 // Slater matrix rows of the occupied orbitals in ascending order (FP64 output); a
 // configuration with another electron count gets a zero matrix (singular).
 template <typename T>
 __global__ void k_ace_phi(Lattice lat, AceNet<T> net, int hl, const int8_t* __restrict__ occ,
-                          const T* __restrict__ HL, double* __restrict__ phi) {
+                          const T* __restrict__ HL, const int* __restrict__ err, double* __restrict__ phi) {
   extern __shared__ int olist[];  // [2N]
   __shared__ int s_n;
   const int b = blockIdx.x, N = lat.N, Ne = lat.Ne;
@@ -332,6 +594,10 @@ __global__ void k_ace_phi(Lattice lat, AceNet<T> net, int hl, const int8_t* __re
   }
   __syncthreads();
   double* P = phi + (size_t)b * Ne * Ne;
+  if (err && *err) {  // a tensor-core layer gave up waiting: no amplitude
+    for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = CUDART_NAN;
+    return;
+  }
   if (s_n != Ne) {
     for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = 0.0;
     return;
@@ -408,17 +674,39 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
   const long long rows = (long long)C * N;
   T* a = (T*)c->act_a;
   T* b = (T*)c->act_b;
-  {
-    const long long total = rows * c->h;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
-    k_ace_embed<T><<<blocks, 256, 0, c->stream>>>(N, c->h, net.per_site, net.embed, occ, total, a);
+  const long long total = rows * c->h;
+  const int eblocks = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
+  bool split = false;  // activations held as (hi, lo) halves of the buffer
+  if constexpr (sizeof(T) == 4) {
+    if (c->ace_tc) {
+      k_ace_embed_split<<<eblocks, 256, 0, c->stream>>>(N, c->h, net.per_site, net.embed, occ, total, a,
+                                                        a + total);
+      split = true;
+    }
   }
+  if (!split) k_ace_embed<T><<<eblocks, 256, 0, c->stream>>>(N, c->h, net.per_site, net.embed, occ, total, a);
   size_t frag_off = 0;
   for (int l = 0; l < c->L; ++l) {
     const bool conv = l < net.n_conv;
     bool done = false;
     if constexpr (sizeof(T) == 4) {
-      if (c->ace_mma) {
+      if (split) {  // conv block on tcgen05; the last one writes plain FP32 rows
+        const float* bimg = (const float*)((const char*)c->ace_frag + frag_off);
+        float* olo = l + 1 < net.n_conv ? b + total : nullptr;
+        cudaError_t e;
+        if (c->h == 48)
+          e = run_conv_tc<48>(c->stream, c->lat, bimg, net.bias[l], net.ln_g[l], net.ln_b[l], net.act,
+                              (float)net.eps, a, a + total, b, olo, rows, c->ace_err);
+        else if (c->h == 144)
+          e = run_conv_tc<144>(c->stream, c->lat, bimg, net.bias[l], net.ln_g[l], net.ln_b[l], net.act,
+                               (float)net.eps, a, a + total, b, olo, rows, c->ace_err);
+        else
+          e = run_conv_tc<192>(c->stream, c->lat, bimg, net.bias[l], net.ln_g[l], net.ln_b[l], net.act,
+                               (float)net.eps, a, a + total, b, olo, rows, c->ace_err);
+        if (e != cudaSuccess) return e;
+        split = olo != nullptr;
+        done = true;
+      } else if (c->ace_mma) {
         const MmaPlan p = plan_of(c->arch, l);
         const WFrag* frag = (const WFrag*)((const char*)c->ace_frag + frag_off);
         done = launch_mma_layer(c->stream, c->lat, p, conv, frag, net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l],
@@ -437,11 +725,13 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
     std::swap(a, b);
   }
   const int hl = net.cout[c->L - 1];
-  k_ace_phi<T><<<C, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, a, phi64);
+  k_ace_phi<T><<<C, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, a, c->ace_err, phi64);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+bool ace_tc_shapes(const scale_arch& a) { return ace_mma_shapes(a) && tc_width(a.h); }
 
 bool ace_mma_shapes(const scale_arch& a) {
   for (int l = 0; l < a.n_layers; ++l)
@@ -462,6 +752,13 @@ cudaError_t launch_ace_build(scale_ctx* c) {
   size_t off = 0;
   for (int l = 0; l < c->L; ++l) {
     const int taps = net.ks[l] * net.ks[l];
+    if (c->ace_tc && l < net.n_conv) {  // the tcgen05 weight-tile image
+      const size_t n = (size_t)taps * 2 * net.cin[l] * net.cout[l];
+      const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+      k_ace_build_bimg<<<blocks, 256, 0, c->stream>>>(net.kernel[l], net.cout[l], (float*)((char*)c->ace_frag + off));
+      off += frag_layer_bytes(c->arch, l);
+      continue;
+    }
     const size_t n = (size_t)taps * (net.cin[l] / 8) * (net.cout[l] / 8) * 32;
     const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
     k_ace_build_frag<<<blocks, 256, 0, c->stream>>>(net.kernel[l], taps, net.cin[l], net.cout[l],

@@ -120,7 +120,8 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   const size_t P = (size_t)param_count(s, a);
   const size_t k0 = a->ksize[0];
   const bool ace = a->family == SCALE_FAMILY_ACE;
-  const size_t hmax = ace ? std::max<size_t>(h, ace_width_out(*a, a->n_layers - 1)) : h;
+  // ACE activations: the widest layer, or the (hi, lo) halves of a tensor-core conv block
+  const size_t hmax = ace ? std::max<size_t>({h, (size_t)ace_width_out(*a, a->n_layers - 1), 2 * h}) : h;
   size_t t = 0;
   t += P * 8 + (T == 4 ? P * 4 : 0);
   t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0) + 2 * N * Ne * T;
@@ -173,7 +174,7 @@ void free_all(scale_ctx* c) {
                   c->commits, c->drift, c->Phi64, c->act_a, c->act_b, c->list, c->list_count, c->stat_dev,
                   c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_terms, c->full_moves,
                   c->commit_scratch, c->la_tmp, c->sg_tmp, c->full_la, c->full_sg, c->full_diag,
-                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag};
+                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag, c->ace_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -268,6 +269,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   c->use_mma = !c->fp64 && c->lowrank_ok && c->h == c->hpad;
   c->hmax = c->ace ? std::max(c->h, ace_width_out(*arch, c->L - 1)) : c->h;
   c->ace_mma = c->ace && !c->fp64 && ace_mma_shapes(*arch);
+  c->ace_tc = c->ace_mma && ace_tc_shapes(*arch);
   std::vector<int32_t> bonds = make_bonds(c->lat, &c->nb_nn, &c->nb_nnn);
   c->max_moves = 2 * (c->nb_nn + c->nb_nnn) + (sys->model == SCALE_MODEL_TJ ? c->nb_nn : 0);
   c->full_chunk = max_batch;
@@ -284,7 +286,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   if (!c->fp64) A(&c->M0_32, 2 * N * Ne * 4);
   A((char**)&c->M0b, 2 * N * Ne * T);
   const bool ace = c->ace;
-  const size_t hmax = c->hmax;
+  const size_t hmax = ace ? std::max<size_t>(c->hmax, 2 * h) : h;
   A((char**)&c->KE, ace ? 16 : Ns * 4 * c->k0 * c->k0 * h * T);
   A(&c->bonds, std::max<size_t>(bonds.size(), 2) * 4);
   A(&c->occ, B * N);
@@ -320,6 +322,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A(&c->full_moves, B * cap * 16);
   if (c->use_mma) A((char**)&c->wfrag, (size_t)c->L * (c->hpad / 8) * (c->hpad / 8) * 32 * 16);
   if (c->ace_mma) A((char**)&c->ace_frag, ace_frag_bytes(*arch));
+  if (c->ace) A(&c->ace_err, 16);
   if (e != cudaSuccess) {
     free_all(c);
     delete c;
@@ -330,6 +333,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stat_dev, 0, 32, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->drift, 0, B * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->commits, 0, B * 4, c->stream);
+  if (e == cudaSuccess && c->ace_err) e = cudaMemsetAsync(c->ace_err, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     free_all(c);

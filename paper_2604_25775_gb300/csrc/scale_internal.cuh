@@ -185,6 +185,8 @@ struct scale_ctx {
   // ACE family (full-recompute network, no cached update)
   bool ace = false;
   bool ace_mma = false;     // mixed mode with tensor-core shapes for every layer
+  bool ace_tc = false;      // conv blocks on tcgen05 (widths 48, 144, 192)
+  int32_t* ace_err = nullptr;  // set by a tcgen05 layer whose bounded wait ran out
   int hmax = 0;             // widest layer (activation buffers are [B][N][hmax])
   void* ace_frag = nullptr; // TF32 hi/lo mma fragments of every ACE layer
 
@@ -203,6 +205,7 @@ inline int ace_width_in(const scale_arch& a, int l) { return l == 0 ? a.h : ace_
 // Bytes of the tensor-core fragments of every ACE layer (0 when a shape has none).
 size_t ace_frag_bytes(const scale_arch& a);
 bool ace_mma_shapes(const scale_arch& a);
+bool ace_tc_shapes(const scale_arch& a);
 cudaError_t launch_ace_build(scale_ctx* c);
 cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64);
 
