@@ -17,17 +17,19 @@
 // Implementations of a layer:
 //   k_ace_conv_tc (mixed mode, conv blocks of width 48, 144 or 192): the 5th-generation
 //               tensor cores. One CTA of 128 threads owns 128 rows (TMEM lanes) and all h
-//               output channels (TMEM columns). The K loop runs over (offset d, 16-channel
-//               chunk) stages in a 3-deep shared-memory ring: each thread gathers its own
-//               row's 16 input channels from the neighbour site with 16-byte cp.async (zero
+//               output channels (TMEM columns). The K loop runs over (offset d, 8-channel
+//               chunk) stages in a 6-slot shared-memory ring with 4 stages of copies in
+//               flight: each thread gathers its own row's 8 input channels from the
+//               neighbour site with 16-byte cp.async (zero
 //               fill past an open edge), the pre-split weight tile arrives by one bulk copy
 //               per half (hi, lo) on an mbarrier, and one thread issues the three TF32
 //               products x_hi W_hi + x_lo W_hi + x_hi W_lo per K=8 step (tcgen05.mma,
 //               FP32 accumulation in TMEM) and commits them to the stage's mbarrier. The
 //               activations between conv blocks are stored already split (hi, lo).
-//               Epilogue per thread = per row: tcgen05.ld of its accumulator row in 16-column
-//               chunks, bias, residual, SiLU, the layer normalisation (sum and sum of
-//               squares over the row), the split for the next block.
+//               Epilogue per thread = per row, held in registers: the residual row (loaded
+//               while the last MMAs finish), tcgen05.ld of the accumulator row in 16-column
+//               chunks, bias, SiLU, the layer normalisation (mean, then the centred variance),
+//               the split for the next block.
 //   k_ace_mma   (mixed mode, site-wise layers): tensor cores, every product as three TF32
 //               products of a hi/lo split (x_hi W_hi + x_lo W_hi + x_hi W_lo, FP32
 //               accumulation, about 2^-21 relative per layer). A warp owns 16 rows and
@@ -326,15 +328,24 @@ __global__ void __launch_bounds__(256, (NTW > 18 || NTW == 16 ? 1 : 2)) k_ace_mm
 
 // ---- conv blocks on tcgen05 ---------------------------------------------------------------
 constexpr int kTcRows = 128;  // M of a tile = TMEM lanes = threads of the CTA
-constexpr int kTcKC = 16;     // input channels per pipeline stage (two K = 8 MMA steps)
-constexpr int kTcStages = 3;
+constexpr int kTcKC = 8;      // input channels per pipeline stage (one K = 8 MMA step)
+constexpr int kTcStages = 6;  // shared-memory ring
+constexpr int kTcAhead = 4;   // stages whose copies are in flight ahead of the MMA
 constexpr uint32_t kTcWaitPolls = 1u << 24;  // bound of every mbarrier wait
 
-// Byte offset of element (r, k) of an [R x 16] tf32 tile in the K-major core-matrix layout:
-// core matrix (r / 8, k / 4) at ((r / 8) * 4 + k / 4) * 128, its row r % 8 at 16 bytes.
-// Neighbours along K are 128 bytes apart (descriptor LBO), along rows 512 (SBO).
+// Byte offset of element (r, k) of an [R x 8] tf32 tile in the K-major core-matrix layout:
+// core matrix (r / 8, k / 4) at ((r / 8) * 2 + k / 4) * 128, its row r % 8 at 16 bytes.
+// Neighbours along K are 128 bytes apart (descriptor LBO), along rows 256 (SBO).
 __host__ __device__ constexpr uint32_t tc_off(int r, int k) {
-  return (uint32_t)(((r >> 3) * 4 + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+  return (uint32_t)(((r >> 3) * 2 + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+constexpr uint32_t kTcLBO = 128, kTcSBO = 256;
+
+// Activation of the tensor-core conv epilogue: SiLU as z / (1 + e^-z) with the fast
+// reciprocal-based division (the exponent capped so the denominator stays finite).
+__device__ __forceinline__ float act_tc(int act, float z) {
+  if (act == SCALE_ACT_SILU) return __fdividef(z, 1.f + __expf(fminf(-z, 80.f)));
+  return tanh_f32(z);
 }
 
 template <int N>
@@ -347,7 +358,7 @@ struct TcShape {
 };
 
 // Weight tiles of a conv block in the shared-memory image the MMA reads:
-// [tap d][chunk kc][hi, lo][N rows (output channel) x 16 (input channel)] core-matrix layout.
+// [tap d][chunk kc][hi, lo][N rows (output channel) x 8 (input channel)] core-matrix layout.
 __global__ void k_ace_build_bimg(const float* __restrict__ K, int N, float* __restrict__ out) {
   const int KC = N / kTcKC;
   const size_t total = (size_t)9 * KC * 2 * N * kTcKC;
@@ -425,42 +436,61 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
 
-  auto issue = [&](int s) {
-    const int b = s % kTcStages, d = s / KC, kc = s % KC;
-    unsigned char* st = smem + b * S::STAGE;
+  // Copies of the stages in order, one per call; each call closes one cp.async group
+  // (empty past the last stage). The neighbour row of the current tap is recomputed only
+  // when the tap changes (every KC stages).
+  int is = 0, id = 0, ikc = 0;
+  size_t isrc = 0;
+  uint32_t inb = 0;
+  auto tap_row = [&](int d) {
     const int j = valid ? site_off(lat, site, d % 3 - 1, d / 3 - 1) : -1;
-    const size_t src = j >= 0 ? ((size_t)cfg * Ns + j) * N + kc * kTcKC : 0;
-    const uint32_t nb = j >= 0 ? 16u : 0u;  // zero fill past an open edge or the last row
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t o = tc_off(tid, 4 * q);
-      tc::cp_async16_zfill(st + o, in_hi + src + 4 * q, nb);
-      tc::cp_async16_zfill(st + S::A_BYTES + o, in_lo + src + 4 * q, nb);
+    isrc = j >= 0 ? ((size_t)cfg * Ns + j) * N : 0;
+    inb = j >= 0 ? 16u : 0u;  // zero fill past an open edge or the last row
+  };
+  tap_row(0);
+  const uint32_t a_off0 = tc_off(tid, 0), a_off1 = tc_off(tid, 4);
+  auto issue_next = [&]() {
+    if (is < STEPS) {
+      const int b = is % kTcStages;
+      unsigned char* st = smem + b * S::STAGE;
+      const size_t src = isrc + (size_t)ikc * kTcKC;
+      tc::cp_async16_zfill(st + a_off0, in_hi + src, inb);
+      tc::cp_async16_zfill(st + a_off1, in_hi + src + 4, inb);
+      tc::cp_async16_zfill(st + S::A_BYTES + a_off0, in_lo + src, inb);
+      tc::cp_async16_zfill(st + S::A_BYTES + a_off1, in_lo + src + 4, inb);
+      if (tid == 0) {
+        const float* w = bimg + ((size_t)id * KC + ikc) * 2 * N * kTcKC;
+        tc::mbar_arrive_expect_tx(&full[b], 2 * S::B_BYTES);
+        tc::bulk_g2s(st + 2 * S::A_BYTES, w, S::B_BYTES, &full[b]);
+        tc::bulk_g2s(st + 2 * S::A_BYTES + S::B_BYTES, w + N * kTcKC, S::B_BYTES, &full[b]);
+      }
+      ++is;
+      if (++ikc == KC) {
+        ikc = 0;
+        if (++id < 9) tap_row(id);
+      }
     }
     tc::cp_async_commit();
-    if (tid == 0) {
-      const float* w = bimg + ((size_t)d * KC + kc) * 2 * N * kTcKC;
-      tc::mbar_arrive_expect_tx(&full[b], 2 * S::B_BYTES);
-      tc::bulk_g2s(st + 2 * S::A_BYTES, w, S::B_BYTES, &full[b]);
-      tc::bulk_g2s(st + 2 * S::A_BYTES + S::B_BYTES, w + N * kTcKC, S::B_BYTES, &full[b]);
-    }
   };
 
-  issue(0);
+#pragma unroll 1
+  for (int p = 0; p < kTcAhead; ++p) issue_next();
+#pragma unroll 1
   for (int s = 0; s < STEPS; ++s) {
     const int b = s % kTcStages;
-    if (s + 1 < STEPS) {
-      const int s1 = s + 1, b1 = s1 % kTcStages;
-      // the ring slot of stage s1 last held stage s1 - kTcStages: its MMAs must be done
-      bool ok = true;
-      if (s1 >= kTcStages) ok = tc::mbar_wait(&done[b1], (uint32_t)((s1 / kTcStages) - 1) & 1u, kTcWaitPolls);
-      if (ok) issue(s1);
-      else s_abort = 1;
-      tc::cp_async_wait<1>();
+    const int s1 = s + kTcAhead;
+    // the ring slot of stage s1 last held stage s1 - kTcStages (two MMA stages back)
+    bool ok = true;
+    if (s1 < STEPS && s1 >= kTcStages)
+      ok = tc::mbar_wait(&done[s1 % kTcStages], (uint32_t)((s1 / kTcStages) - 1) & 1u, kTcWaitPolls);
+    if (ok) {
+      issue_next();  // stage s1
     } else {
-      tc::cp_async_wait<0>();
+      s_abort = 1;
+      tc::cp_async_commit();
     }
-    tc::fence_proxy_async();  // this thread's A rows -> visible to the tensor core
+    tc::cp_async_wait<kTcAhead>();  // this thread's copies of stage s have landed
+    tc::fence_proxy_async();        // ... and are visible to the tensor core
     __syncthreads();
     if (s_abort) break;
     if (tid == 0) {
@@ -469,18 +499,30 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
       } else {
         tc::fence_after_sync();
         const uint32_t a0 = tc::smem_u32(smem + b * S::STAGE);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {  // K = 8 steps: core-matrix columns 2k and 2k + 1
-          const uint64_t ah = tc::smem_desc_kmajor(a0 + 256 * k, 128, 512);
-          const uint64_t al = tc::smem_desc_kmajor(a0 + S::A_BYTES + 256 * k, 128, 512);
-          const uint64_t bh = tc::smem_desc_kmajor(a0 + 2 * S::A_BYTES + 256 * k, 128, 512);
-          const uint64_t bl = tc::smem_desc_kmajor(a0 + 2 * S::A_BYTES + S::B_BYTES + 256 * k, 128, 512);
-          tc::mma_tf32(tmem, ah, bh, IDESC, (s > 0 || k > 0) ? 1u : 0u);
-          tc::mma_tf32(tmem, al, bh, IDESC, 1u);
-          tc::mma_tf32(tmem, ah, bl, IDESC, 1u);
-        }
+        const uint64_t ah = tc::smem_desc_kmajor(a0, kTcLBO, kTcSBO);
+        const uint64_t al = tc::smem_desc_kmajor(a0 + S::A_BYTES, kTcLBO, kTcSBO);
+        const uint64_t bh = tc::smem_desc_kmajor(a0 + 2 * S::A_BYTES, kTcLBO, kTcSBO);
+        const uint64_t bl = tc::smem_desc_kmajor(a0 + 2 * S::A_BYTES + S::B_BYTES, kTcLBO, kTcSBO);
+        tc::mma_tf32(tmem, ah, bh, IDESC, s > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem, al, bh, IDESC, 1u);
+        tc::mma_tf32(tmem, ah, bl, IDESC, 1u);
         tc::mma_commit(&done[b]);
       }
+    }
+  }
+  // the residual rows do not depend on the MMAs: load them while the last ones finish
+  float u[N];
+  {
+    const float* xh = in_hi + (size_t)(valid ? R : 0) * N;
+    const float* xl = in_lo + (size_t)(valid ? R : 0) * N;
+#pragma unroll
+    for (int c = 0; c < N; c += 4) {
+      const float4 h4 = __ldg(reinterpret_cast<const float4*>(xh + c));
+      const float4 l4 = __ldg(reinterpret_cast<const float4*>(xl + c));
+      u[c] = h4.x + l4.x;
+      u[c + 1] = h4.y + l4.y;
+      u[c + 2] = h4.z + l4.z;
+      u[c + 3] = h4.w + l4.w;
     }
   }
   if (!s_abort) {
@@ -492,60 +534,39 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
   tc::fence_after_sync();
   if (!s_abort) {
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    const float* xh = in_hi + (size_t)(valid ? R : 0) * N;
-    const float* xl = in_lo + (size_t)(valid ? R : 0) * N;
-    float s1 = 0.f, s2 = 0.f;
-#pragma unroll 1
+#pragma unroll
     for (int cc = 0; cc < N / 16; ++cc) {
       float z[16];
       tc::tmem_ld16(trow + cc * 16, z);
 #pragma unroll
-      for (int q = 0; q < 16; q += 4) {
-        const int col = cc * 16 + q;
-        const float4 h4 = *reinterpret_cast<const float4*>(xh + col);
-        const float4 l4 = *reinterpret_cast<const float4*>(xl + col);
-        const float x[4] = {h4.x + l4.x, h4.y + l4.y, h4.z + l4.z, h4.w + l4.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float u = x[e] + act_fast(act, z[q + e] + bias[col + e]);
-          s1 += u;
-          s2 += u * u;
-        }
-      }
+      for (int q = 0; q < 16; ++q) u[cc * 16 + q] += act_tc(act, z[q] + __ldg(bias + cc * 16 + q));
     }
+    float s1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < N; ++c) s1 += u[c];
     const float mean = s1 * (1.f / N);
-    const float var = fmaxf(s2 * (1.f / N) - mean * mean, 0.f);
-    const float inv = 1.f / sqrtf(var + eps);
-#pragma unroll 1
-    for (int cc = 0; cc < N / 16; ++cc) {
-      float z[16];
-      tc::tmem_ld16(trow + cc * 16, z);
+    float s2 = 0.f;
 #pragma unroll
-      for (int q = 0; q < 16; q += 4) {
-        const int col = cc * 16 + q;
-        const float4 h4 = *reinterpret_cast<const float4*>(xh + col);
-        const float4 l4 = *reinterpret_cast<const float4*>(xl + col);
-        const float x[4] = {h4.x + l4.x, h4.y + l4.y, h4.z + l4.z, h4.w + l4.w};
-        float y[4];
+    for (int c = 0; c < N; ++c) s2 += (u[c] - mean) * (u[c] - mean);
+    const float inv = 1.f / sqrtf(s2 * (1.f / N) + eps);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float u = x[e] + act_fast(act, z[q + e] + bias[col + e]);
-          y[e] = (u - mean) * inv * gam[col + e] + bet[col + e];
-        }
-        if (valid) {
-          if (out_lo) {
-            uint32_t hi[4], lo[4];
+    for (int c = 0; c < N; c += 4) {
+      float y[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) split_tf32(y[e], hi[e], lo[e]);
-            *reinterpret_cast<float4*>(out_hi + (size_t)R * N + col) =
-                make_float4(__uint_as_float(hi[0]), __uint_as_float(hi[1]), __uint_as_float(hi[2]),
-                            __uint_as_float(hi[3]));
-            *reinterpret_cast<float4*>(out_lo + (size_t)R * N + col) =
-                make_float4(__uint_as_float(lo[0]), __uint_as_float(lo[1]), __uint_as_float(lo[2]),
-                            __uint_as_float(lo[3]));
-          } else {
-            *reinterpret_cast<float4*>(out_hi + (size_t)R * N + col) = make_float4(y[0], y[1], y[2], y[3]);
-          }
+      for (int e = 0; e < 4; ++e) y[e] = (u[c + e] - mean) * inv * __ldg(gam + c + e) + __ldg(bet + c + e);
+      if (valid) {
+        if (out_lo) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) split_tf32(y[e], hi[e], lo[e]);
+          *reinterpret_cast<float4*>(out_hi + (size_t)R * N + c) =
+              make_float4(__uint_as_float(hi[0]), __uint_as_float(hi[1]), __uint_as_float(hi[2]),
+                          __uint_as_float(hi[3]));
+          *reinterpret_cast<float4*>(out_lo + (size_t)R * N + c) =
+              make_float4(__uint_as_float(lo[0]), __uint_as_float(lo[1]), __uint_as_float(lo[2]),
+                          __uint_as_float(lo[3]));
+        } else {
+          *reinterpret_cast<float4*>(out_hi + (size_t)R * N + c) = make_float4(y[0], y[1], y[2], y[3]);
         }
       }
     }
