@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(256, (NTW > 18 || NTW == 16 ? 1 : 2)) k_ace_mm
 }
 
 // ---- conv blocks on tcgen05 ---------------------------------------------------------------
-constexpr int kTcRows = 128;  // M of a tile = TMEM lanes = threads of the CTA
+constexpr int kTcRows = 128;  // M of a tile = TMEM lanes
+constexpr int kTcThreads = 256;  // two threads per row
 constexpr int kTcKC = 8;      // input channels per pipeline stage (one K = 8 MMA step)
 constexpr int kTcStages = 6;  // shared-memory ring
 constexpr int kTcAhead = 4;   // stages whose copies are in flight ahead of the MMA
@@ -398,8 +399,11 @@ __global__ void k_ace_embed_split(int N, int h, int per_site, const float* __res
 
 // One conv block (3x3, N -> N channels, Eq. ACE) on tcgen05; out_lo == nullptr writes plain
 // FP32 rows to out_hi (the input of the site-wise layers). err: set when a wait ran out.
+// 256 threads: thread t serves row t % 128 -- copies of its hi (t < 128) or lo half, and
+// in the epilogue output columns [0, N/2) (warps 0-3) or [N/2, N) (warps 4-7); a warp reads
+// the TMEM lanes of its quarter (warp % 4).
 template <int N>
-__global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
+__global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
     Lattice lat, const float* __restrict__ bimg, const float* __restrict__ bias, const float* __restrict__ gam,
     const float* __restrict__ bet, int act, float eps, const float* __restrict__ in_hi,
     const float* __restrict__ in_lo, float* __restrict__ out_hi, float* __restrict__ out_lo, long long rows,
@@ -407,6 +411,7 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
   using S = TcShape<N>;
   constexpr int KC = N / kTcKC;
   constexpr int STEPS = 9 * KC;
+  constexpr int H2 = N / 2;  // epilogue columns per thread
   constexpr uint32_t IDESC = tc::idesc_tf32<kTcRows, N>();
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte aligned ring (descriptors address 16-byte units; core matrices 128 bytes)
@@ -415,9 +420,10 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
   uint64_t* done = full + kTcStages;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + kTcStages);
   __shared__ int s_abort;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  __shared__ float s_sum[2][kTcRows], s_sq[2][kTcRows];  // per-half row sums for the normalisation
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcRows - 1), part = tid >> 7;
   const int Ns = lat.N;
-  const long long R = (long long)blockIdx.x * kTcRows + tid;
+  const long long R = (long long)blockIdx.x * kTcRows + row;
   const bool valid = R < rows;
   const long long cfg = valid ? R / Ns : 0;
   const int site = valid ? (int)(R - cfg * Ns) : 0;
@@ -439,6 +445,7 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
   // Copies of the stages in order, one per call; each call closes one cp.async group
   // (empty past the last stage). The neighbour row of the current tap is recomputed only
   // when the tap changes (every KC stages).
+  const float* in_part = part ? in_lo : in_hi;
   int is = 0, id = 0, ikc = 0;
   size_t isrc = 0;
   uint32_t inb = 0;
@@ -448,16 +455,14 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
     inb = j >= 0 ? 16u : 0u;  // zero fill past an open edge or the last row
   };
   tap_row(0);
-  const uint32_t a_off0 = tc_off(tid, 0), a_off1 = tc_off(tid, 4);
+  const uint32_t a_off0 = part * S::A_BYTES + tc_off(row, 0), a_off1 = part * S::A_BYTES + tc_off(row, 4);
   auto issue_next = [&]() {
     if (is < STEPS) {
       const int b = is % kTcStages;
       unsigned char* st = smem + b * S::STAGE;
       const size_t src = isrc + (size_t)ikc * kTcKC;
-      tc::cp_async16_zfill(st + a_off0, in_hi + src, inb);
-      tc::cp_async16_zfill(st + a_off1, in_hi + src + 4, inb);
-      tc::cp_async16_zfill(st + S::A_BYTES + a_off0, in_lo + src, inb);
-      tc::cp_async16_zfill(st + S::A_BYTES + a_off1, in_lo + src + 4, inb);
+      tc::cp_async16_zfill(st + a_off0, in_part + src, inb);
+      tc::cp_async16_zfill(st + a_off1, in_part + src + 4, inb);
       if (tid == 0) {
         const float* w = bimg + ((size_t)id * KC + ikc) * 2 * N * kTcKC;
         tc::mbar_arrive_expect_tx(&full[b], 2 * S::B_BYTES);
@@ -510,13 +515,14 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
       }
     }
   }
-  // the residual rows do not depend on the MMAs: load them while the last ones finish
-  float u[N];
+  // this thread's half of the residual row (independent of the MMAs: loaded under them)
+  const int c0 = part * H2;
+  float u[H2];
   {
-    const float* xh = in_hi + (size_t)(valid ? R : 0) * N;
-    const float* xl = in_lo + (size_t)(valid ? R : 0) * N;
+    const float* xh = in_hi + (size_t)(valid ? R : 0) * N + c0;
+    const float* xl = in_lo + (size_t)(valid ? R : 0) * N + c0;
 #pragma unroll
-    for (int c = 0; c < N; c += 4) {
+    for (int c = 0; c < H2; c += 4) {
       const float4 h4 = __ldg(reinterpret_cast<const float4*>(xh + c));
       const float4 l4 = __ldg(reinterpret_cast<const float4*>(xl + c));
       u[c] = h4.x + l4.x;
@@ -525,48 +531,57 @@ __global__ void __launch_bounds__(kTcRows) k_ace_conv_tc(
       u[c + 3] = h4.w + l4.w;
     }
   }
-  if (!s_abort) {
+  if (!s_abort && tid == 0) {
     const int sl = STEPS - 1;
     if (!tc::mbar_wait(&done[sl % kTcStages], (uint32_t)(sl / kTcStages) & 1u, kTcWaitPolls)) s_abort = 1;
   }
   tc::cp_async_wait<0>();
   __syncthreads();
   tc::fence_after_sync();
-  if (!s_abort) {
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  const bool run = !s_abort;
+  if (run) {
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + c0;
 #pragma unroll
-    for (int cc = 0; cc < N / 16; ++cc) {
-      float z[16];
-      tc::tmem_ld16(trow + cc * 16, z);
+    for (int cc = 0; cc < H2 / 8; ++cc) {
+      float z[8];
+      tc::tmem_ld8(trow + cc * 8, z);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) u[cc * 16 + q] += act_tc(act, z[q] + __ldg(bias + cc * 16 + q));
+      for (int q = 0; q < 8; ++q) u[cc * 8 + q] += act_tc(act, z[q] + __ldg(bias + c0 + cc * 8 + q));
     }
     float s1 = 0.f;
 #pragma unroll
-    for (int c = 0; c < N; ++c) s1 += u[c];
-    const float mean = s1 * (1.f / N);
+    for (int c = 0; c < H2; ++c) s1 += u[c];
+    s_sum[part][row] = s1;
+  }
+  __syncthreads();
+  float mean = 0.f;
+  if (run) {
+    mean = (s_sum[0][row] + s_sum[1][row]) * (1.f / N);
     float s2 = 0.f;
 #pragma unroll
-    for (int c = 0; c < N; ++c) s2 += (u[c] - mean) * (u[c] - mean);
-    const float inv = 1.f / sqrtf(s2 * (1.f / N) + eps);
+    for (int c = 0; c < H2; ++c) s2 += (u[c] - mean) * (u[c] - mean);
+    s_sq[part][row] = s2;
+  }
+  __syncthreads();
+  if (run) {
+    const float inv = 1.f / sqrtf((s_sq[0][row] + s_sq[1][row]) * (1.f / N) + eps);
 #pragma unroll
-    for (int c = 0; c < N; c += 4) {
+    for (int c = 0; c < H2; c += 4) {
       float y[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) y[e] = (u[c + e] - mean) * inv * __ldg(gam + c + e) + __ldg(bet + c + e);
+      for (int e = 0; e < 4; ++e) y[e] = (u[c + e] - mean) * inv * __ldg(gam + c0 + c + e) + __ldg(bet + c0 + c + e);
       if (valid) {
+        const size_t o = (size_t)R * N + c0 + c;
         if (out_lo) {
           uint32_t hi[4], lo[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) split_tf32(y[e], hi[e], lo[e]);
-          *reinterpret_cast<float4*>(out_hi + (size_t)R * N + c) =
-              make_float4(__uint_as_float(hi[0]), __uint_as_float(hi[1]), __uint_as_float(hi[2]),
-                          __uint_as_float(hi[3]));
-          *reinterpret_cast<float4*>(out_lo + (size_t)R * N + c) =
-              make_float4(__uint_as_float(lo[0]), __uint_as_float(lo[1]), __uint_as_float(lo[2]),
-                          __uint_as_float(lo[3]));
+          *reinterpret_cast<float4*>(out_hi + o) = make_float4(__uint_as_float(hi[0]), __uint_as_float(hi[1]),
+                                                               __uint_as_float(hi[2]), __uint_as_float(hi[3]));
+          *reinterpret_cast<float4*>(out_lo + o) = make_float4(__uint_as_float(lo[0]), __uint_as_float(lo[1]),
+                                                               __uint_as_float(lo[2]), __uint_as_float(lo[3]));
         } else {
-          *reinterpret_cast<float4*>(out_hi + (size_t)R * N + c) = make_float4(y[0], y[1], y[2], y[3]);
+          *reinterpret_cast<float4*>(out_hi + o) = make_float4(y[0], y[1], y[2], y[3]);
         }
       }
     }
@@ -586,7 +601,7 @@ cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, 
   cudaError_t e = cudaFuncSetAttribute(k_ace_conv_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e != cudaSuccess) return e;
   const long long blocks = (rows + kTcRows - 1) / kTcRows;
-  k_ace_conv_tc<N><<<(unsigned)blocks, kTcRows, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, in_hi, in_lo,
+  k_ace_conv_tc<N><<<(unsigned)blocks, kTcThreads, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, in_hi, in_lo,
                                                                  out_hi, out_lo, rows, err);
   return cudaGetLastError();
 }
