@@ -48,8 +48,11 @@ __device__ __forceinline__ void argmax_merge(TW& v, int& i, TW v2, int i2) {
 }
 
 // TW: working precision; TOUT: inverse output precision.
-template <typename TW, typename TOUT, bool kInverse, int W>
-__global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, const int32_t* __restrict__ list,
+// TH threads per CTA (one matrix): 1024 hides the DFMA latency inside one CTA; the
+// determinant-only path runs 256-thread CTAs, several per SM, so that one matrix's serial
+// pivot steps overlap the trailing updates of the others.
+template <typename TW, typename TOUT, bool kInverse, int W, int TH = kThreads>
+__global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const int32_t* __restrict__ list,
                                                  TOUT* __restrict__ binv, double* __restrict__ logabs_out,
                                                  int32_t* __restrict__ sign_out, int32_t* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
@@ -60,8 +63,8 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
   int* piv = reinterpret_cast<int*>(rowp + W);   // [n] pivot row of column k
   int* qinv = piv + n;                           // [n] column whose pivot row is r
   unsigned char* used = reinterpret_cast<unsigned char*>(qinv + n);  // [n]
-  __shared__ TW red_v[kThreads / 32];
-  __shared__ int red_i[kThreads / 32];
+  __shared__ TW red_v[TH / 32];
+  __shared__ int red_i[TH / 32];
   __shared__ int s_p;
   __shared__ int s_singular;
 
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
   TW* A = mats + (size_t)b * n * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int i = tid; i < n; i += kThreads) used[i] = 0;
+  for (int i = tid; i < n; i += TH) used[i] = 0;
   if (tid == 0) s_singular = 0;
   double logdet = 0.0;  // kept by thread 0
   int sgn = 1;
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
   for (int K0 = 0; K0 < n; K0 += W) {
     const int w = min(W, n - K0);
     // panel <- columns [K0, K0+w)
-    for (int q = tid; q < n * w; q += kThreads) {
+    for (int q = tid; q < n * w; q += TH) {
       const int i = q / w, j = q - i * w;
       panel[i * W + j] = A[(size_t)i * n + K0 + j];
     }
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
       // pivot search over unpivoted rows
       TW bv = TW(-1);
       int bi = n;
-      for (int i = tid; i < n; i += kThreads) {
+      for (int i = tid; i < n; i += TH) {
         if (used[i]) continue;
         const TW v = fabs(panel[i * W + jj]);
         argmax_merge(bv, bi, v, i);
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
       if (tid == 0) {
         TW v = red_v[0];
         int i = red_i[0];
-        for (int q = 1; q < kThreads / 32; ++q) argmax_merge(v, i, red_v[q], red_i[q]);
+        for (int q = 1; q < TH / 32; ++q) argmax_merge(v, i, red_v[q], red_i[q]);
         if (!(v > TW(0)) || i >= n) {
           s_singular = 1;
           i = 0;
@@ -120,8 +123,8 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
       const TW pv = panel[p * W + jj];
       const TW inv = TW(1) / pv;
       // snapshot the pivot row (panel part) and column jj before updating
-      for (int j = tid; j < w; j += kThreads) rowp[j] = (j == jj) ? inv : panel[p * W + j] * inv;
-      for (int i = tid; i < n; i += kThreads) colk[i] = panel[i * W + jj];
+      for (int j = tid; j < w; j += TH) rowp[j] = (j == jj) ? inv : panel[p * W + j] * inv;
+      for (int i = tid; i < n; i += TH) colk[i] = panel[i * W + jj];
       if (tid == 0) {
         piv[k] = p;
         used[p] = 1;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
         if (pv < TW(0)) sgn = -sgn;
       }
       __syncthreads();
-      for (int q = tid; q < n * w; q += kThreads) {
+      for (int q = tid; q < n * w; q += TH) {
         const int i = q / w, j = q - i * w;
         if (i == p) {
           panel[i * W + j] = rowp[j];
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
     }
     if (s_singular) break;
     // old pivot rows of the block (all columns outside the panel)
-    for (int q = tid; q < w * n; q += kThreads) {
+    for (int q = tid; q < w * n; q += TH) {
       const int j = q / n, c = q - j * n;
       prow[j * n + c] = A[(size_t)piv[K0 + j] * n + c];
     }
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
     // rank-w update of the columns outside the panel: warp per row, lanes over columns,
     // the row's multipliers u_j = U[i][j] in registers, two columns per lane in flight
     const int c_lo = kInverse ? 0 : K0 + w;
-    for (int i = warp; i < n; i += kThreads / 32) {
+    for (int i = warp; i < n; i += TH / 32) {
       if (!kInverse && used[i]) continue;
       TW u[W];
 #pragma unroll
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
       }
     }
     // write the swept panel back
-    for (int q = tid; q < n * w; q += kThreads) {
+    for (int q = tid; q < n * w; q += TH) {
       const int i = q / w, j = q - i * w;
       A[(size_t)i * n + K0 + j] = panel[i * W + j];
     }
@@ -214,13 +217,13 @@ __global__ void __launch_bounds__(kThreads) k_gj(TW* __restrict__ mats, int n, c
   __syncthreads();
   if (s_singular) {
     if (binv)
-      for (int q = tid; q < n * n; q += kThreads) binv[(size_t)b * n * n + q] = TOUT(0);
+      for (int q = tid; q < n * n; q += TH) binv[(size_t)b * n * n + q] = TOUT(0);
     return;
   }
-  for (int k = tid; k < n; k += kThreads) qinv[piv[k]] = k;
+  for (int k = tid; k < n; k += TH) qinv[piv[k]] = k;
   __syncthreads();
   // Binv[s][cf] = A^-1[cf][s] = A_final[piv[cf]][qinv[s]]
-  for (int q = tid; q < n * n; q += kThreads) {
+  for (int q = tid; q < n * n; q += TH) {
     const int s = q / n, cf = q - s * n;
     binv[(size_t)b * n * n + q] = (TOUT)A[(size_t)piv[cf] * n + qinv[s]];
   }
@@ -469,14 +472,14 @@ cudaError_t run_gj_cluster(cudaStream_t st, double* mats, int n, int B, const in
   return cudaLaunchKernelEx(&cfg, kern, mats, n, list, binv, la, sg, status);
 }
 
-template <typename TW, typename TOUT, bool kInverse, int W>
+template <typename TW, typename TOUT, bool kInverse, int W, int TH = kThreads>
 cudaError_t run_gj(cudaStream_t st, TW* mats, int n, int B, const int32_t* list, TOUT* binv, double* la,
                    int32_t* sg, int32_t* status) {
   const size_t smem = sizeof(TW) * ((size_t)2 * n * W + n + W) + sizeof(int) * 2 * n + n + 16;
-  auto kern = k_gj<TW, TOUT, kInverse, W>;
+  auto kern = k_gj<TW, TOUT, kInverse, W, TH>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<B, kThreads, smem, st>>>(mats, n, list, binv, la, sg, status);
+  kern<<<B, TH, smem, st>>>(mats, n, list, binv, la, sg, status);
   return cudaGetLastError();
 }
 
@@ -508,7 +511,7 @@ cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32
     return run_gj<double, float, true, 16>(c->stream, A, n, B, list, (float*)Binv, logabs, sign, status);
   }
   if (n > 448) return run_gj<double, double, false, 8>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
-  return run_gj<double, double, false, 16>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
+  return run_gj<double, double, false, 16, 256>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
 }
 
 // Determinant only, FP32 working precision (full-recompute path in mixed mode).
