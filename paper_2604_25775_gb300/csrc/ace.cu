@@ -608,45 +608,97 @@ cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, 
 
 bool tc_width(int h) { return h == 48 || h == 144 || h == 192; }
 
-// Slater matrix rows of the occupied orbitals in ascending order (FP64 output); a
-// configuration with another electron count gets a zero matrix (singular).
+// Slater matrix rows of the occupied orbitals in ascending order (FP64 output):
+//   Phi[a][k] = M0[o_a][k] + proj_b[s Ne + k] + sum_c H(L)_i[c] proj_w[c][s Ne + k].
+// A register-tiled GEMM per configuration: CTA (row tile, column tile, configuration) of
+// 64 x 64 outputs, rows of one spin only (the up rows precede the down rows in ascending
+// order), 4 x 4 outputs per thread, channels staged 32 at a time through shared memory.
+// A configuration with another electron count gets a zero matrix (singular); after a
+// tensor-core layer gave up waiting, NaN.
+constexpr int kPhiT = 64, kPhiK = 32;
+
 template <typename T>
-__global__ void k_ace_phi(Lattice lat, AceNet<T> net, int hl, const int8_t* __restrict__ occ,
-                          const T* __restrict__ HL, const int* __restrict__ err, double* __restrict__ phi) {
+__global__ void __launch_bounds__(256) k_ace_phi(Lattice lat, AceNet<T> net, int hl, const int8_t* __restrict__ occ,
+                                                 const T* __restrict__ HL, const int* __restrict__ err,
+                                                 double* __restrict__ phi) {
   extern __shared__ int olist[];  // [2N]
+  __shared__ T Xs[kPhiK][kPhiT + 1];
+  __shared__ T Ws[kPhiK][kPhiT];
   __shared__ int s_n;
-  const int b = blockIdx.x, N = lat.N, Ne = lat.Ne;
+  const int b = blockIdx.z, N = lat.N, Ne = lat.Ne, tid = threadIdx.x;
   const int8_t* ob = occ + (size_t)b * N;
-  if (threadIdx.x < 32) {  // one warp lists the occupied orbitals in order
+  if (tid < 32) {  // one warp lists the occupied orbitals in order
     int n = 0;
     for (int base = 0; base < 2 * N; base += 32) {
-      const int o = base + threadIdx.x;
+      const int o = base + tid;
       const bool on = o < 2 * N && ((ob[o % N] >> (o / N)) & 1);
       const unsigned m = __ballot_sync(0xffffffffu, on);
-      if (on) olist[n + __popc(m & ((1u << threadIdx.x) - 1u))] = o;
+      if (on) olist[n + __popc(m & ((1u << tid) - 1u))] = o;
       n += __popc(m);
     }
-    if (threadIdx.x == 0) s_n = n;
+    if (tid == 0) s_n = n;
   }
   __syncthreads();
   double* P = phi + (size_t)b * Ne * Ne;
-  if (err && *err) {  // a tensor-core layer gave up waiting: no amplitude
-    for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = CUDART_NAN;
+  const int k0 = blockIdx.y * kPhiT;
+  // row tile -> spin and row range: tiles [0, tu) cover the up rows, the rest the down rows
+  const int tu = (lat.n_up + kPhiT - 1) / kPhiT;
+  const int s = (int)blockIdx.x < tu ? 0 : 1;
+  const int r_lo = s == 0 ? 0 : lat.n_up, r_hi = s == 0 ? lat.n_up : Ne;
+  const int a0 = r_lo + (s == 0 ? (int)blockIdx.x : (int)blockIdx.x - tu) * kPhiT;
+  if (a0 >= r_hi || k0 >= Ne) return;  // whole CTA
+  if ((err && *err) || s_n != Ne) {
+    const double v = (err && *err) ? CUDART_NAN : 0.0;
+    for (int q = tid; q < kPhiT * kPhiT; q += 256) {
+      const int a = a0 + q / kPhiT, k = k0 + q % kPhiT;
+      if (a < r_hi && k < Ne) P[(size_t)a * Ne + k] = v;
+    }
     return;
   }
-  if (s_n != Ne) {
-    for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = 0.0;
-    return;
+  const int tx = tid & 15, ty = tid >> 4;  // 4 columns x 4 rows each
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+  const T* W = net.proj_w + s * Ne;
+  for (int kc = 0; kc < hl; kc += kPhiK) {
+    for (int q = tid; q < kPhiK * kPhiT; q += 256) {  // X^T tile: channel kk of row r
+      const int r = q / kPhiK, kk = q % kPhiK;
+      const int a = a0 + r;
+      T v = T(0);
+      if (a < r_hi && kc + kk < hl) v = HL[((size_t)b * N + (olist[a] - s * N)) * hl + kc + kk];
+      Xs[kk][r] = v;
+    }
+    for (int q = tid; q < kPhiK * kPhiT; q += 256) {  // W tile: channel kk, column k
+      const int kk = q / kPhiT, c = q % kPhiT;
+      Ws[kk][c] = (kc + kk < hl && k0 + c < Ne) ? W[(size_t)(kc + kk) * 2 * Ne + k0 + c] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kPhiK; ++kk) {
+      T x[4], w[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x[r] = Xs[kk][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) w[c] = Ws[kk][tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] += x[r] * w[c];
+    }
+    __syncthreads();
   }
-  const T* Hb = HL + (size_t)b * N * hl;
-  for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) {
-    const int a = q / Ne, k = q - a * Ne;
-    const int o = olist[a], s = o / N, i = o - s * N;
-    T v = net.M0[(size_t)o * Ne + k] + net.proj_b[s * Ne + k];
-    const T* w = net.proj_w + s * Ne + k;
-    const T* x = Hb + (size_t)i * hl;
-    for (int c = 0; c < hl; ++c) v += x[c] * w[(size_t)c * 2 * Ne];
-    P[q] = (double)v;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int a = a0 + ty * 4 + r;
+    if (a >= r_hi) continue;
+    const int o = olist[a];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = k0 + tx * 4 + c;
+      if (k < Ne) P[(size_t)a * Ne + k] = (double)(net.M0[(size_t)o * Ne + k] + net.proj_b[s * Ne + k] + acc[r][c]);
+    }
   }
 }
 
@@ -761,7 +813,11 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
     std::swap(a, b);
   }
   const int hl = net.cout[c->L - 1];
-  k_ace_phi<T><<<C, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, a, c->ace_err, phi64);
+  const int Ne = c->Ne;
+  const dim3 pgrid((c->sys.n_up + kPhiT - 1) / kPhiT + (c->sys.n_dn + kPhiT - 1) / kPhiT, (Ne + kPhiT - 1) / kPhiT, C);
+  cudaError_t e = cudaFuncSetAttribute(k_ace_phi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * 2 * N));
+  if (e != cudaSuccess) return e;
+  k_ace_phi<T><<<pgrid, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, a, c->ace_err, phi64);
   return cudaGetLastError();
 }
 
