@@ -452,57 +452,13 @@ def main():
                              "steps_per_sweep": steps_per_sample}
             del pk_d, dr_d, uu_d, pk_t, dr_t, uu_t
             ctxs.close()
-        # symmetry projection over the lattice translations: |G| fresh amplitudes per walker
+        # symmetry projection over the lattice translations: |G| fresh amplitudes per walker;
+        # ACE (no cached update: every psi(n') of a local energy is a fresh forward + LU)
+        from paper_2604_25775_gb300 import next_bench
         if args.sym_walkers > 0:
-            ns = args.sym_walkers
-            perms = torch.from_numpy(I.symmetry_group(pb, translations=True)).cuda()
-            chi = torch.ones(perms.shape[0], dtype=torch.float64, device="cuda")
-            ctxy = Bd.make_context(pb, params, M0, ns)
-            ctxy.scale_load(occ_d[:ns].contiguous())
-            ctxy.log_psi_sym(perms[:4].contiguous(), chi[:4].contiguous())
-            torch.cuda.synchronize()
-            a.record()
-            ctxy.log_psi_sym(perms, chi)
-            b2.record()
-            torch.cuda.synchronize()
-            sy_ms = a.elapsed_time(b2)
-            line["symmetry"] = {"walkers": ns, "group": int(perms.shape[0]), "ms": sy_ms,
-                                "amplitudes_per_s": ns * perms.shape[0] / (sy_ms / 1e3),
-                                "walkers_per_s": ns / (sy_ms / 1e3)}
-            ctxy.close()
-        # ACE (deep conv stack with layer normalisation, Table tab:model shape at 16x16): no
-        # cached update, so every psi(n') of a local energy is a fresh forward + FP64 LU
+            line["symmetry"] = next_bench.run_symmetry(args.sym_walkers)
         if args.ace_walkers > 0:
-            pa = I.workload("ace16x16")
-            pa_params = I.random_params(pa, 1253, 0.02)
-            pa_M0 = I.plane_wave_M0(pa)
-            chunk = 1024
-            ctxa = Bd.make_context(pa, pa_params, pa_M0, chunk)
-            occ_a = torch.from_numpy(I.random_configs(pa, chunk, 5703)).cuda()
-            ctxa.scale_load(occ_a)
-            torch.cuda.synchronize()
-            a.record()
-            ctxa.scale_load(occ_a)
-            b2.record()
-            torch.cuda.synchronize()
-            load_ms = a.elapsed_time(b2)
-            nw = args.ace_walkers
-            ctxa.scale_load(occ_a[:nw].contiguous())
-            ea = torch.empty(nw, dtype=torch.float64, device="cuda")
-            ctxa.scale_local_energy(ea, Bd.PATH_FULL)
-            torch.cuda.synchronize()
-            a.record()
-            ctxa.scale_local_energy(ea, Bd.PATH_FULL)
-            b2.record()
-            torch.cuda.synchronize()
-            ace_ms = a.elapsed_time(b2)
-            conv_flops = 2.0 * pa.n_conv * pa.N * 9 * pa.h * pa.h  # per configuration
-            line["ace"] = {"workload": "ace16x16: 16x16 torus, U=8, 112+112, 16 conv blocks h=144 + 2 site-wise h=256",
-                           "walkers": nw, "ms": ace_ms, "eloc_per_s": nw / (ace_ms / 1e3),
-                           "load_1024_ms": load_ms, "amplitudes_per_s": chunk / (load_ms / 1e3),
-                           "conv_gflop_per_amplitude": conv_flops / 1e9,
-                           "finite": bool(torch.isfinite(ea).all().item())}
-            ctxa.close()
+            line["ace"] = next_bench.run_ace(args.ace_walkers)
         # serving: open-loop Poisson sweep-step requests over mixed chains, continuous batching
         if args.serve_seconds > 0:
             from paper_2604_25775_gb300 import serve_bench

@@ -1,0 +1,91 @@
+"""Timings of the paths beyond the SCALE chain step, used by bench.py and callable on
+their own (one GPU, inputs resident on the device, CUDA events on the context's stream):
+
+    python -m paper_2604_25775_gb300.next_bench ace [walkers]
+        ACE (Sec. II "ACE", Table tab:model shape: 16 conv blocks at h = 144, two site-wise
+        layers at 256) on the 16x16 torus, 112 + 112: the full-recompute local energy of
+        `walkers` walkers (every psi(n') a fresh forward and FP64 LU), and the amplitudes of
+        1024 configurations (forward + determinant).
+    python -m paper_2604_25775_gb300.next_bench symmetry [walkers]
+        The symmetry-projected amplitude (App. "Symmetry Projection") over the 256
+        translations of the SCALE 16x16 bench workload.
+"""
+from __future__ import annotations
+
+import json
+import sys
+
+from . import binding as Bd
+from . import inputs as I
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_ace(walkers: int = 16, chunk: int = 1024) -> dict:
+    import torch
+    pb = I.workload("ace16x16")
+    params = I.random_params(pb, 1253, 0.02)
+    M0 = I.plane_wave_M0(pb)
+    ctx = Bd.make_context(pb, params, M0, chunk)
+    occ = torch.from_numpy(I.random_configs(pb, chunk, 5703)).cuda()
+    a, b = _events()
+    ctx.scale_load(occ)  # warm-up
+    torch.cuda.synchronize()
+    a.record()
+    ctx.scale_load(occ)
+    b.record()
+    torch.cuda.synchronize()
+    load_ms = a.elapsed_time(b)
+    ctx.scale_load(occ[:walkers].contiguous())
+    e = torch.empty(walkers, dtype=torch.float64, device="cuda")
+    ctx.scale_local_energy(e, Bd.PATH_FULL)
+    torch.cuda.synchronize()
+    a.record()
+    ctx.scale_local_energy(e, Bd.PATH_FULL)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    conv_flops = 2.0 * pb.n_conv * pb.N * 9 * pb.h * pb.h  # per configuration
+    out = {"workload": "ace16x16: 16x16 torus, U=8, 112+112, 16 conv blocks h=144 + 2 site-wise h=256",
+           "precision": "mixed (TF32x3 tensor-core layers, FP64 Slater matrices and LU)",
+           "walkers": walkers, "ms": ms, "eloc_per_s": walkers / (ms / 1e3),
+           "load_1024_ms": load_ms, "amplitudes_per_s": chunk / (load_ms / 1e3),
+           "conv_gflop_per_amplitude": conv_flops / 1e9,
+           "finite": bool(torch.isfinite(e).all().item())}
+    ctx.close()
+    return out
+
+
+def run_symmetry(walkers: int = 1024) -> dict:
+    import torch
+    pb = I.workload("hubbard16x16")
+    pseed, cseed = I.workload_seeds("hubbard16x16")
+    ctx = Bd.make_context(pb, I.random_params(pb, pseed, 0.05), I.plane_wave_M0(pb), walkers)
+    ctx.scale_load(torch.from_numpy(I.random_configs(pb, walkers, cseed)).cuda())
+    perms = torch.from_numpy(I.symmetry_group(pb, translations=True)).cuda()
+    chi = torch.ones(perms.shape[0], dtype=torch.float64, device="cuda")
+    ctx.log_psi_sym(perms[:4].contiguous(), chi[:4].contiguous())  # warm-up
+    a, b = _events()
+    torch.cuda.synchronize()
+    a.record()
+    la, sg = ctx.log_psi_sym(perms, chi)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out = {"walkers": walkers, "group": int(perms.shape[0]), "ms": ms,
+           "amplitudes_per_s": walkers * perms.shape[0] / (ms / 1e3), "walkers_per_s": walkers / (ms / 1e3),
+           "finite": bool(torch.isfinite(la).any().item())}
+    ctx.close()
+    return out
+
+
+if __name__ == "__main__":
+    what = sys.argv[1] if len(sys.argv) > 1 else "ace"
+    n = int(sys.argv[2]) if len(sys.argv) > 2 else None
+    if what == "ace":
+        print(json.dumps(run_ace(n or 16)))
+    else:
+        print(json.dumps(run_symmetry(n or 1024)))
