@@ -32,7 +32,11 @@
  *     site-wise layers of Eq. MLP at width h_mlp and the orbital projection. Every psi
  *     that the functions above take goes through the same amplitude routine, so the ACE
  *     log psi, local energy (full recompute of every psi(n')) and symmetry projection
- *     follow from it.
+ *     follow from it;
+ *   * the wide SCALE shapes of Table tab:model (family 2): the SCALE layout with per-layer
+ *     widths (conv h, site-wise h_mlp) and no normalisation, and the plus-shaped stencil of
+ *     SCALE-L (stencil 1: the offsets of a k x k box with dx^2 + dy^2 <= ((k-1)/2)^2, 13
+ *     sites for k = 5, weights stored for those taps only, in row-major box order).
  *
  * Parity status: every function here is pinned by CPU tests (closed-form U=0 energy,
  * library convolution and slogdet, dense-Hamiltonian enumeration, finite differences,
@@ -55,10 +59,11 @@ typedef struct {
   int32_t n_layers, h, act, per_site_embed; /* act: 0 tanh, 1 SiLU */
   int32_t ksize[ORA_MAX_LAYERS];
   int32_t residual[ORA_MAX_LAYERS];
-  int32_t family;       /* 0 SCALE, 1 ACE */
+  int32_t family;       /* 0 SCALE, 1 ACE, 2 SCALE at per-layer widths (full recompute) */
   int32_t n_conv;       /* ACE: layers [0, n_conv) are conv blocks with layer normalisation */
   int32_t h_mlp;        /* ACE: width of the site-wise layers after the conv blocks */
   double ln_eps;        /* ACE: epsilon of the layer normalisation */
+  int32_t stencil;      /* 0: k x k box; 1: the box offsets within L2 distance (k-1)/2 */
   const double *params; /* flat parameter vector (layout in the Python wrapper) */
   const double *M0;     /* [2N][Ne] reference orbitals */
 } ora_model;
@@ -105,12 +110,23 @@ int ora_bonds(const ora_model *m, int which, int32_t *pairs) {
 /* Channel widths. SCALE: every layer has h channels. ACE: the conv blocks keep h, the
  * site-wise layers after them have h_mlp (the first one maps h -> h_mlp). */
 static int width_out(const ora_model *m, int l) {
-  return (m->family == 1 && l >= m->n_conv) ? m->h_mlp : m->h;
+  return (m->family != 0 && l >= m->n_conv) ? m->h_mlp : m->h;
+}
+/* Whether the offset (dx, dy) belongs to the stencil of a k x k layer. */
+static int in_stencil(const ora_model *m, int k, int dx, int dy) {
+  const int r = (k - 1) / 2;
+  return m->stencil == 0 || dx * dx + dy * dy <= r * r;
+}
+static int taps_of(const ora_model *m, int k) {
+  int n = 0;
+  for (int dy = -(k - 1) / 2; dy <= (k - 1) / 2; ++dy)
+    for (int dx = -(k - 1) / 2; dx <= (k - 1) / 2; ++dx) n += in_stencil(m, k, dx, dy);
+  return n;
 }
 static int width_in(const ora_model *m, int l) { return l == 0 ? m->h : width_out(m, l - 1); }
 static int width_last(const ora_model *m) { return m->n_layers ? width_out(m, m->n_layers - 1) : m->h; }
 static int width_max(const ora_model *m) {
-  return (m->family == 1 && m->h_mlp > m->h && m->n_layers > m->n_conv) ? m->h_mlp : m->h;
+  return (m->family != 0 && m->h_mlp > m->h && m->n_layers > m->n_conv) ? m->h_mlp : m->h;
 }
 static int has_ln(const ora_model *m, int l) { return m->family == 1 && l < m->n_conv; }
 
@@ -119,7 +135,7 @@ int64_t ora_param_count(const ora_model *m) {
   int64_t n = (m->per_site_embed ? N : 1) * 4 * h;
   for (int l = 0; l < m->n_layers; ++l) {
     const int64_t ci = width_in(m, l), co = width_out(m, l);
-    n += (int64_t)m->ksize[l] * m->ksize[l] * ci * co + co;
+    n += (int64_t)taps_of(m, m->ksize[l]) * ci * co + co;
     if (has_ln(m, l)) n += 2 * co;
   }
   n += (int64_t)width_last(m) * 2 * Ne + 2 * Ne;
@@ -141,7 +157,7 @@ static ora_offsets offsets_of(const ora_model *m) {
   o.embed = p; p += (m->per_site_embed ? N : 1) * 4 * h;
   for (int l = 0; l < m->n_layers; ++l) {
     const int64_t ci = width_in(m, l), co = width_out(m, l);
-    o.kernel[l] = p; p += (int64_t)m->ksize[l] * m->ksize[l] * ci * co;
+    o.kernel[l] = p; p += (int64_t)taps_of(m, m->ksize[l]) * ci * co;
     o.bias[l] = p; p += co;
     o.ln_g[l] = o.ln_b[l] = -1;
     if (has_ln(m, l)) {
@@ -197,11 +213,14 @@ static void forward(const ora_model *m, const int8_t *occ, double *H, double *Z)
     for (int i = 0; i < N; ++i) {
       for (int co = 0; co < co_n; ++co) {
         double z = b[co];
+        int tap = 0; /* index of the offset among the stencil's taps, row-major over the box */
         for (int ky = 0; ky < k; ++ky)
           for (int kx = 0; kx < k; ++kx) {
+            if (!in_stencil(m, k, kx - r, ky - r)) continue;
+            const int t = tap++;
             int j = site_offset(m, i, kx - r, ky - r);
             if (j < 0) continue; /* zero padding on open edges */
-            const double *w = K + ((int64_t)(ky * k + kx) * ci_n) * co_n;
+            const double *w = K + ((int64_t)t * ci_n) * co_n;
             for (int ci = 0; ci < ci_n; ++ci) z += in[(int64_t)j * hs + ci] * w[(int64_t)ci * co_n + co];
           }
         if (Z) Z[((int64_t)l * N + i) * h + co] = z;
@@ -816,7 +835,7 @@ static void grad_one(const ora_model *m, const int8_t *occ, double *g, double *H
 int ora_grad_logpsi(const ora_model *m, int B, const int8_t *occ, double *grad) {
   const int N = m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn, L = m->n_layers;
   const int64_t P = ora_param_count(m);
-  if (m->family != 0) return -1; /* the backward pass covers the SCALE family */
+  if (m->family != 0 || m->stencil != 0) return -1; /* the backward pass covers the SCALE family */
 #pragma omp parallel
   {
     double *H = (double *)malloc(sizeof(double) * (int64_t)(L + 1) * N * h);

@@ -34,7 +34,7 @@ class _Model(ctypes.Structure):
         ("per_site_embed", ctypes.c_int32),
         ("ksize", ctypes.c_int32 * MAX_LAYERS), ("residual", ctypes.c_int32 * MAX_LAYERS),
         ("family", ctypes.c_int32), ("n_conv", ctypes.c_int32), ("h_mlp", ctypes.c_int32),
-        ("ln_eps", ctypes.c_double),
+        ("ln_eps", ctypes.c_double), ("stencil", ctypes.c_int32),
         ("params", ctypes.POINTER(ctypes.c_double)), ("M0", ctypes.POINTER(ctypes.c_double)),
     ]
 
@@ -117,7 +117,8 @@ class Model:
         s.n_conv = int(d.get("n_conv", 0))
         s.h_mlp = int(d.get("h_mlp", 0)) or self.h
         s.ln_eps = float(d.get("ln_eps", 1e-5))
-        ace = s.family == 1 and self.L > s.n_conv
+        s.stencil = int(d.get("stencil", 0))
+        ace = s.family != 0 and self.L > s.n_conv
         self.h_last = s.h_mlp if ace else self.h
         self.h_max = max(self.h, self.h_last)
         s.params = self.params.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -19,7 +19,9 @@ Parameter layout (flat, float64, in this order; the C header documents the same 
 The ACE family (Eq. ACE) uses the same order with per-layer widths: layers [0, n_conv) are
 conv blocks h -> h followed by ln_gamma [h] and ln_beta [h] of the layer normalisation;
 the site-wise layers after them map h -> h_mlp, then h_mlp -> h_mlp; proj_w is
-[h_mlp][2*Ne]. The layer-normalisation gains are drawn as 1 + N(0, scale^2).
+[h_mlp][2*Ne]. The layer-normalisation gains are drawn as 1 + N(0, scale^2). The wide SCALE
+family uses the same per-layer widths without normalisation. With the disk stencil a
+kernel is stored for its taps only, [taps][c_in][c_out], taps in row-major box order.
 """
 from __future__ import annotations
 
@@ -36,6 +38,9 @@ ACT_TANH = 0
 ACT_SILU = 1
 FAMILY_SCALE = 0
 FAMILY_ACE = 1
+FAMILY_WIDE = 2   # the SCALE layout at Table tab:model widths, full recompute only
+STENCIL_BOX = 0   # k x k offsets
+STENCIL_DISK = 1  # offsets of the k x k box within L2 distance (k-1)/2 (k = 5: SCALE-L's 13 sites)
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_MIXED_BF16 = 2
@@ -73,6 +78,7 @@ class Problem:
     n_conv: int = 0       # ACE: number of conv blocks with layer normalisation
     h_mlp: int = 0        # ACE: width of the site-wise layers (0 = h)
     ln_eps: float = 1e-5  # ACE: layer-normalisation epsilon
+    stencil: int = STENCIL_BOX
 
     @property
     def N(self) -> int:
@@ -107,10 +113,17 @@ def ace_layout(n_conv: int, n_mlp: int, ksize: int = 3):
     return [ksize] * n_conv + [1] * n_mlp, [1] * n_conv + [0] * n_mlp
 
 
+def stencil_taps(k: int, stencil: int):
+    """(dx, dy) offsets of a k x k layer's stencil in row-major box order."""
+    r = (k - 1) // 2
+    return [(dx, dy) for dy in range(-r, r + 1) for dx in range(-r, r + 1)
+            if stencil == STENCIL_BOX or dx * dx + dy * dy <= r * r]
+
+
 def layer_widths(pb: Problem, l: int):
     """(c_in, c_out) of layer l."""
     hm = pb.h_mlp or pb.h
-    if pb.family != FAMILY_ACE:
+    if pb.family == FAMILY_SCALE:
         return pb.h, pb.h
     c_out = pb.h if l < pb.n_conv else hm
     c_in = pb.h if l <= pb.n_conv else hm
@@ -125,7 +138,10 @@ def param_shapes(pb: Problem) -> List[tuple]:
     for l in range(pb.n_layers):
         k = int(pb.ksize[l])
         ci, co = layer_widths(pb, l)
-        shapes.append((f"kernel{l}", (k, k, ci, co)))
+        if pb.stencil == STENCIL_DISK:
+            shapes.append((f"kernel{l}", (len(stencil_taps(k, pb.stencil)), ci, co)))
+        else:
+            shapes.append((f"kernel{l}", (k, k, ci, co)))
         shapes.append((f"bias{l}", (co,)))
         if pb.family == FAMILY_ACE and l < pb.n_conv:
             shapes.append((f"ln_gamma{l}", (co,)))
@@ -387,6 +403,20 @@ def workload(name: str) -> Problem:
         ks, rs = ace_layout(16, 2)
         return Problem(16, 4, 1, 1, 28, 28, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 18, 144, ks, rs,
                        ACT_SILU, 1, PREC_MIXED, 64, 1e-4, FAMILY_ACE, 16, 256)
+    if name == "scale_l5x5":  # SCALE-L layout (13-site plus stencil), small widths, FP64
+        return Problem(5, 5, 1, 1, 8, 8, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 3, 6, [5, 1, 1], [1, 0, 0],
+                       ACT_SILU, 1, PREC_FP64, 64, 1e-10, FAMILY_WIDE, 1, 10, 1e-5, STENCIL_DISK)
+    if name == "scale_l8x8":  # SCALE-L layout at 8x8, 28+28, widths 96 / 128, mixed
+        return Problem(8, 8, 1, 1, 28, 28, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 5, 96, [5, 1, 1, 1, 1],
+                       [1, 0, 0, 0, 0], ACT_SILU, 1, PREC_MIXED, 64, 1e-4, FAMILY_WIDE, 1, 128, 1e-5,
+                       STENCIL_DISK)
+    if name == "scale_l16x16":  # Table tab:model SCALE-L: plus stencil (L2 <= 2), h 384, 4 x 512
+        return Problem(16, 16, 1, 1, 112, 112, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 5, 384, [5, 1, 1, 1, 1],
+                       [1, 0, 0, 0, 0], ACT_SILU, 1, PREC_MIXED, 64, 1e-4, FAMILY_WIDE, 1, 512, 1e-5,
+                       STENCIL_DISK)
+    if name == "scale_xl32x32":  # Table tab:model SCALE-XL (32x32 only): 3x3, h 640, 4 x 1280
+        return Problem(32, 32, 1, 1, 448, 448, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 5, 640, [3, 1, 1, 1, 1],
+                       [1, 0, 0, 0, 0], ACT_SILU, 1, PREC_MIXED, 64, 1e-4, FAMILY_WIDE, 1, 1280)
     if name == "tj16x16":
         ks, rs = scale_layout(6)
         return Problem(16, 16, 1, 1, 112, 112, MODEL_TJ, 1.0, 0.0, 0.0, 0.4, 6, 32, ks, rs,
@@ -404,7 +434,8 @@ def workload(name: str) -> Problem:
 
 WORKLOAD_INDEX = {"hubbard4x4": 0, "hubbard8x8": 1, "hubbard16x16": 2, "cylinder16x4": 3,
                   "tj8x8": 4, "tj16x16": 4, "hubbard32x32": 4, "tj32x32": 4,
-                  "hubbard_ph8x8": 5, "ace4x4": 6, "ace8x8": 6, "ace16x16": 6, "ace16x4": 6}
+                  "hubbard_ph8x8": 5, "ace4x4": 6, "ace8x8": 6, "ace16x16": 6, "ace16x4": 6,
+                  "scale_l5x5": 7, "scale_l8x8": 7, "scale_l16x16": 7, "scale_xl32x32": 7}
 
 
 def workload_seeds(name: str):
