@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--sweep-steps", type=int, default=64)
     ap.add_argument("--sym-walkers", type=int, default=1024)
     ap.add_argument("--ace-walkers", type=int, default=16)
+    ap.add_argument("--wide-walkers", type=int, default=8)
     return ap.parse_args()
 
 
@@ -459,6 +460,8 @@ def main():
             line["symmetry"] = next_bench.run_symmetry(args.sym_walkers)
         if args.ace_walkers > 0:
             line["ace"] = next_bench.run_ace(args.ace_walkers)
+        if args.wide_walkers > 0:  # Table tab:model SCALE-L / SCALE-XL shapes, full recompute
+            line["wide"] = next_bench.run_wide(args.wide_walkers)
         # serving: open-loop Poisson sweep-step requests over mixed chains, continuous batching
         if args.serve_seconds > 0:
             from paper_2604_25775_gb300 import serve_bench

@@ -80,7 +80,16 @@ enum { SCALE_ACT_TANH = 0, SCALE_ACT_SILU = 1 };
  * stack, so ACE has no cached update: scale_load, scale_log_psi, scale_local_energy with
  * SCALE_PATH_FULL and scale_log_psi_sym run it; the low-rank entry points, the gradient,
  * the server and the allocation-free call return SCALE_EUNSUPPORTED. */
-enum { SCALE_FAMILY_SCALE = 0, SCALE_FAMILY_ACE = 1 };
+/* SCALE_FAMILY_WIDE: the SCALE layout (one residual k x k conv, then site-wise layers) at the
+ * widths of Table tab:model (conv h up to 1024, site-wise h_mlp up to 2048) and with
+ * SCALE-L's plus-shaped stencil; without the cached update (the move path holds one channel
+ * vector per lane group and one electron per lane, which these shapes exceed), so the same
+ * entry points as ACE apply. */
+enum { SCALE_FAMILY_SCALE = 0, SCALE_FAMILY_ACE = 1, SCALE_FAMILY_WIDE = 2 };
+/* Stencil of the k x k layers: the whole box, or the box offsets within L2 distance
+ * (k - 1) / 2 (k = 5: the 13 sites of SCALE-L, Table tab:model); a kernel holds weights for
+ * its taps only, [taps][c_in][c_out], taps in row-major box order. */
+enum { SCALE_STENCIL_BOX = 0, SCALE_STENCIL_DISK = 1 };
 enum { SCALE_PREC_FP64 = 0, SCALE_PREC_MIXED = 1, SCALE_PREC_MIXED_BF16 = 2 };
 enum { SCALE_PATH_LOWRANK = 0, SCALE_PATH_FULL = 1 };
 
@@ -107,7 +116,8 @@ typedef struct {
 /* Network shape and numerics. */
 typedef struct {
   int32_t n_layers;       /* L >= 1 */
-  int32_t h;              /* channels of every layer, 1..64 (ACE: of the conv blocks, 1..256) */
+  int32_t h;              /* channels of every layer, 1..64 (ACE: of the conv blocks, 1..256;
+                             wide SCALE: of the conv, 1..1024) */
   int32_t act;            /* SCALE_ACT_* */
   int32_t per_site_embed; /* 1: tables E_i per site (Sec. II.B); 0: one shared table */
   int32_t precision;      /* SCALE_PREC_FP64: everything FP64.
@@ -132,8 +142,9 @@ typedef struct {
   int32_t family;         /* SCALE_FAMILY_* (0 = SCALE) */
   int32_t n_conv;         /* ACE: layers [0, n_conv) are conv blocks (residual 1, odd ksize);
                              layers after them are site-wise (ksize 1, residual 0) */
-  int32_t h_mlp;          /* ACE: width of the site-wise layers, 1..512 (0 = h) */
+  int32_t h_mlp;          /* ACE: width of the site-wise layers, 1..512 (wide SCALE 1..2048; 0 = h) */
   double ln_eps;          /* ACE: epsilon of the layer normalisation (>= 0) */
+  int32_t stencil;        /* SCALE_STENCIL_* (the SCALE family needs the box) */
 } scale_arch;
 
 typedef struct {

@@ -50,7 +50,7 @@ class scale_arch(ctypes.Structure):
                 ("refresh_every", ctypes.c_int32), ("drift_tol", ctypes.c_double),
                 ("ksize", ctypes.c_int32 * MAX_LAYERS), ("residual", ctypes.c_int32 * MAX_LAYERS),
                 ("family", ctypes.c_int32), ("n_conv", ctypes.c_int32), ("h_mlp", ctypes.c_int32),
-                ("ln_eps", ctypes.c_double)]
+                ("ln_eps", ctypes.c_double), ("stencil", ctypes.c_int32)]
 
 
 class scale_stats(ctypes.Structure):
@@ -113,6 +113,7 @@ def make_descriptors(pb: I.Problem):
         a.ksize[l] = int(pb.ksize[l])
         a.residual[l] = int(pb.residual[l])
     a.family, a.n_conv, a.h_mlp, a.ln_eps = pb.family, pb.n_conv, pb.h_mlp, pb.ln_eps
+    a.stencil = pb.stencil
     return s, a
 
 

@@ -53,7 +53,7 @@ constexpr int kAceRowsGeneric = 8;  // rows (one warp each) per CTA of k_ace_lay
 
 template <typename T>
 struct AceNet {
-  int h, L, n_conv, act, per_site;
+  int h, L, n_conv, act, per_site, stencil;
   double eps;
   int cin[kMaxLayers], cout[kMaxLayers], ks[kMaxLayers];
   const T* embed;
@@ -77,7 +77,9 @@ AceNet<T> make_ace_net(const scale_ctx* c) {
   n.n_conv = a.n_conv;
   n.act = a.act;
   n.per_site = a.per_site_embed;
+  n.stencil = a.stencil;
   n.eps = a.ln_eps;
+  const bool ln = a.family == SCALE_FAMILY_ACE;
   const T* base = c->fp64 ? (const T*)c->params64 : (const T*)c->params32;
   int64_t p = 0;
   n.embed = base;
@@ -87,11 +89,11 @@ AceNet<T> make_ace_net(const scale_ctx* c) {
     n.cin[l] = ace_width_in(a, l);
     n.cout[l] = ace_width_out(a, l);
     n.kernel[l] = base + p;
-    p += (int64_t)n.ks[l] * n.ks[l] * n.cin[l] * n.cout[l];
+    p += (int64_t)stencil_taps(a.stencil, n.ks[l]) * n.cin[l] * n.cout[l];
     n.bias[l] = base + p;
     p += n.cout[l];
     n.ln_g[l] = n.ln_b[l] = nullptr;
-    if (l < a.n_conv) {
+    if (ln && l < a.n_conv) {
       n.ln_g[l] = base + p;
       p += n.cout[l];
       n.ln_b[l] = base + p;
@@ -126,12 +128,13 @@ __global__ void k_ace_embed(int N, int h, int per_site, const T* __restrict__ em
   }
 }
 
-// One layer on CUDA cores, one warp per row (configuration, site); up to 512 output
-// channels (16 per lane).
+// One layer on CUDA cores, one warp per row (configuration, site); 16 output channels per
+// lane at a time (chunks of 512; a normalised layer has at most 512). The taps run over the
+// k x k box in row-major order, skipping the offsets outside the stencil.
 template <typename T>
 __global__ void __launch_bounds__(32 * kAceRowsGeneric) k_ace_layer(
     Lattice lat, const T* __restrict__ K, const T* __restrict__ bias, const T* __restrict__ gam,
-    const T* __restrict__ bet, int ks, int cin, int cout, int res, int act, double eps,
+    const T* __restrict__ bet, int ks, int stencil, int cin, int cout, int res, int act, double eps,
     const T* __restrict__ in, T* __restrict__ out, long long rows) {
   constexpr int MQ = kAceMaxHMlp / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -140,59 +143,65 @@ __global__ void __launch_bounds__(32 * kAceRowsGeneric) k_ace_layer(
   const int N = lat.N;
   const long long cfg = R / N;
   const int i = (int)(R - cfg * N);
-  T acc[MQ];
-#pragma unroll
-  for (int q = 0; q < MQ; ++q) {
-    const int co = lane + 32 * q;
-    acc[q] = co < cout ? bias[co] : T(0);
-  }
   const int r = (ks - 1) / 2;
-  for (int d = 0; d < ks * ks; ++d) {
-    const int j = site_off(lat, i, d % ks - r, d / ks - r);
-    if (j < 0) continue;  // zero padding past an open edge
-    const T* x = in + ((size_t)cfg * N + j) * cin;
-    const T* w = K + (size_t)d * cin * cout;
-    for (int ci = 0; ci < cin; ++ci) {
-      const T xv = x[ci];
-      const T* wr = w + (size_t)ci * cout;
+  const T* self = in + (size_t)R * cin;
+  T* o = out + (size_t)R * cout;
+  for (int cb = 0; cb < cout; cb += 32 * MQ) {
+    T acc[MQ];
 #pragma unroll
-      for (int q = 0; q < MQ; ++q) {
-        const int co = lane + 32 * q;
-        if (co < cout) acc[q] += xv * wr[co];
+    for (int q = 0; q < MQ; ++q) {
+      const int co = cb + lane + 32 * q;
+      acc[q] = co < cout ? bias[co] : T(0);
+    }
+    int tap = 0;
+    for (int d = 0; d < ks * ks; ++d) {
+      const int dx = d % ks - r, dy = d / ks - r;
+      if (!stencil_has(stencil, ks, dx, dy)) continue;
+      const int t = tap++;
+      const int j = site_off(lat, i, dx, dy);
+      if (j < 0) continue;  // zero padding past an open edge
+      const T* x = in + ((size_t)cfg * N + j) * cin;
+      const T* w = K + (size_t)t * cin * cout;
+      for (int ci = 0; ci < cin; ++ci) {
+        const T xv = x[ci];
+        const T* wr = w + (size_t)ci * cout;
+#pragma unroll
+        for (int q = 0; q < MQ; ++q) {
+          const int co = cb + lane + 32 * q;
+          if (co < cout) acc[q] += xv * wr[co];
+        }
       }
     }
-  }
-  const T* self = in + (size_t)R * cin;
-  T s = T(0);
-#pragma unroll
-  for (int q = 0; q < MQ; ++q) {
-    const int co = lane + 32 * q;
-    if (co < cout) {
-      acc[q] = (res ? self[co] : T(0)) + act_fn<T>(act, acc[q]);
-      s += acc[q];
-    }
-  }
-  if (gam) {  // layer normalisation over this site's channels
-    const T mean = warp_sum(s) / T(cout);
-    T v = T(0);
+    T s = T(0);
 #pragma unroll
     for (int q = 0; q < MQ; ++q) {
-      const int co = lane + 32 * q;
-      if (co < cout) v += (acc[q] - mean) * (acc[q] - mean);
+      const int co = cb + lane + 32 * q;
+      if (co < cout) {
+        acc[q] = (res ? self[co] : T(0)) + act_fn<T>(act, acc[q]);
+        s += acc[q];
+      }
     }
-    v = warp_sum(v) / T(cout);
-    const T inv = T(1) / sqrt(v + T(eps));
+    if (gam) {  // layer normalisation over this site's channels (cout <= 512: one chunk)
+      const T mean = warp_sum(s) / T(cout);
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < MQ; ++q) {
+        const int co = cb + lane + 32 * q;
+        if (co < cout) v += (acc[q] - mean) * (acc[q] - mean);
+      }
+      v = warp_sum(v) / T(cout);
+      const T inv = T(1) / sqrt(v + T(eps));
+#pragma unroll
+      for (int q = 0; q < MQ; ++q) {
+        const int co = cb + lane + 32 * q;
+        if (co < cout) acc[q] = (acc[q] - mean) * inv * gam[co] + bet[co];
+      }
+    }
 #pragma unroll
     for (int q = 0; q < MQ; ++q) {
-      const int co = lane + 32 * q;
-      if (co < cout) acc[q] = (acc[q] - mean) * inv * gam[co] + bet[co];
+      const int co = cb + lane + 32 * q;
+      if (co < cout) o[co] = acc[q];
     }
-  }
-  T* o = out + (size_t)R * cout;
-#pragma unroll
-  for (int q = 0; q < MQ; ++q) {
-    const int co = lane + 32 * q;
-    if (co < cout) o[co] = acc[q];
   }
 }
 
@@ -226,8 +235,8 @@ __global__ void k_ace_build_frag(const float* __restrict__ K, int taps, int cin,
 template <int NTW, int WC, bool LN>
 __global__ void __launch_bounds__(256, (NTW > 18 || NTW == 16 ? 1 : 2)) k_ace_mma(
     Lattice lat, const WFrag* __restrict__ frag, const float* __restrict__ bias, const float* __restrict__ gam,
-    const float* __restrict__ bet, int ks, int cin, int res, int act, float eps, const float* __restrict__ in,
-    float* __restrict__ out, long long rows) {
+    const float* __restrict__ bet, int ks, int stencil, int cin, int res, int act, float eps,
+    const float* __restrict__ in, float* __restrict__ out, long long rows) {
   static_assert(!LN || WC == 1, "the epilogue normalisation needs a row's channels in one warp");
   constexpr int NT = NTW * WC, COUT = 8 * NT, WR = 8 / WC, ROWS = 16 * WR;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -249,13 +258,16 @@ __global__ void __launch_bounds__(256, (NTW > 18 || NTW == 16 ? 1 : 2)) k_ace_mm
     acc[j][3] = b1;
   }
   const int KT = cin / 8, rad = (ks - 1) / 2;
+  int tap = 0;
   for (int d = 0; d < ks * ks; ++d) {
     const int dx = d % ks - rad, dy = d / ks - rad;
+    if (!stencil_has(stencil, ks, dx, dy)) continue;
+    const int tp = tap++;
     const int j0 = v0 ? site_off(lat, i0, dx, dy) : -1;
     const int j1 = v1 ? site_off(lat, i1, dx, dy) : -1;
     const float* p0 = j0 >= 0 ? in + ((size_t)c0 * N + j0) * cin + 2 * t : nullptr;
     const float* p1 = j1 >= 0 ? in + ((size_t)c1 * N + j1) * cin + 2 * t : nullptr;
-    const WFrag* fd = frag + (size_t)d * KT * NT * 32 + (size_t)wc * NTW * 32 + lane;
+    const WFrag* fd = frag + (size_t)tp * KT * NT * 32 + (size_t)wc * NTW * 32 + lane;
     for (int kk = 0; kk < KT; ++kk) {
       const float2 x0 = p0 ? __ldg(reinterpret_cast<const float2*>(p0 + 8 * kk)) : make_float2(0.f, 0.f);
       const float2 x1 = p1 ? __ldg(reinterpret_cast<const float2*>(p1 + 8 * kk)) : make_float2(0.f, 0.f);
@@ -710,37 +722,44 @@ struct MmaPlan {
 MmaPlan plan_of(const scale_arch& a, int l) {
   const int ci = ace_width_in(a, l), co = ace_width_out(a, l);
   if (ci % 8 != 0) return {0, 0};
-  if (l < a.n_conv) {  // conv block with the normalisation in the epilogue
-    if (co == 48 || co == 144 || co == 192) return {co / 8, 1};
+  if (l < a.n_conv) {
+    if (a.family == SCALE_FAMILY_ACE) {  // conv block with the normalisation in the epilogue
+      if (co == 48 || co == 144 || co == 192) return {co / 8, 1};
+      return {0, 0};
+    }
+    if (co == 384) return {24, 2};  // wide SCALE conv (no normalisation)
+    if (co == 640) return {20, 4};
     return {0, 0};
   }
   if (co == 64) return {8, 1};
   if (co == 128) return {16, 1};
   if (co == 256) return {16, 2};
+  if (co == 512) return {16, 4};
+  if (co == 1280) return {20, 8};
   return {0, 0};
 }
 
 size_t frag_layer_bytes(const scale_arch& a, int l) {
-  const size_t k = a.ksize[l];
-  return k * k * (size_t)ace_width_in(a, l) * ace_width_out(a, l) * 8;  // (ci/8)(co/8) 32 lanes x 16 B
+  const size_t taps = stencil_taps(a.stencil, a.ksize[l]);
+  return taps * (size_t)ace_width_in(a, l) * ace_width_out(a, l) * 8;  // (ci/8)(co/8) 32 lanes x 16 B
 }
 
 template <int NTW, int WC, bool LN>
 void run_mma(cudaStream_t st, const Lattice& lat, const WFrag* frag, const float* bias, const float* g,
-             const float* be, int ks, int cin, int res, int act, float eps, const float* in, float* out,
-             long long rows) {
+             const float* be, int ks, int stencil, int cin, int res, int act, float eps, const float* in,
+             float* out, long long rows) {
   constexpr int ROWS = 16 * (8 / WC);
   const long long blocks = (rows + ROWS - 1) / ROWS;
-  k_ace_mma<NTW, WC, LN><<<(unsigned)blocks, 256, 0, st>>>(lat, frag, bias, g, be, ks, cin, res, act, eps, in, out,
-                                                            rows);
+  k_ace_mma<NTW, WC, LN><<<(unsigned)blocks, 256, 0, st>>>(lat, frag, bias, g, be, ks, stencil, cin, res, act, eps,
+                                                            in, out, rows);
 }
 
-bool launch_mma_layer(cudaStream_t st, const Lattice& lat, const MmaPlan& p, bool conv, const WFrag* frag,
-                      const float* bias, const float* g, const float* be, int ks, int cin, int res, int act,
-                      float eps, const float* in, float* out, long long rows) {
+bool launch_mma_layer(cudaStream_t st, const Lattice& lat, const MmaPlan& p, bool ln, const WFrag* frag,
+                      const float* bias, const float* g, const float* be, int ks, int stencil, int cin, int res,
+                      int act, float eps, const float* in, float* out, long long rows) {
 #define SCALE_ACE_MMA(NTW, WC, LN) \
-  run_mma<NTW, WC, LN>(st, lat, frag, bias, g, be, ks, cin, res, act, eps, in, out, rows)
-  if (conv) {
+  run_mma<NTW, WC, LN>(st, lat, frag, bias, g, be, ks, stencil, cin, res, act, eps, in, out, rows)
+  if (ln) {
     if (p.ntw == 6) SCALE_ACE_MMA(6, 1, true);
     else if (p.ntw == 18) SCALE_ACE_MMA(18, 1, true);
     else if (p.ntw == 24) SCALE_ACE_MMA(24, 1, true);
@@ -749,6 +768,10 @@ bool launch_mma_layer(cudaStream_t st, const Lattice& lat, const MmaPlan& p, boo
     if (p.ntw == 8 && p.wc == 1) SCALE_ACE_MMA(8, 1, false);
     else if (p.ntw == 16 && p.wc == 1) SCALE_ACE_MMA(16, 1, false);
     else if (p.ntw == 16 && p.wc == 2) SCALE_ACE_MMA(16, 2, false);
+    else if (p.ntw == 16 && p.wc == 4) SCALE_ACE_MMA(16, 4, false);
+    else if (p.ntw == 20 && p.wc == 4) SCALE_ACE_MMA(20, 4, false);
+    else if (p.ntw == 20 && p.wc == 8) SCALE_ACE_MMA(20, 8, false);
+    else if (p.ntw == 24 && p.wc == 2) SCALE_ACE_MMA(24, 2, false);
     else return false;
   }
 #undef SCALE_ACE_MMA
@@ -797,15 +820,16 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
       } else if (c->ace_mma) {
         const MmaPlan p = plan_of(c->arch, l);
         const WFrag* frag = (const WFrag*)((const char*)c->ace_frag + frag_off);
-        done = launch_mma_layer(c->stream, c->lat, p, conv, frag, net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l],
-                                net.cin[l], conv ? 1 : 0, net.act, (float)net.eps, a, b, rows);
+        done = launch_mma_layer(c->stream, c->lat, p, net.ln_g[l] != nullptr, frag, net.bias[l], net.ln_g[l],
+                                net.ln_b[l], net.ks[l], net.stencil, net.cin[l], c->arch.residual[l], net.act,
+                                (float)net.eps, a, b, rows);
       }
     }
     if (!done) {
       const long long blocks = (rows + kAceRowsGeneric - 1) / kAceRowsGeneric;
       k_ace_layer<T><<<(unsigned)blocks, 32 * kAceRowsGeneric, 0, c->stream>>>(
-          c->lat, net.kernel[l], net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l], net.cin[l], net.cout[l],
-          conv ? 1 : 0, net.act, net.eps, a, b, rows);
+          c->lat, net.kernel[l], net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l], net.stencil, net.cin[l],
+          net.cout[l], c->arch.residual[l], net.act, net.eps, a, b, rows);
     }
     frag_off += frag_layer_bytes(c->arch, l);
     cudaError_t e = cudaGetLastError();
@@ -823,7 +847,12 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
 
 }  // namespace
 
-bool ace_tc_shapes(const scale_arch& a) { return ace_mma_shapes(a) && tc_width(a.h); }
+bool ace_tc_shapes(const scale_arch& a) {
+  if (a.family != SCALE_FAMILY_ACE || a.stencil != SCALE_STENCIL_BOX || !tc_width(a.h)) return false;
+  for (int l = 0; l < a.n_conv; ++l)
+    if (a.ksize[l] != 3) return false;
+  return ace_mma_shapes(a);
+}
 
 bool ace_mma_shapes(const scale_arch& a) {
   for (int l = 0; l < a.n_layers; ++l)
@@ -843,7 +872,7 @@ cudaError_t launch_ace_build(scale_ctx* c) {
   const AceNet<float> net = make_ace_net<float>(c);
   size_t off = 0;
   for (int l = 0; l < c->L; ++l) {
-    const int taps = net.ks[l] * net.ks[l];
+    const int taps = stencil_taps(net.stencil, net.ks[l]);
     if (c->ace_tc && l < net.n_conv) {  // the tcgen05 weight-tile image
       const size_t n = (size_t)taps * 2 * net.cin[l] * net.cout[l];
       const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);

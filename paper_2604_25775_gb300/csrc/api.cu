@@ -40,21 +40,26 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
                 "on nearest-neighbour bonds only)");
   if (s->model == SCALE_MODEL_TJ && s->n_up + s->n_dn > N) return fail("t-J: more electrons than sites");
   if (a->n_layers < 1 || a->n_layers > SCALE_MAX_LAYERS) return fail("n_layers must be in [1, 32]");
-  if (a->family != SCALE_FAMILY_SCALE && a->family != SCALE_FAMILY_ACE) return fail("unknown network family");
-  if (a->family == SCALE_FAMILY_ACE) {
-    if (a->h < 1 || a->h > kAceMaxH) return fail("ACE: h must be in [1, 256]");
-    if (a->n_conv < 1 || a->n_conv > a->n_layers) return fail("ACE: n_conv must be in [1, n_layers]");
-    if (a->n_layers > a->n_conv && (a->h_mlp < 0 || a->h_mlp > kAceMaxHMlp))
-      return fail("ACE: h_mlp must be in [0, 512]");
-    if (!(a->ln_eps >= 0.0)) return fail("ACE: ln_eps must be >= 0");
+  if (a->family != SCALE_FAMILY_SCALE && a->family != SCALE_FAMILY_ACE && a->family != SCALE_FAMILY_WIDE)
+    return fail("unknown network family");
+  if (a->stencil != SCALE_STENCIL_BOX && a->stencil != SCALE_STENCIL_DISK) return fail("unknown stencil");
+  if (a->family == SCALE_FAMILY_ACE || a->family == SCALE_FAMILY_WIDE) {
+    const bool ace = a->family == SCALE_FAMILY_ACE;
+    if (a->h < 1 || a->h > (ace ? kAceMaxH : kWideMaxH))
+      return fail(ace ? "ACE: h must be in [1, 256]" : "wide SCALE: h must be in [1, 1024]");
+    if (a->n_conv < 1 || a->n_conv > a->n_layers) return fail("n_conv must be in [1, n_layers]");
+    if (a->n_layers > a->n_conv && (a->h_mlp < 0 || a->h_mlp > (ace ? kAceMaxHMlp : kWideMaxHMlp)))
+      return fail(ace ? "ACE: h_mlp must be in [0, 512]" : "wide SCALE: h_mlp must be in [0, 2048]");
+    if (ace && !(a->ln_eps >= 0.0)) return fail("ACE: ln_eps must be >= 0");
     for (int l = 0; l < a->n_layers; ++l) {
       const bool conv = l < a->n_conv;
-      if (conv && a->residual[l] != 1) return fail("ACE: conv blocks carry the residual (Eq. ACE)");
+      if (ace && conv && a->residual[l] != 1) return fail("ACE: conv blocks carry the residual (Eq. ACE)");
       if (!conv && (a->ksize[l] != 1 || a->residual[l] != 0))
-        return fail("ACE: layers after the conv blocks are site-wise (kernel size 1, no residual)");
+        return fail("layers after the conv blocks are site-wise (kernel size 1, no residual)");
     }
-  } else if (a->h < 1 || a->h > kMaxH) {
-    return fail("h must be in [1, 64]");
+  } else {
+    if (a->h < 1 || a->h > kMaxH) return fail("h must be in [1, 64]");
+    if (a->stencil != SCALE_STENCIL_BOX) return fail("the SCALE family's cached update needs the box stencil");
   }
   if (a->act != SCALE_ACT_TANH && a->act != SCALE_ACT_SILU) return fail("unknown activation");
   if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED && a->precision != SCALE_PREC_MIXED_BF16)
@@ -75,10 +80,11 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
 int64_t param_count(const scale_system* s, const scale_arch* a) {
   const int64_t N = (int64_t)s->Lx * s->Ly, h = a->h, Ne = s->n_up + s->n_dn;
   int64_t n = (a->per_site_embed ? N : 1) * 4 * h;
-  if (a->family == SCALE_FAMILY_ACE) {
+  if (a->family != SCALE_FAMILY_SCALE) {
+    const bool ln = a->family == SCALE_FAMILY_ACE;
     for (int l = 0; l < a->n_layers; ++l) {
       const int64_t ci = ace_width_in(*a, l), co = ace_width_out(*a, l);
-      n += (int64_t)a->ksize[l] * a->ksize[l] * ci * co + co + (l < a->n_conv ? 2 * co : 0);
+      n += (int64_t)stencil_taps(a->stencil, a->ksize[l]) * ci * co + co + (ln && l < a->n_conv ? 2 * co : 0);
     }
     return n + (int64_t)ace_width_out(*a, a->n_layers - 1) * 2 * Ne + 2 * Ne;
   }
@@ -119,7 +125,7 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   z.cap = (int)(2 * (nb_nn + nb_nnn) + (s->model == SCALE_MODEL_TJ ? nb_nn : 0));
   const size_t P = (size_t)param_count(s, a);
   const size_t k0 = a->ksize[0];
-  const bool ace = a->family == SCALE_FAMILY_ACE;
+  const bool ace = a->family != SCALE_FAMILY_SCALE;
   // ACE activations: the widest layer, or the (hi, lo) halves of a tensor-core conv block
   const size_t hmax = ace ? std::max<size_t>({h, (size_t)ace_width_out(*a, a->n_layers - 1), 2 * h}) : h;
   size_t t = 0;
@@ -194,7 +200,8 @@ scale_status check_loaded(scale_ctx* c) {
 
 scale_status require_lowrank(scale_ctx* c) {
   if (c->ace) {
-    c->err = "the ACE network has no cached update (Sec. II \"ACE\"): use the full-recompute path";
+    c->err = "this network family (ACE, or SCALE at the wide shapes) has no cached update: use the "
+             "full-recompute path";
     return SCALE_EUNSUPPORTED;
   }
   if (!c->lowrank_ok) {
@@ -262,7 +269,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   c->budget = hbm_budget_bytes;
   c->lat = Lattice{sys->Lx, sys->Ly, sys->pbc_x, sys->pbc_y, c->N, sys->n_up, sys->n_dn, c->Ne, sys->model,
                    sys->t, sys->tp, sys->U, sys->J};
-  c->ace = arch->family == SCALE_FAMILY_ACE;
+  c->ace = arch->family != SCALE_FAMILY_SCALE;  // ACE and the wide SCALE shapes: full recompute
   c->lowrank_ok = !c->ace && c->k0 <= 3;
   for (int l = 1; l < c->L; ++l) c->lowrank_ok = c->lowrank_ok && arch->ksize[l] == 1;
   c->hpad = c->h <= 16 ? 16 : (c->h <= 32 ? 32 : 64);
@@ -355,7 +362,7 @@ scale_status scale_set_params(scale_ctx* c, const double* params, const double* 
     k_convert<float, double><<<1024, 256, 0, c->stream>>>(c->M0_64, c->M0_32, 2 * N * Ne);
     SCALE_TRY(c, cudaGetLastError());
   }
-  if (c->ace) {  // the ACE network has no cached update: only its tensor-core fragments
+  if (c->ace) {  // no cached update (ACE, wide SCALE): only the tensor-core fragments
     SCALE_TRY(c, launch_ace_build(c));
     c->params_set = true;
     c->B = 0;

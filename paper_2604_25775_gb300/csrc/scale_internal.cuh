@@ -198,8 +198,21 @@ namespace scale {
 // ACE widths: the conv blocks keep h, the site-wise layers after them have h_mlp.
 constexpr int kAceMaxH = 256;
 constexpr int kAceMaxHMlp = 512;
+constexpr int kWideMaxH = 1024;
+constexpr int kWideMaxHMlp = 2048;
 inline int ace_width_out(const scale_arch& a, int l) {
   return l < a.n_conv ? a.h : (a.h_mlp > 0 ? a.h_mlp : a.h);
+}
+// Taps of a k x k layer under the network's stencil (row-major box order).
+__host__ __device__ inline bool stencil_has(int stencil, int k, int dx, int dy) {
+  const int r = (k - 1) / 2;
+  return stencil == SCALE_STENCIL_BOX || dx * dx + dy * dy <= r * r;
+}
+inline int stencil_taps(int stencil, int k) {
+  int n = 0;
+  for (int dy = -(k - 1) / 2; dy <= (k - 1) / 2; ++dy)
+    for (int dx = -(k - 1) / 2; dx <= (k - 1) / 2; ++dx) n += stencil_has(stencil, k, dx, dy);
+  return n;
 }
 inline int ace_width_in(const scale_arch& a, int l) { return l == 0 ? a.h : ace_width_out(a, l - 1); }
 // Bytes of the tensor-core fragments of every ACE layer (0 when a shape has none).

@@ -6,6 +6,10 @@ their own (one GPU, inputs resident on the device, CUDA events on the context's 
         layers at 256) on the 16x16 torus, 112 + 112: the full-recompute local energy of
         `walkers` walkers (every psi(n') a fresh forward and FP64 LU), and the amplitudes of
         1024 configurations (forward + determinant).
+    python -m paper_2604_25775_gb300.next_bench wide [walkers]
+        Table tab:model SCALE-L (plus stencil, conv 384, site-wise 4 x 512) local energies on
+        the 16x16 torus and SCALE-XL (conv 640, site-wise 4 x 1280) amplitudes on the 32x32
+        torus, both by full recompute.
     python -m paper_2604_25775_gb300.next_bench symmetry [walkers]
         The symmetry-projected amplitude (App. "Symmetry Projection") over the 256
         translations of the SCALE 16x16 bench workload.
@@ -82,10 +86,57 @@ def run_symmetry(walkers: int = 1024) -> dict:
     return out
 
 
+def run_wide(walkers: int = 8) -> dict:
+    """SCALE-L (plus stencil, conv 384, site-wise 4 x 512) local energies on the 16x16 torus
+    and SCALE-XL (conv 640, site-wise 4 x 1280) amplitudes on the 32x32 torus, full recompute."""
+    import torch
+    out = {}
+    pl = I.workload("scale_l16x16")
+    ctx = Bd.make_context(pl, I.random_params(pl, 1262, 0.02), I.plane_wave_M0(pl), 1024)
+    occ = torch.from_numpy(I.random_configs(pl, 1024, 5712)).cuda()
+    a, b = _events()
+    ctx.scale_load(occ)
+    torch.cuda.synchronize()
+    a.record()
+    ctx.scale_load(occ)
+    b.record()
+    torch.cuda.synchronize()
+    load_ms = a.elapsed_time(b)
+    ctx.scale_load(occ[:walkers].contiguous())
+    e = torch.empty(walkers, dtype=torch.float64, device="cuda")
+    ctx.scale_local_energy(e, Bd.PATH_FULL)
+    torch.cuda.synchronize()
+    a.record()
+    ctx.scale_local_energy(e, Bd.PATH_FULL)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out["scale_l16x16"] = {"walkers": walkers, "ms": ms, "eloc_per_s": walkers / (ms / 1e3),
+                           "amplitudes_per_s": 1024 / (load_ms / 1e3),
+                           "finite": bool(torch.isfinite(e).all().item())}
+    ctx.close()
+    px = I.workload("scale_xl32x32")
+    nx = 128
+    ctx = Bd.make_context(px, I.random_params(px, 1264, 0.02), I.plane_wave_M0(px), nx)
+    occ = torch.from_numpy(I.random_configs(px, nx, 5714)).cuda()
+    ctx.scale_load(occ)
+    torch.cuda.synchronize()
+    a.record()
+    ctx.scale_load(occ)
+    b.record()
+    torch.cuda.synchronize()
+    xl_ms = a.elapsed_time(b)
+    out["scale_xl32x32"] = {"configurations": nx, "ms": xl_ms, "amplitudes_per_s": nx / (xl_ms / 1e3)}
+    ctx.close()
+    return out
+
+
 if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "ace"
     n = int(sys.argv[2]) if len(sys.argv) > 2 else None
     if what == "ace":
         print(json.dumps(run_ace(n or 16)))
+    elif what == "wide":
+        print(json.dumps(run_wide(n or 8)))
     else:
         print(json.dumps(run_symmetry(n or 1024)))

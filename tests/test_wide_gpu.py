@@ -1,0 +1,100 @@
+"""GPU parity of the wide SCALE shapes of Table tab:model (SCALE-L's plus-shaped 13-site
+stencil, conv and site-wise widths up to 640 / 1280) on the full-recompute path, against the
+FP64 oracle through the C ABI.
+
+Tolerances as for the other paths: FP64 <= 1e-10 relative (cond(Phi) < 1e6); mixed (tensor-core
+or FP32 layers, FP64 Slater matrices and LU) <= 1e-4 on samples with cond < 1e3 (1e4 at 16x16
+and above), every sample within cond * c * u; mixed local energies against their term scale.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_25775_gb300 import binding as Bd
+from paper_2604_25775_gb300 import inputs as I
+from tests.gpu_common import conditioning, eloc_term_scale, rel_err, setup
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(name, gpu, ora, cond, tol, cond_ok, min_good=1):
+    err = rel_err(gpu, ora)
+    good = cond < cond_ok
+    unit, c = (2.0 ** -24, 8.0) if tol > 1e-8 else (2.0 ** -53, 1e3)
+    print(f"{name}: n={len(err)} good={good.sum()} max_err(good)={err[good].max() if good.any() else 0:.3e} "
+          f"max_err={err.max():.3e}")
+    assert good.sum() >= min_good
+    if good.any():
+        assert err[good].max() <= tol
+    assert np.all(err <= np.maximum(tol, cond * c * unit))
+
+
+@pytest.mark.parametrize("variant", ["torus", "open_tj", "box_stencil"])
+def test_wide_fp64_plus_stencil(variant):
+    pb = I.workload("scale_l5x5")
+    if variant == "open_tj":
+        pb = pb.replace(pbc_y=0, model=I.MODEL_TJ, U=0.0, J=0.4, n_up=7, n_dn=7)
+    elif variant == "box_stencil":
+        pb = pb.replace(stencil=I.STENCIL_BOX, ksize=[3, 1, 1], tp=-0.2)
+    ctx, ora, occ, st = setup(pb, 48, 1260, 5710, scale=0.3)
+    cond = conditioning(ora, occ)
+    la, sg = ctx.log_psi()
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    la_o, sg_o = ora.log_psi(occ)
+    good = cond < 1e6
+    assert (sg[good] == sg_o[good]).all()
+    assert np.abs(la[good] - la_o[good]).max() <= 1e-10
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    _check(f"wide fp64 {variant}", e, e_o, cond, 1e-10, 1e6, min_good=24)
+
+
+def test_wide_mixed_8x8_generic_conv():
+    """Plus stencil at width 96 (FP32 CUDA-core conv), site-wise 128 on the tensor cores."""
+    pb = I.workload("scale_l8x8")
+    ctx, ora, occ, st = setup(pb, 16, 1261, 5711, scale=0.05)
+    cond = conditioning(ora, occ)
+    la = ctx.log_psi()[0].cpu().numpy()
+    la_o, _ = ora.log_psi(occ)
+    _check("scale_l8x8 log|psi|", la, la_o, cond, 1e-4, 1e3)
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    scale = np.maximum(eloc_term_scale(ora, occ), 1.0)
+    _check("scale_l8x8 E_loc / term scale", e / scale, e_o / scale, cond, 1e-4, 1e3)
+
+
+def test_scale_l_table_widths():
+    """Table tab:model SCALE-L widths (plus stencil, conv 384 and site-wise 4 x 512, all on the
+    tensor cores): log|psi| of 4 samples on the 16x16 torus and the local energies of 2 walkers
+    on an 8x8 torus with the same network shape."""
+    pb = I.workload("scale_l16x16")
+    ctx, ora, occ, st = setup(pb, 4, 1262, 5712, scale=0.02)
+    cond = conditioning(ora, occ)
+    la = ctx.log_psi()[0].cpu().numpy()
+    la_o, _ = ora.log_psi(occ)
+    _check("scale_l16x16 log|psi|", la, la_o, cond, 1e-4, 1e4, min_good=0)
+    p8 = pb.replace(Lx=8, Ly=8, n_up=28, n_dn=28)
+    ctx8, ora8, occ8, _ = setup(p8, 2, 1263, 5713, scale=0.02)
+    cond8 = conditioning(ora8, occ8)
+    e = ctx8.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora8.local_energy(occ8)
+    scale = np.maximum(eloc_term_scale(ora8, occ8), 1.0)
+    _check("SCALE-L widths 8x8 E_loc / term scale", e / scale, e_o / scale, cond8, 1e-4, 1e3, min_good=0)
+
+
+def test_scale_xl_table_widths():
+    """Table tab:model SCALE-XL (32x32, conv 640 and site-wise 4 x 1280 on the tensor cores):
+    log|psi| of 2 samples (the oracle takes about ten seconds per amplitude)."""
+    pb = I.workload("scale_xl32x32")
+    ctx, ora, occ, st = setup(pb, 2, 1264, 5714, scale=0.02)
+    cond = conditioning(ora, occ)
+    la = ctx.log_psi()[0].cpu().numpy()
+    la_o, _ = ora.log_psi(occ)
+    _check("scale_xl32x32 log|psi|", la, la_o, cond, 1e-4, 1e4, min_good=0)
+
+
+def test_wide_rejects_cached_update_entry_points():
+    pb = I.workload("scale_l5x5")
+    ctx, ora, occ, st = setup(pb, 4, 1265, 5715)
+    with pytest.raises(Bd.ScaleError) as e:
+        ctx.local_energy(Bd.PATH_LOWRANK)
+    assert e.value.status == Bd.EUNSUPPORTED
