@@ -39,6 +39,28 @@ struct ArgMax {
   int i;
 };
 
+// Pivot search on integer keys: the bit pattern of |x| orders like |x| (and puts NaN above
+// every number), so the search runs on the integer pipe instead of FP64 compares.
+template <typename TW>
+struct AbsKey;
+template <>
+struct AbsKey<double> {
+  using T = unsigned long long;
+  __device__ static T of(double x) { return (T)__double_as_longlong(x) & 0x7fffffffffffffffull; }
+};
+template <>
+struct AbsKey<float> {
+  using T = unsigned int;
+  __device__ static T of(float x) { return (T)__float_as_uint(x) & 0x7fffffffu; }
+};
+template <typename K>
+__device__ __forceinline__ void key_merge(K& k, int& i, K k2, int i2) {
+  if (k2 > k || (k2 == k && i2 < i)) {
+    k = k2;
+    i = i2;
+  }
+}
+
 template <typename TW>
 __device__ __forceinline__ void argmax_merge(TW& v, int& i, TW v2, int i2) {
   if (v2 > v || (v2 == v && i2 < i)) {
@@ -57,15 +79,19 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
                                                  TOUT* __restrict__ binv, double* __restrict__ logabs_out,
                                                  int32_t* __restrict__ sign_out, int32_t* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
-  TW* panel = reinterpret_cast<TW*>(smem_raw);   // [n][W]
+  using KeyT = typename AbsKey<TW>::T;
+  double* pabs = reinterpret_cast<double*>(smem_raw);  // [n] |pivot| of column k (log taken at the end)
+  TW* panel = reinterpret_cast<TW*>(pabs + n);         // [n][W]
   TW* prow = panel + (size_t)n * W;              // [W][n]
   TW* colk = prow + (size_t)W * n;               // [n]
   TW* rowp = colk + n;                           // [W]
   int* piv = reinterpret_cast<int*>(rowp + W);   // [n] pivot row of column k
   int* qinv = piv + n;                           // [n] column whose pivot row is r
   unsigned char* used = reinterpret_cast<unsigned char*>(qinv + n);  // [n]
+  __shared__ KeyT red_k[TH / 32];
   __shared__ TW red_v[TH / 32];
   __shared__ int red_i[TH / 32];
+  __shared__ double red_l[TH / 32];
   __shared__ int s_p;
   __shared__ int s_singular;
 
@@ -76,8 +102,8 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
 
   for (int i = tid; i < n; i += TH) used[i] = 0;
   if (tid == 0) s_singular = 0;
-  double logdet = 0.0;  // kept by thread 0
-  int sgn = 1;
+  double logdet = 0.0;  // inverse mode: kept by thread 0
+  int sgn = 1;          // kept by thread 0
   __syncthreads();
 
   for (int K0 = 0; K0 < n; K0 += W) {
@@ -90,29 +116,46 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
     __syncthreads();
     for (int jj = 0; jj < w; ++jj) {
       const int k = K0 + jj;
-      // pivot search over unpivoted rows
-      TW bv = TW(-1);
+      // pivot search over unpivoted rows (largest |value|, ties to the lowest row); the
+      // determinant-only kernels compare integer keys, the inverse kernels FP values
       int bi = n;
-      for (int i = tid; i < n; i += TH) {
-        if (used[i]) continue;
-        const TW v = fabs(panel[i * W + jj]);
-        argmax_merge(bv, bi, v, i);
+      if constexpr (!kInverse) {
+        KeyT bk = 0;
+        for (int i = tid; i < n; i += TH) {
+          if (used[i]) continue;
+          key_merge(bk, bi, AbsKey<TW>::of(panel[i * W + jj]), i);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const KeyT k2 = __shfl_down_sync(0xffffffffu, bk, off);
+          const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
+          key_merge(bk, bi, k2, i2);
+        }
+        if (lane == 0) red_k[warp] = bk;
+      } else {
+        TW bv = TW(-1);
+        for (int i = tid; i < n; i += TH) {
+          if (used[i]) continue;
+          argmax_merge(bv, bi, TW(fabs(panel[i * W + jj])), i);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const TW v2 = __shfl_down_sync(0xffffffffu, bv, off);
+          const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
+          argmax_merge(bv, bi, v2, i2);
+        }
+        if (lane == 0) red_v[warp] = bv;
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        const TW v2 = __shfl_down_sync(0xffffffffu, bv, off);
-        const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
-        argmax_merge(bv, bi, v2, i2);
-      }
-      if (lane == 0) {
-        red_v[warp] = bv;
-        red_i[warp] = bi;
-      }
+      if (lane == 0) red_i[warp] = bi;
       __syncthreads();
       if (tid == 0) {
-        TW v = red_v[0];
         int i = red_i[0];
-        for (int q = 1; q < TH / 32; ++q) argmax_merge(v, i, red_v[q], red_i[q]);
-        if (!(v > TW(0)) || i >= n) {
+        if constexpr (!kInverse) {
+          KeyT kk = red_k[0];
+          for (int q = 1; q < TH / 32; ++q) key_merge(kk, i, red_k[q], red_i[q]);
+        } else {
+          TW v = red_v[0];
+          for (int q = 1; q < TH / 32; ++q) argmax_merge(v, i, red_v[q], red_i[q]);
+        }
+        if (i >= n || !(fabs(panel[i * W + jj]) > TW(0))) {
           s_singular = 1;
           i = 0;
         }
@@ -129,7 +172,8 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
       if (tid == 0) {
         piv[k] = p;
         used[p] = 1;
-        logdet += log(fabs((double)pv));
+        if constexpr (kInverse) logdet += log(fabs((double)pv));
+        else pabs[k] = fabs((double)pv);
         if (pv < TW(0)) sgn = -sgn;
       }
       __syncthreads();
@@ -161,6 +205,19 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
 #pragma unroll
       for (int j = 0; j < W; ++j) u[j] = (j < w) ? panel[i * W + j] - ((piv[K0 + j] == i) ? TW(1) : TW(0)) : TW(0);
       TW* Ai = A + (size_t)i * n;
+      if constexpr (!kInverse) {
+        // determinant only: every column from c_lo on lies right of the panel; one column
+        // per lane (several matrices per SM supply the parallelism), so a strip wastes at most
+        // 31 lanes instead of 63
+        for (int c = c_lo + lane; c < n; c += 32) {
+          TW a1 = Ai[c];
+#pragma unroll
+          for (int j = 0; j < W; ++j)
+            if (j < w) a1 += u[j] * prow[j * n + c];
+          Ai[c] = a1;
+        }
+        continue;
+      }
       for (int c = c_lo + lane; c < n; c += 64) {
         const int c2 = c + 32;
         const bool in1 = !(c >= K0 && c < K0 + w);
@@ -186,6 +243,17 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
     __syncthreads();
   }
 
+  // determinant only: log|det| = sum of log|pivot|, one log per thread
+  if constexpr (!kInverse) {
+    double part = 0.0;
+    if (!s_singular)
+      for (int k = tid; k < n; k += TH) part += log(pabs[k]);
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if (lane == 0) red_l[warp] = part;
+    __syncthreads();
+    if (tid == 0)
+      for (int q = 0; q < TH / 32; ++q) logdet += red_l[q];
+  }
   if (tid == 0) {
     int st = 0;
     double la = logdet;
@@ -476,7 +544,7 @@ cudaError_t run_gj_cluster(cudaStream_t st, double* mats, int n, int B, const in
 template <typename TW, typename TOUT, bool kInverse, int W, int TH = kThreads>
 cudaError_t run_gj(cudaStream_t st, TW* mats, int n, int B, const int32_t* list, TOUT* binv, double* la,
                    int32_t* sg, int32_t* status) {
-  const size_t smem = sizeof(TW) * ((size_t)2 * n * W + n + W) + sizeof(int) * 2 * n + n + 16;
+  const size_t smem = sizeof(double) * n + sizeof(TW) * ((size_t)2 * n * W + n + W) + sizeof(int) * 2 * n + n + 16;
   auto kern = k_gj<TW, TOUT, kInverse, W, TH>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -511,15 +579,15 @@ cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32
     if (n > 448) return run_gj<double, float, true, 8>(c->stream, A, n, B, list, (float*)Binv, logabs, sign, status);
     return run_gj<double, float, true, 16>(c->stream, A, n, B, list, (float*)Binv, logabs, sign, status);
   }
-  if (n > 448) return run_gj<double, double, false, 8>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
+  if (n > 448) return run_gj<double, double, false, 8, 512>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
   return run_gj<double, double, false, 8, 256>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
 }
 
 // Determinant only, FP32 working precision (full-recompute path in mixed mode).
 cudaError_t launch_det_f32(scale_ctx* c, float* mats, int n, int B, double* logabs, int32_t* sign) {
   if (B <= 0) return cudaSuccess;
-  if (n > 448) return run_gj<float, float, false, 8>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
-  return run_gj<float, float, false, 16>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
+  if (n > 448) return run_gj<float, float, false, 8, 512>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
+  return run_gj<float, float, false, 16, 256>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
 }
 
 }  // namespace scale
