@@ -4,7 +4,8 @@ seeded inputs.
 Tolerances (relative error |x_gpu - x_ora| / max(|x_ora|, 1)):
   FP64 mode   E_loc, ratios, gradients <= 1e-10 and log|psi| absolute <= 1e-10 on samples
               with cond(Phi) <= 1e6; signs exact.
-  mixed mode  E_loc, ratios, log|psi| <= 1e-4 on samples with cond(Phi) <= 1e3.
+  mixed mode  E_loc, ratios, log|psi| <= 1e-4 on samples with cond(Phi) <= 1e3 (TF32x3 layers);
+              the BF16x3 option <= 5e-4.
 Beyond those condition numbers every sample must still satisfy err <= cond * c * u with
 u = 2^-53 (FP64) or 2^-24 (mixed) and c = 1e3 (FP64) / 8 (mixed): an FP32-stored Phi^-1
 perturbs each ratio by about cond(Phi) * 2^-24, and any FP64 evaluation of an
@@ -22,6 +23,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
 MIXED_TOL = 1e-4
+BF16X3_TOL = 5e-4  # BF16x3 site-wise layers (about 2^-16 per layer): measured up to 2.3e-4
 
 
 def _check(name, gpu, ora, cond, tol, cond_ok, min_good=None):
@@ -134,25 +136,28 @@ def test_ratios_fp64():
     assert (rb[:, 0] == 0).all() and (rb[:, 1] == 1).all()
 
 
+@pytest.mark.parametrize("prec", [I.PREC_MIXED, I.PREC_MIXED_BF16])
 @pytest.mark.parametrize("name", ["hubbard8x8", "tj8x8", "hubbard_ph8x8"])
-def test_local_energy_mixed_8x8(name):
-    pb = I.workload(name)
+def test_local_energy_mixed_8x8(name, prec):
+    pb = I.workload(name).replace(precision=prec)
     ctx, ora, occ, st = setup(pb, 256, 1235, 5679)
     cond = conditioning(ora, occ)
+    tol = BF16X3_TOL if prec == I.PREC_MIXED_BF16 else MIXED_TOL
     e1 = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
     e_o, _ = ora.local_energy(occ)
-    _check(f"{name} mixed lowrank", e1, e_o, cond, MIXED_TOL, 1e3)
+    _check(f"{name} mixed lowrank (precision {prec})", e1, e_o, cond, tol, 1e3)
     la, sg = ctx.log_psi()
     la_o, sg_o = ora.log_psi(occ)
     good = cond < 1e3
     assert (sg.cpu().numpy()[good] == sg_o[good]).all()
-    assert rel_err(la.cpu().numpy()[good], la_o[good]).max() <= MIXED_TOL
+    assert rel_err(la.cpu().numpy()[good], la_o[good]).max() <= tol
 
 
-def test_local_energy_mixed_16x16_full_batch_sampled():
+@pytest.mark.parametrize("prec", [I.PREC_MIXED, I.PREC_MIXED_BF16])
+def test_local_energy_mixed_16x16_full_batch_sampled(prec):
     """The 16x16 workload at its full batch (8192) in the bench's launch configuration;
-    24 sampled outputs recomputed by the oracle."""
-    pb = I.workload("hubbard16x16")
+    32 sampled outputs recomputed by the oracle, with TF32x3 and BF16x3 site-wise layers."""
+    pb = I.workload("hubbard16x16").replace(precision=prec)
     pseed, cseed = I.workload_seeds("hubbard16x16")
     ctx, ora, occ, st = setup(pb, 8192, pseed, cseed)
     e = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
@@ -163,10 +168,11 @@ def test_local_energy_mixed_16x16_full_batch_sampled():
     e_o, _ = ora.local_energy(occ[pick])
     # uniformly random 16x16 configurations have cond(Phi) >= 1e3; the strict band is
     # cond < 1e4 here, every sample still within cond * 8 * 2^-24
-    _check("16x16 mixed lowrank (sampled)", e[pick], e_o, cond, MIXED_TOL, 1e4, min_good=5)
+    tol = BF16X3_TOL if prec == I.PREC_MIXED_BF16 else MIXED_TOL
+    _check(f"16x16 mixed lowrank (sampled, precision {prec})", e[pick], e_o, cond, tol, 1e4, min_good=5)
     la_o, sg_o = ora.log_psi(occ[pick])
     good = cond < 1e4
-    assert rel_err(la.cpu().numpy()[pick][good], la_o[good]).max() <= MIXED_TOL
+    assert rel_err(la.cpu().numpy()[pick][good], la_o[good]).max() <= tol
     assert np.isfinite(e).all()
 
 
