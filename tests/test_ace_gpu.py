@@ -127,3 +127,30 @@ def test_ace_rejects_cached_update_entry_points():
         ctx.scale_grad_logpsi(torch.empty((8, ctx.P), dtype=torch.float64, device="cuda"))
     # the context still answers after the refusals
     assert np.isfinite(ctx.log_psi()[0].cpu().numpy()).any()
+
+
+@pytest.mark.parametrize("case", ["open_ragged", "polarised", "single"])
+def test_ace_mixed_edges(case):
+    """The tensor-core conv at its edges: open boundaries (zero-filled gathers), a batch whose
+    rows end inside a 128-row tile (3 x 64 = 192 rows), a spin-polarised sector (no down
+    electrons: one spin's Slater-matrix tiles only) and a single configuration."""
+    pb = I.workload("ace8x8")
+    B = 3
+    if case == "open_ragged":
+        pb = pb.replace(pbc_x=0, pbc_y=0)
+    elif case == "polarised":
+        pb = pb.replace(n_up=20, n_dn=0, U=0.0)
+    else:
+        B = 1
+    ctx, ora, occ, st = setup(pb, B, 1256, 5706, scale=0.05)
+    cond = conditioning(ora, occ)
+    la, sg = ctx.log_psi()
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    la_o, sg_o = ora.log_psi(occ)
+    _check(f"ace8x8 {case} log|psi|", la, la_o, cond, 1e-4, 1e3, min_good=0)
+    good = cond < 1e3
+    assert (sg[good] == sg_o[good]).all()
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    scale = np.maximum(eloc_term_scale(ora, occ), 1.0)
+    _check(f"ace8x8 {case} E_loc / term scale", e / scale, e_o / scale, cond, 1e-4, 1e3, min_good=0)

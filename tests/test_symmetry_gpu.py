@@ -145,3 +145,11 @@ def test_sym_mixed_16x16_translations():
     perms = I.symmetry_group(pb, translations=True)
     # uniformly random 16x16 configurations have cond(Phi) >= 1e3: the strict band is 1e4 here
     _compare("mixed 16x16", pb, ctx, ora, occ, perms, _momentum_pi(pb, perms), 1e-4, 1e4, min_good=2)
+
+
+def test_sym_single_walker_and_single_element():
+    """One walker, and a group of one translation (no identity): psi_sym = Pi psi(t n)."""
+    pb = I.workload("hubbard4x4")
+    ctx, ora, occ, _ = setup(pb, 1, 1247, 5697)
+    perms = I.symmetry_group(pb)[3:4].copy()
+    _compare("fp64 single", pb, ctx, ora, occ, perms, np.array([-1.0]), 1e-10, 1e6, min_good=0)

@@ -98,3 +98,18 @@ def test_wide_rejects_cached_update_entry_points():
     with pytest.raises(Bd.ScaleError) as e:
         ctx.local_energy(Bd.PATH_LOWRANK)
     assert e.value.status == Bd.EUNSUPPORTED
+
+
+def test_wide_open_ragged_single():
+    """Plus stencil with open boundaries on a single configuration (the stencil's zero padding
+    on both axes, one partial tile of every layer)."""
+    pb = I.workload("scale_l8x8").replace(pbc_x=0, pbc_y=0)
+    ctx, ora, occ, st = setup(pb, 1, 1266, 5716, scale=0.05)
+    cond = conditioning(ora, occ)
+    la = ctx.log_psi()[0].cpu().numpy()
+    la_o, _ = ora.log_psi(occ)
+    _check("scale_l8x8 open single log|psi|", la, la_o, cond, 1e-4, 1e3, min_good=0)
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    scale = np.maximum(eloc_term_scale(ora, occ), 1.0)
+    _check("scale_l8x8 open single E_loc / term scale", e / scale, e_o / scale, cond, 1e-4, 1e3, min_good=0)
