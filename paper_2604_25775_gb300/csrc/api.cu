@@ -59,7 +59,6 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
     }
   } else {
     if (a->h < 1 || a->h > kMaxH) return fail("h must be in [1, 64]");
-    if (a->stencil != SCALE_STENCIL_BOX) return fail("the SCALE family's cached update needs the box stencil");
   }
   if (a->act != SCALE_ACT_TANH && a->act != SCALE_ACT_SILU) return fail("unknown activation");
   if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED && a->precision != SCALE_PREC_MIXED_BF16)
@@ -88,7 +87,7 @@ int64_t param_count(const scale_system* s, const scale_arch* a) {
     }
     return n + (int64_t)ace_width_out(*a, a->n_layers - 1) * 2 * Ne + 2 * Ne;
   }
-  for (int l = 0; l < a->n_layers; ++l) n += (int64_t)a->ksize[l] * a->ksize[l] * h * h + h;
+  for (int l = 0; l < a->n_layers; ++l) n += (int64_t)stencil_taps(a->stencil, a->ksize[l]) * h * h + h;
   return n + h * 2 * Ne + 2 * Ne;
 }
 
@@ -131,7 +130,7 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   size_t t = 0;
   t += P * 8 + (T == 4 ? P * 4 : 0);
   t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0) + 2 * N * Ne * T;
-  t += ace ? 16 : (a->per_site_embed ? N : 1) * 4 * k0 * k0 * h * T;  // KE
+  t += ace ? 16 : (a->per_site_embed ? N : 1) * 4 * stencil_taps(a->stencil, (int)k0) * h * T;  // KE
   t += (nb_nn + nb_nnn) * 2 * 4;
   t += (size_t)B * (N + Ne * 4 + 2 * N * 4);
   t += ace ? 32 : (size_t)B * N * h * T * 2;  // z0, HL
@@ -205,8 +204,8 @@ scale_status require_lowrank(scale_ctx* c) {
     return SCALE_EUNSUPPORTED;
   }
   if (!c->lowrank_ok) {
-    c->err = "low-rank path needs the SCALE layer layout: layer 0 with kernel size 1 or 3 and "
-             "site-wise layers (kernel size 1) after it; use the full-recompute path";
+    c->err = "low-rank path needs the SCALE layer layout: layer 0 a 1x1 or 3x3 box or the 5x5 plus "
+             "(disk stencil), site-wise layers (kernel size 1) after it; use the full-recompute path";
     return SCALE_EUNSUPPORTED;
   }
   return SCALE_OK;
@@ -270,7 +269,9 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   c->lat = Lattice{sys->Lx, sys->Ly, sys->pbc_x, sys->pbc_y, c->N, sys->n_up, sys->n_dn, c->Ne, sys->model,
                    sys->t, sys->tp, sys->U, sys->J};
   c->ace = arch->family != SCALE_FAMILY_SCALE;  // ACE and the wide SCALE shapes: full recompute
-  c->lowrank_ok = !c->ace && c->k0 <= 3;
+  // the cached update: layer 0 a 3x3 box or (disk stencil) up to the 13-site plus, so that the
+  // pairs (touched site, tap) of a hop fit one warp and its affected sites kSMax
+  c->lowrank_ok = !c->ace && (c->k0 <= 3 || (c->k0 == 5 && arch->stencil == SCALE_STENCIL_DISK));
   for (int l = 1; l < c->L; ++l) c->lowrank_ok = c->lowrank_ok && arch->ksize[l] == 1;
   c->hpad = c->h <= 16 ? 16 : (c->h <= 32 ? 32 : 64);
   c->use_mma = !c->fp64 && c->lowrank_ok && c->h == c->hpad;
@@ -294,7 +295,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A((char**)&c->M0b, 2 * N * Ne * T);
   const bool ace = c->ace;
   const size_t hmax = ace ? std::max<size_t>(c->hmax, 2 * h) : h;
-  A((char**)&c->KE, ace ? 16 : Ns * 4 * c->k0 * c->k0 * h * T);
+  A((char**)&c->KE, ace ? 16 : Ns * 4 * stencil_taps(arch->stencil, c->k0) * h * T);
   A(&c->bonds, std::max<size_t>(bonds.size(), 2) * 4);
   A(&c->occ, B * N);
   A(&c->orb_of_slot, B * Ne * 4);
@@ -504,8 +505,8 @@ scale_status scale_grad_logpsi(scale_ctx* c, double* grad, int32_t recompute) {
   scale_status s = check_loaded(c);
   if (s != SCALE_OK) return s;
   if (!grad) return SCALE_EINVAL;
-  if (c->ace) {
-    c->err = "the per-sample gradient covers the SCALE family";
+  if (c->ace || c->arch.stencil != SCALE_STENCIL_BOX) {
+    c->err = "the per-sample gradient covers the SCALE family with the box stencil";
     return SCALE_EUNSUPPORTED;
   }
   SCALE_TRY(c, launch_grad(c, grad, recompute));

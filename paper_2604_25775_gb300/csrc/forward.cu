@@ -32,11 +32,14 @@ __global__ void k_layer(Lattice lat, Net<T> net, int l, const int8_t* __restrict
   T z = net.bias[l][c];
   const int8_t* ob = occ + (size_t)b * N;
   const T* ib = in ? in + (size_t)b * N * h : nullptr;
+  int tap = 0;
   for (int ky = 0; ky < k; ++ky)
     for (int kx = 0; kx < k; ++kx) {
+      if (!stencil_in(net.stencil, k, kx - r, ky - r)) continue;
+      const int tp = tap++;
       const int j = site_off(lat, i, kx - r, ky - r);
       if (j < 0) continue;
-      const T* w = K + (size_t)(ky * k + kx) * h * h + c;
+      const T* w = K + (size_t)tp * h * h + c;
       const T* x = (l == 0) ? net.embed + ((size_t)(net.per_site ? j * 4 : 0) + (ob[j] & 3)) * h
                             : ib + (size_t)j * h;
 #pragma unroll 8
@@ -170,7 +173,7 @@ __global__ void k_phi(Lattice lat, Net<T> net, const int8_t* __restrict__ occ, c
 // state n on site t, for every stencil offset d.
 template <typename T>
 __global__ void k_build_ke(Net<T> net, int Ns, T* __restrict__ KE) {
-  const int h = net.h, k = net.ksize[0], kk = k * k;
+  const int h = net.h, kk = net.taps0;
   const size_t total = (size_t)Ns * 4 * kk * h;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int c = q % h;
@@ -324,6 +327,8 @@ Net<T> make_net(scale_ctx* c) {
   n.L = c->L;
   n.act = c->arch.act;
   n.per_site = c->arch.per_site_embed;
+  n.stencil = c->arch.stencil;
+  n.taps0 = stencil_taps(c->arch.stencil, c->arch.ksize[0]);
   const T* base = c->fp64 ? (const T*)c->params64 : (const T*)c->params32;
   int64_t p = 0;
   n.embed = base + p;
@@ -332,7 +337,7 @@ Net<T> make_net(scale_ctx* c) {
     n.ksize[l] = c->arch.ksize[l];
     n.resid[l] = c->arch.residual[l];
     n.kernel[l] = base + p;
-    p += (int64_t)n.ksize[l] * n.ksize[l] * c->h * c->h;
+    p += (int64_t)stencil_taps(c->arch.stencil, n.ksize[l]) * c->h * c->h;
     n.bias[l] = base + p;
     p += c->h;
   }
@@ -432,7 +437,7 @@ cudaError_t launch_slots_list(scale_ctx* c, const int32_t* list, int B) {
 
 cudaError_t launch_build_ke(scale_ctx* c) {
   const int Ns = c->arch.per_site_embed ? c->N : 1;
-  const size_t total = (size_t)Ns * 4 * c->k0 * c->k0 * c->h;
+  const size_t total = (size_t)Ns * 4 * stencil_taps(c->arch.stencil, c->k0) * c->h;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
   if (c->fp64)
     k_build_ke<double><<<blocks, 256, 0, c->stream>>>(make_net<double>(c), Ns, (double*)c->KE);

@@ -21,7 +21,7 @@
 
 namespace scale {
 
-constexpr int kSMax = 18;  // affected sites for two touched sites and a 3x3 stencil
+constexpr int kSMax = 18;  // affected sites for two touched sites and a 3x3 box or the 13-site plus
 constexpr int kRMax = 32;  // electrons on the affected sites (lane per column)
 
 template <typename T, int H>
@@ -29,7 +29,7 @@ struct MoveScratch {
   int nS, r, kind, src, dst, spin;
   int site[kSMax];
   int nold[kSMax], nnew[kSMax];
-  int pair_s[2 * 9];  // S index of each (touched site, offset) pair, -1 if none
+  int pair_s[2 * 13];  // S index of each (touched site, tap) pair, -1 if none (up to 13 taps)
   int slot[kRMax], orb[kRMax], sidx[kRMax], moved[kRMax];
   alignas(16) T feat[kSMax][H];   // new features H'(L) on S (tile loads/stores stop at nS)
   alignas(16) T hl[kSMax][H];     // cached features H(L) on S
@@ -140,14 +140,15 @@ template <typename T, int H>
 __device__ void move_features(const Lattice& lat, const Net<T>& net, int k0, const SampleView<T>& sv,
                               const MlpFrags& mf, MoveScratch<T, H>& ms, T (*z0_new)[H] = nullptr) {
   const int lane = threadIdx.x & 31;
-  const int h = net.h, r0 = (k0 - 1) / 2, kk = k0 * k0;
-  const int npairs = 2 * kk;
-  // pairs (t, d): t = src (pair < kk) or dst; the site reached is t - d
+  const int h = net.h, kk = net.taps0;  // taps of layer 0 (9 for the 3x3 box, 13 for the plus)
+  const int npairs = 2 * kk;            // <= 32: one lane per pair
+  // pairs (t, d): t = src (pair < kk) or dst; the site reached is t - offset(d)
   int s_site = -1;
   if (lane < npairs) {
     const int t = (lane < kk) ? ms.src : ms.dst;
     const int d = lane % kk;
-    const int dx = d % k0 - r0, dy = d / k0 - r0;
+    int dx, dy;
+    stencil_tap(net.stencil, k0, d, dx, dy);
     s_site = site_off(lat, t, -dx, -dy);
   }
   const unsigned act_mask = __ballot_sync(0xffffffffu, s_site >= 0);
@@ -206,7 +207,8 @@ __device__ void move_features(const Lattice& lat, const Net<T>& net, int k0, con
     const int c = lane;
     const bool on_c = c < h;
 #pragma unroll
-    for (int p0 = 0; p0 < 2 * 9; p0 += 9) {
+    for (int p0 = 0; p0 < 27; p0 += 9) {  // the pairs in groups of nine (two groups for the box)
+      if (p0 >= npairs) break;
       T kn[9], ko[9];
 #pragma unroll
       for (int g = 0; g < 9; ++g) {

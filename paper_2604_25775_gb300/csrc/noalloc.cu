@@ -79,7 +79,7 @@ extern "C" scale_status scale_log_psi_noalloc(const scale_system* sys, const sca
   c.stream = (cudaStream_t)cuda_stream;
   c.lat = Lattice{sys->Lx, sys->Ly, sys->pbc_x, sys->pbc_y, c.N, sys->n_up, sys->n_dn, c.Ne, sys->model,
                   sys->t, sys->tp, sys->U, sys->J};
-  c.lowrank_ok = c.k0 <= 3;
+  c.lowrank_ok = c.k0 <= 3 || (c.k0 == 5 && arch->stencil == SCALE_STENCIL_DISK);
   for (int l = 1; l < c.L; ++l) c.lowrank_ok = c.lowrank_ok && arch->ksize[l] == 1;
   c.hpad = c.h <= 16 ? 16 : (c.h <= 32 ? 32 : 64);
   c.use_mma = !c.fp64 && c.lowrank_ok && c.h == c.hpad;

@@ -13,7 +13,8 @@
 //   Pt           T     [B][2][Ne][h]     Pt[s][c] = W_s Binv[c], W_s = proj_w[:, s*Ne:(s+1)*Ne]
 //   logabs       f64   [B]               log|det Phi| in slot order, sign_slot int32 [B]
 // Parameters are kept as FP64 and T copies; the layer-0 conv-of-embedding table
-//   KE [Ns][4][k0*k0][h] = K_0[d]^T E_t[n]   (Ns = N with per-site tables, else 1)
+//   KE [Ns][4][taps0][h] = K_0[d]^T E_t[n]   (Ns = N with per-site tables, else 1; d over the
+//                                             taps of layer 0's stencil)
 // turns the layer-0 receptive-field update into table additions.
 #pragma once
 
@@ -35,6 +36,34 @@ struct Lattice {
   double t, tp, U, J;
 };
 
+// Offset (dx, dy) of tap d of a k x k layer: taps run over the box in row-major order; the
+// disk stencil keeps the offsets within L2 distance (k-1)/2 (k = 5: the 13 sites of SCALE-L).
+__host__ __device__ __forceinline__ void stencil_tap(int stencil, int k, int d, int& dx, int& dy) {
+  const int r = (k - 1) / 2;
+  if (stencil == SCALE_STENCIL_BOX) {
+    dx = d % k - r;
+    dy = d / k - r;
+    return;
+  }
+  int t = 0;
+  for (int q = 0; q < k * k; ++q) {
+    const int x = q % k - r, y = q / k - r;
+    if (x * x + y * y > r * r) continue;
+    if (t == d) {
+      dx = x;
+      dy = y;
+      return;
+    }
+    ++t;
+  }
+  dx = dy = 0;
+}
+
+__host__ __device__ __forceinline__ bool stencil_in(int stencil, int k, int dx, int dy) {
+  const int r = (k - 1) / 2;
+  return stencil == SCALE_STENCIL_BOX || dx * dx + dy * dy <= r * r;
+}
+
 // Site reached from i by (dx, dy), or -1 past an open edge.
 __host__ __device__ __forceinline__ int site_off(const Lattice& lat, int i, int dx, int dy) {
   int x = i % lat.Lx + dx, y = i / lat.Lx + dy;
@@ -53,6 +82,8 @@ __host__ __device__ __forceinline__ int site_off(const Lattice& lat, int i, int 
 template <typename T>
 struct Net {
   int h, L, act, per_site;
+  int stencil;                   // SCALE_STENCIL_* of the k x k layers
+  int taps0;                     // taps of layer 0 under the stencil
   int ksize[kMaxLayers];
   int resid[kMaxLayers];
   const T* embed;                // [Ns][4][h]
@@ -62,7 +93,7 @@ struct Net {
   const T* proj_b;               // [2Ne]
   const T* M0;                   // [2N][Ne]
   const T* M0b;                  // [2N][Ne] M0[o] + proj_b[s(o)] (derived at set_params)
-  const T* KE;                   // [Ns][4][k0*k0][h]
+  const T* KE;                   // [Ns][4][taps0][h]
 };
 
 // FP32 tanh for the tensor-core layers, from the odd Taylor series

@@ -403,6 +403,14 @@ def workload(name: str) -> Problem:
         ks, rs = ace_layout(16, 2)
         return Problem(16, 4, 1, 1, 28, 28, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 18, 144, ks, rs,
                        ACT_SILU, 1, PREC_MIXED, 64, 1e-4, FAMILY_ACE, 16, 256)
+    if name == "scale_plus16x16":  # the bench network with SCALE-L's 13-site plus stencil (cached update)
+        ks, rs = scale_layout(6, ksize_first=5)
+        return Problem(16, 16, 1, 1, 112, 112, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 6, 32, ks, rs,
+                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4, FAMILY_SCALE, 0, 0, 1e-5, STENCIL_DISK)
+    if name == "scale_plus6x6":  # plus stencil, SCALE family, FP64 (parity of the cached update)
+        ks, rs = scale_layout(2, ksize_first=5)
+        return Problem(6, 6, 1, 1, 12, 12, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 2, 8, ks, rs,
+                       ACT_TANH, 1, PREC_FP64, 64, 1e-10, FAMILY_SCALE, 0, 0, 1e-5, STENCIL_DISK)
     if name == "scale_l5x5":  # SCALE-L layout (13-site plus stencil), small widths, FP64
         return Problem(5, 5, 1, 1, 8, 8, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 3, 6, [5, 1, 1], [1, 0, 0],
                        ACT_SILU, 1, PREC_FP64, 64, 1e-10, FAMILY_WIDE, 1, 10, 1e-5, STENCIL_DISK)
@@ -435,7 +443,8 @@ def workload(name: str) -> Problem:
 WORKLOAD_INDEX = {"hubbard4x4": 0, "hubbard8x8": 1, "hubbard16x16": 2, "cylinder16x4": 3,
                   "tj8x8": 4, "tj16x16": 4, "hubbard32x32": 4, "tj32x32": 4,
                   "hubbard_ph8x8": 5, "ace4x4": 6, "ace8x8": 6, "ace16x16": 6, "ace16x4": 6,
-                  "scale_l5x5": 7, "scale_l8x8": 7, "scale_l16x16": 7, "scale_xl32x32": 7}
+                  "scale_l5x5": 7, "scale_l8x8": 7, "scale_l16x16": 7, "scale_xl32x32": 7,
+                  "scale_plus16x16": 2, "scale_plus6x6": 8}
 
 
 def workload_seeds(name: str):

@@ -10,6 +10,8 @@ their own (one GPU, inputs resident on the device, CUDA events on the context's 
         Table tab:model SCALE-L (plus stencil, conv 384, site-wise 4 x 512) local energies on
         the 16x16 torus and SCALE-XL (conv 640, site-wise 4 x 1280) amplitudes on the 32x32
         torus, both by full recompute.
+    python -m paper_2604_25775_gb300.next_bench plus [walkers]
+        Low-rank local energies of the bench network with SCALE-L's plus stencil.
     python -m paper_2604_25775_gb300.next_bench symmetry [walkers]
         The symmetry-projected amplitude (App. "Symmetry Projection") over the 256
         translations of the SCALE 16x16 bench workload.
@@ -131,6 +133,30 @@ def run_wide(walkers: int = 8) -> dict:
     return out
 
 
+def run_plus(walkers: int = 8192) -> dict:
+    """The SCALE chain step's local energies (cached update) on the bench network with
+    SCALE-L's 13-site plus stencil in place of the 3x3 box, 16x16 torus."""
+    import torch
+    pb = I.workload("scale_plus16x16")
+    pseed, cseed = I.workload_seeds("scale_plus16x16")
+    ctx = Bd.make_context(pb, I.random_params(pb, pseed, 0.05), I.plane_wave_M0(pb), walkers)
+    ctx.scale_load(torch.from_numpy(I.random_configs(pb, walkers, cseed)).cuda())
+    e = torch.empty(walkers, dtype=torch.float64, device="cuda")
+    ctx.scale_local_energy(e, Bd.PATH_LOWRANK)
+    a, b = _events()
+    torch.cuda.synchronize()
+    a.record()
+    ctx.scale_local_energy(e, Bd.PATH_LOWRANK)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out = {"workload": "scale_plus16x16: 16x16 torus, U=8, 112+112, 5x5 plus conv + 5 site-wise, h=32",
+           "walkers": walkers, "eloc_ms": ms, "eloc_per_s": walkers / (ms / 1e3),
+           "finite": bool(torch.isfinite(e).all().item())}
+    ctx.close()
+    return out
+
+
 if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "ace"
     n = int(sys.argv[2]) if len(sys.argv) > 2 else None
@@ -138,5 +164,7 @@ if __name__ == "__main__":
         print(json.dumps(run_ace(n or 16)))
     elif what == "wide":
         print(json.dumps(run_wide(n or 8)))
+    elif what == "plus":
+        print(json.dumps(run_plus(n or 8192)))
     else:
         print(json.dumps(run_symmetry(n or 1024)))

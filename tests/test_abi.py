@@ -28,6 +28,7 @@ def test_library_exports_every_declared_symbol():
 
 
 @pytest.mark.parametrize("name", ["hubbard4x4", "hubbard16x16", "cylinder16x4", "tj8x8", "hubbard32x32",
+                                  "scale_plus16x16",
                                   "ace4x4", "ace8x8", "ace16x16", "scale_l5x5", "scale_l16x16",
                                   "scale_xl32x32"])
 def test_param_count_matches_layout(name):
@@ -52,7 +53,6 @@ def test_invalid_descriptors_rejected_on_host():
         I.workload("ace4x4").replace(residual=[1, 1, 0, 0, 0]),  # ACE conv block without residual
         I.workload("ace4x4").replace(ksize=[3, 3, 3, 3, 1]),     # ACE site-wise layer with a stencil
         I.workload("ace4x4").replace(ln_eps=-1.0),
-        I.workload("hubbard4x4").replace(stencil=1),     # the cached update needs the box stencil
         I.workload("scale_l5x5").replace(stencil=2),     # unknown stencil
         I.workload("scale_l5x5").replace(h=2000),        # wide SCALE conv above 1024
     ]
