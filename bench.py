@@ -462,6 +462,8 @@ def main():
             line["ace"] = next_bench.run_ace(args.ace_walkers)
         if args.wide_walkers > 0:  # Table tab:model SCALE-L / SCALE-XL shapes, full recompute
             line["wide"] = next_bench.run_wide(args.wide_walkers)
+        # the cached update with SCALE-L's plus stencil (bench network otherwise)
+        line["plus_stencil"] = next_bench.run_plus(B)
         # serving: open-loop Poisson sweep-step requests over mixed chains, continuous batching
         if args.serve_seconds > 0:
             from paper_2604_25775_gb300 import serve_bench
