@@ -80,6 +80,10 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
                                                  int32_t* __restrict__ sign_out, int32_t* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
   using KeyT = typename AbsKey<TW>::T;
+  // small determinant-only CTAs (several matrices per SM): integer-key pivot search, log|pivot|
+  // summed by all threads at the end, one column per lane; the 1024-thread kernels keep FP
+  // compares, the running log and two columns per lane (their registers stay unspilled)
+  constexpr bool kLean = !kInverse && TH <= 512;
   double* pabs = reinterpret_cast<double*>(smem_raw);  // [n] |pivot| of column k (log taken at the end)
   TW* panel = reinterpret_cast<TW*>(pabs + n);         // [n][W]
   TW* prow = panel + (size_t)n * W;              // [W][n]
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
       // pivot search over unpivoted rows (largest |value|, ties to the lowest row); the
       // determinant-only kernels compare integer keys, the inverse kernels FP values
       int bi = n;
-      if constexpr (!kInverse) {
+      if constexpr (kLean) {
         KeyT bk = 0;
         for (int i = tid; i < n; i += TH) {
           if (used[i]) continue;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
       __syncthreads();
       if (tid == 0) {
         int i = red_i[0];
-        if constexpr (!kInverse) {
+        if constexpr (kLean) {
           KeyT kk = red_k[0];
           for (int q = 1; q < TH / 32; ++q) key_merge(kk, i, red_k[q], red_i[q]);
         } else {
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
       if (tid == 0) {
         piv[k] = p;
         used[p] = 1;
-        if constexpr (kInverse) logdet += log(fabs((double)pv));
+        if constexpr (!kLean) logdet += log(fabs((double)pv));
         else pabs[k] = fabs((double)pv);
         if (pv < TW(0)) sgn = -sgn;
       }
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
 #pragma unroll
       for (int j = 0; j < W; ++j) u[j] = (j < w) ? panel[i * W + j] - ((piv[K0 + j] == i) ? TW(1) : TW(0)) : TW(0);
       TW* Ai = A + (size_t)i * n;
-      if constexpr (!kInverse) {
+      if constexpr (kLean) {
         // determinant only: every column from c_lo on lies right of the panel; one column
         // per lane (several matrices per SM supply the parallelism), so a strip wastes at most
         // 31 lanes instead of 63
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
   }
 
   // determinant only: log|det| = sum of log|pivot|, one log per thread
-  if constexpr (!kInverse) {
+  if constexpr (kLean) {
     double part = 0.0;
     if (!s_singular)
       for (int k = tid; k < n; k += TH) part += log(pabs[k]);
@@ -580,6 +584,9 @@ cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32
     return run_gj<double, float, true, 16>(c->stream, A, n, B, list, (float*)Binv, logabs, sign, status);
   }
   if (n > 448) return run_gj<double, double, false, 8, 512>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
+  // several matrices per SM: small CTAs overlap one's pivot steps with the others' updates;
+  // fewer matrices than a few per SM: one wide CTA per matrix
+  if (B < 4 * 152) return run_gj<double, double, false, 16>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
   return run_gj<double, double, false, 8, 256>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
 }
 
@@ -587,6 +594,7 @@ cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32
 cudaError_t launch_det_f32(scale_ctx* c, float* mats, int n, int B, double* logabs, int32_t* sign) {
   if (B <= 0) return cudaSuccess;
   if (n > 448) return run_gj<float, float, false, 8, 512>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
+  if (B < 4 * 152) return run_gj<float, float, false, 16>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
   return run_gj<float, float, false, 16, 256>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
 }
 
