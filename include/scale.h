@@ -144,7 +144,9 @@ typedef struct {
                              layers after them are site-wise (ksize 1, residual 0) */
   int32_t h_mlp;          /* ACE: width of the site-wise layers, 1..512 (wide SCALE 1..2048; 0 = h) */
   double ln_eps;          /* ACE: epsilon of the layer normalisation (>= 0) */
-  int32_t stencil;        /* SCALE_STENCIL_* (the SCALE family needs the box) */
+  int32_t stencil;        /* SCALE_STENCIL_*; the SCALE family's cached update takes layer 0 as a
+                             1x1 or 3x3 box or the 5x5 plus (disk), other shapes run by full
+                             recompute; scale_grad_logpsi needs the box */
 } scale_arch;
 
 typedef struct {
