@@ -370,11 +370,12 @@ struct TcShape {
   static constexpr uint32_t TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
 };
 
-// Weight tiles of a conv block in the shared-memory image the MMA reads:
-// [tap d][chunk kc][hi, lo][N rows (output channel) x 8 (input channel)] core-matrix layout.
-__global__ void k_ace_build_bimg(const float* __restrict__ K, int N, float* __restrict__ out) {
+// Weight tiles of a conv layer in the shared-memory image the MMA reads:
+// [tap d][chunk kc][hi, lo][N rows (output channel) x 8 (input channel)] core-matrix layout;
+// the rows [c0, c0 + n) of a tile are the contiguous bytes [32 c0, 32 (c0 + n)).
+__global__ void k_ace_build_bimg(const float* __restrict__ K, int N, int taps, float* __restrict__ out) {
   const int KC = N / kTcKC;
-  const size_t total = (size_t)9 * KC * 2 * N * kTcKC;
+  const size_t total = (size_t)taps * KC * 2 * N * kTcKC;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(q % kTcKC);
     size_t r = q / kTcKC;
@@ -409,20 +410,23 @@ __global__ void k_ace_embed_split(int N, int h, int per_site, const float* __res
   }
 }
 
-// One conv block (3x3, N -> N channels, Eq. ACE) on tcgen05; out_lo == nullptr writes plain
-// FP32 rows to out_hi (the input of the site-wise layers). err: set when a wait ran out.
-// 256 threads: thread t serves row t % 128 -- copies of its hi (t < 128) or lo half, and
-// in the epilogue output columns [0, N/2) (warps 0-3) or [N/2, N) (warps 4-7); a warp reads
-// the TMEM lanes of its quarter (warp % 4).
-template <int N>
+// One conv layer (ks x ks stencil, C -> C channels) on tcgen05: ACE blocks with the layer
+// normalisation in the epilogue (LN, one column tile of N = C), or the wide SCALE conv (no
+// normalisation, column tiles of N: blockIdx.y selects columns [N y, N y + N)). out_lo ==
+// nullptr writes plain FP32 rows to out_hi (the input of the site-wise layers). err: set when
+// a wait ran out. 256 threads: thread t serves row t % 128 -- copies of its hi (t < 128) or
+// lo half, and in the epilogue the tile's columns [0, N/2) (warps 0-3) or [N/2, N) (warps
+// 4-7); a warp reads the TMEM lanes of its quarter (warp % 4).
+template <int N, bool LN>
 __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
     Lattice lat, const float* __restrict__ bimg, const float* __restrict__ bias, const float* __restrict__ gam,
-    const float* __restrict__ bet, int act, float eps, const float* __restrict__ in_hi,
-    const float* __restrict__ in_lo, float* __restrict__ out_hi, float* __restrict__ out_lo, long long rows,
-    int* __restrict__ err) {
+    const float* __restrict__ bet, int act, float eps, int C, int ks, int stencil, int taps,
+    const float* __restrict__ in_hi, const float* __restrict__ in_lo, float* __restrict__ out_hi,
+    float* __restrict__ out_lo, long long rows, int* __restrict__ err) {
   using S = TcShape<N>;
-  constexpr int KC = N / kTcKC;
-  constexpr int STEPS = 9 * KC;
+  const int KC = C / kTcKC;
+  const int STEPS = taps * KC;
+  const int cb = blockIdx.y * N;  // first output column of this CTA
   constexpr int H2 = N / 2;  // epilogue columns per thread
   constexpr uint32_t IDESC = tc::idesc_tf32<kTcRows, N>();
   extern __shared__ unsigned char smem_raw[];
@@ -462,8 +466,10 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
   size_t isrc = 0;
   uint32_t inb = 0;
   auto tap_row = [&](int d) {
-    const int j = valid ? site_off(lat, site, d % 3 - 1, d / 3 - 1) : -1;
-    isrc = j >= 0 ? ((size_t)cfg * Ns + j) * N : 0;
+    int dx, dy;
+    stencil_tap(stencil, ks, d, dx, dy);
+    const int j = valid ? site_off(lat, site, dx, dy) : -1;
+    isrc = j >= 0 ? ((size_t)cfg * Ns + j) * C : 0;
     inb = j >= 0 ? 16u : 0u;  // zero fill past an open edge or the last row
   };
   tap_row(0);
@@ -476,15 +482,15 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
       tc::cp_async16_zfill(st + a_off0, in_part + src, inb);
       tc::cp_async16_zfill(st + a_off1, in_part + src + 4, inb);
       if (tid == 0) {
-        const float* w = bimg + ((size_t)id * KC + ikc) * 2 * N * kTcKC;
+        const float* w = bimg + ((size_t)id * KC + ikc) * 2 * C * kTcKC + (size_t)cb * kTcKC;
         tc::mbar_arrive_expect_tx(&full[b], 2 * S::B_BYTES);
         tc::bulk_g2s(st + 2 * S::A_BYTES, w, S::B_BYTES, &full[b]);
-        tc::bulk_g2s(st + 2 * S::A_BYTES + S::B_BYTES, w + N * kTcKC, S::B_BYTES, &full[b]);
+        tc::bulk_g2s(st + 2 * S::A_BYTES + S::B_BYTES, w + C * kTcKC, S::B_BYTES, &full[b]);
       }
       ++is;
       if (++ikc == KC) {
         ikc = 0;
-        if (++id < 9) tap_row(id);
+        if (++id < taps) tap_row(id);
       }
     }
     tc::cp_async_commit();
@@ -527,12 +533,12 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
       }
     }
   }
-  // this thread's half of the residual row (independent of the MMAs: loaded under them)
+  // this thread's half of the tile's residual row (independent of the MMAs: loaded under them)
   const int c0 = part * H2;
   float u[H2];
   {
-    const float* xh = in_hi + (size_t)(valid ? R : 0) * N + c0;
-    const float* xl = in_lo + (size_t)(valid ? R : 0) * N + c0;
+    const float* xh = in_hi + (size_t)(valid ? R : 0) * C + cb + c0;
+    const float* xl = in_lo + (size_t)(valid ? R : 0) * C + cb + c0;
 #pragma unroll
     for (int c = 0; c < H2; c += 4) {
       const float4 h4 = __ldg(reinterpret_cast<const float4*>(xh + c));
@@ -558,32 +564,39 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
       float z[8];
       tc::tmem_ld8(trow + cc * 8, z);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) u[cc * 8 + q] += act_tc(act, z[q] + __ldg(bias + c0 + cc * 8 + q));
+      for (int q = 0; q < 8; ++q) u[cc * 8 + q] += act_tc(act, z[q] + __ldg(bias + cb + c0 + cc * 8 + q));
     }
-    float s1 = 0.f;
+    if constexpr (LN) {
+      float s1 = 0.f;
 #pragma unroll
-    for (int c = 0; c < H2; ++c) s1 += u[c];
-    s_sum[part][row] = s1;
+      for (int c = 0; c < H2; ++c) s1 += u[c];
+      s_sum[part][row] = s1;
+    }
   }
-  __syncthreads();
-  float mean = 0.f;
-  if (run) {
-    mean = (s_sum[0][row] + s_sum[1][row]) * (1.f / N);
-    float s2 = 0.f;
+  float mean = 0.f, inv = 1.f;
+  if constexpr (LN) {
+    __syncthreads();
+    if (run) {
+      mean = (s_sum[0][row] + s_sum[1][row]) * (1.f / N);
+      float s2 = 0.f;
 #pragma unroll
-    for (int c = 0; c < H2; ++c) s2 += (u[c] - mean) * (u[c] - mean);
-    s_sq[part][row] = s2;
+      for (int c = 0; c < H2; ++c) s2 += (u[c] - mean) * (u[c] - mean);
+      s_sq[part][row] = s2;
+    }
+    __syncthreads();
+    if (run) inv = 1.f / sqrtf((s_sq[0][row] + s_sq[1][row]) * (1.f / N) + eps);
   }
-  __syncthreads();
   if (run) {
-    const float inv = 1.f / sqrtf((s_sq[0][row] + s_sq[1][row]) * (1.f / N) + eps);
 #pragma unroll
     for (int c = 0; c < H2; c += 4) {
       float y[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) y[e] = (u[c + e] - mean) * inv * __ldg(gam + c0 + c + e) + __ldg(bet + c0 + c + e);
+      for (int e = 0; e < 4; ++e) {
+        if constexpr (LN) y[e] = (u[c + e] - mean) * inv * __ldg(gam + c0 + c + e) + __ldg(bet + c0 + c + e);
+        else y[e] = u[c + e];
+      }
       if (valid) {
-        const size_t o = (size_t)R * N + c0 + c;
+        const size_t o = (size_t)R * C + cb + c0 + c;
         if (out_lo) {
           uint32_t hi[4], lo[4];
 #pragma unroll
@@ -605,20 +618,47 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
   if (warp == 0) tc::tmem_dealloc(tmem, S::TCOLS);
 }
 
-template <int N>
+template <int N, bool LN>
 cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, const float* bias, const float* g,
-                        const float* be, int act, float eps, const float* in_hi, const float* in_lo, float* out_hi,
-                        float* out_lo, long long rows, int* err) {
+                        const float* be, int act, float eps, int C, int ks, int stencil, const float* in_hi,
+                        const float* in_lo, float* out_hi, float* out_lo, long long rows, int* err) {
   using S = TcShape<N>;
-  cudaError_t e = cudaFuncSetAttribute(k_ace_conv_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_ace_conv_tc<N, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e != cudaSuccess) return e;
-  const long long blocks = (rows + kTcRows - 1) / kTcRows;
-  k_ace_conv_tc<N><<<(unsigned)blocks, kTcThreads, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, in_hi, in_lo,
-                                                                 out_hi, out_lo, rows, err);
+  const dim3 grid((unsigned)((rows + kTcRows - 1) / kTcRows), (unsigned)(C / N));
+  k_ace_conv_tc<N, LN><<<grid, kTcThreads, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, C, ks, stencil,
+                                                          stencil_taps(stencil, ks), in_hi, in_lo, out_hi, out_lo,
+                                                          rows, err);
   return cudaGetLastError();
 }
 
+// Conv layers on tcgen05: ACE blocks of width 48, 144 or 192 (3x3 box, one column tile,
+// normalisation in the epilogue); the wide SCALE conv of width 384 (two tiles of 192) or 640
+// (four tiles of 160), 3x3 box or the 5x5 plus.
 bool tc_width(int h) { return h == 48 || h == 144 || h == 192; }
+bool tc_wide_width(int h) { return h == 384 || h == 640; }
+
+cudaError_t launch_conv_tc(const scale_ctx* c, bool ln, int h, int ks, const float* bimg, const float* bias,
+                           const float* g, const float* be, int act, float eps, const float* in_hi,
+                           const float* in_lo, float* out_hi, float* out_lo, long long rows) {
+  const int st = c->arch.stencil;
+  if (ln) {
+    if (h == 48)
+      return run_conv_tc<48, true>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
+                                   out_lo, rows, c->ace_err);
+    if (h == 144)
+      return run_conv_tc<144, true>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
+                                    out_lo, rows, c->ace_err);
+    return run_conv_tc<192, true>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
+                                  out_lo, rows, c->ace_err);
+  }
+  if (h == 384)
+    return run_conv_tc<192, false>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
+                                   out_lo, rows, c->ace_err);
+  return run_conv_tc<160, false>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
+                                 out_lo, rows, c->ace_err);
+}
 
 // Slater matrix rows of the occupied orbitals in ascending order (FP64 output):
 //   Phi[a][k] = M0[o_a][k] + proj_b[s Ne + k] + sum_c H(L)_i[c] proj_w[c][s Ne + k].
@@ -804,16 +844,8 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
       if (split) {  // conv block on tcgen05; the last one writes plain FP32 rows
         const float* bimg = (const float*)((const char*)c->ace_frag + frag_off);
         float* olo = l + 1 < net.n_conv ? b + total : nullptr;
-        cudaError_t e;
-        if (c->h == 48)
-          e = run_conv_tc<48>(c->stream, c->lat, bimg, net.bias[l], net.ln_g[l], net.ln_b[l], net.act,
-                              (float)net.eps, a, a + total, b, olo, rows, c->ace_err);
-        else if (c->h == 144)
-          e = run_conv_tc<144>(c->stream, c->lat, bimg, net.bias[l], net.ln_g[l], net.ln_b[l], net.act,
-                               (float)net.eps, a, a + total, b, olo, rows, c->ace_err);
-        else
-          e = run_conv_tc<192>(c->stream, c->lat, bimg, net.bias[l], net.ln_g[l], net.ln_b[l], net.act,
-                               (float)net.eps, a, a + total, b, olo, rows, c->ace_err);
+        const cudaError_t e = launch_conv_tc(c, net.ln_g[l] != nullptr, c->h, net.ks[l], bimg, net.bias[l], net.ln_g[l],
+                                             net.ln_b[l], net.act, (float)net.eps, a, a + total, b, olo, rows);
         if (e != cudaSuccess) return e;
         split = olo != nullptr;
         done = true;
@@ -848,10 +880,19 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
 }  // namespace
 
 bool ace_tc_shapes(const scale_arch& a) {
-  if (a.family != SCALE_FAMILY_ACE || a.stencil != SCALE_STENCIL_BOX || !tc_width(a.h)) return false;
-  for (int l = 0; l < a.n_conv; ++l)
-    if (a.ksize[l] != 3) return false;
-  return ace_mma_shapes(a);
+  if (a.family == SCALE_FAMILY_ACE) {
+    if (a.stencil != SCALE_STENCIL_BOX || !tc_width(a.h)) return false;
+    for (int l = 0; l < a.n_conv; ++l)
+      if (a.ksize[l] != 3) return false;
+    return ace_mma_shapes(a);
+  }
+  if (a.family == SCALE_FAMILY_WIDE) {  // one conv: 3x3 box or 5x5 plus, then site-wise layers
+    if (a.n_conv != 1 || !tc_wide_width(a.h)) return false;
+    const bool box3 = a.ksize[0] == 3 && a.stencil == SCALE_STENCIL_BOX;
+    const bool plus5 = a.ksize[0] == 5 && a.stencil == SCALE_STENCIL_DISK;
+    return (box3 || plus5) && ace_mma_shapes(a);
+  }
+  return false;
 }
 
 bool ace_mma_shapes(const scale_arch& a) {
@@ -876,7 +917,8 @@ cudaError_t launch_ace_build(scale_ctx* c) {
     if (c->ace_tc && l < net.n_conv) {  // the tcgen05 weight-tile image
       const size_t n = (size_t)taps * 2 * net.cin[l] * net.cout[l];
       const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
-      k_ace_build_bimg<<<blocks, 256, 0, c->stream>>>(net.kernel[l], net.cout[l], (float*)((char*)c->ace_frag + off));
+      k_ace_build_bimg<<<blocks, 256, 0, c->stream>>>(net.kernel[l], net.cout[l], taps,
+                                                       (float*)((char*)c->ace_frag + off));
       off += frag_layer_bytes(c->arch, l);
       continue;
     }
