@@ -480,7 +480,9 @@ def main():
         dt = time.perf_counter() - t0c
         line["cpu_baseline"] = {"value": n_cpu / dt, "unit": "E_loc/s", "cores": O.num_threads(), "kind": "oracle",
                                 "sample": f"{n_cpu} walkers of the same workload, FP64 full recompute"}
-    line["gpu_launches"] = K * (2 + 6 + 6)  # per step: k_eloc, k_commit, mark, 6 forward/refresh kernels
+    # per step, as an ncu launch list of the chain step shows: k_eloc, k_commit, k_mark_refresh,
+    # and the refresh of the due samples: k_slots, k_layer, k_mlp_fwd, k_phi, k_gj, k_project
+    line["gpu_launches"] = K * 9
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
