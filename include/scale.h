@@ -61,7 +61,7 @@ typedef enum {
   SCALE_EBUDGET = 3,      /* request does not fit the HBM budget */
   SCALE_ECUDA = 4,        /* a CUDA call failed (text in scale_last_error) */
   SCALE_ETIMEOUT = 5,     /* a bounded wait ran out */
-  SCALE_EUNSUPPORTED = 6  /* valid but not supported by this build (see text) */
+  SCALE_EUNSUPPORTED = 6  /* valid but not supported by this library (see text) */
 } scale_status;
 
 /* SCALE_MODEL_HUBBARD_PH: the Hubbard model after the particle-hole transformation of the
