@@ -15,23 +15,27 @@
 // by neighbour offset.
 //
 // Implementations of a layer:
-//   k_ace_conv_tc (mixed mode, conv blocks of width 48, 144 or 192): the 5th-generation
-//               tensor cores. One CTA of 128 threads owns 128 rows (TMEM lanes) and all h
-//               output channels (TMEM columns). The K loop runs over (offset d, 8-channel
-//               chunk) stages in a 6-slot shared-memory ring with 4 stages of copies in
-//               flight: each thread gathers its own row's 8 input channels from the
-//               neighbour site with 16-byte cp.async (zero
-//               fill past an open edge), the pre-split weight tile arrives by one bulk copy
-//               per half (hi, lo) on an mbarrier, and one thread issues the three TF32
-//               products x_hi W_hi + x_lo W_hi + x_hi W_lo per K=8 step (tcgen05.mma,
-//               FP32 accumulation in TMEM) and commits them to the stage's mbarrier. The
-//               activations between conv blocks are stored already split (hi, lo).
-//               Epilogue per thread = per row, held in registers: the residual row (loaded
-//               while the last MMAs finish), tcgen05.ld of the accumulator row in 16-column
-//               chunks, bias, SiLU, the layer normalisation (mean, then the centred variance),
-//               the split for the next block.
-//   k_ace_mma   (mixed mode, site-wise layers): tensor cores, every product as three TF32
-//               products of a hi/lo split (x_hi W_hi + x_lo W_hi + x_hi W_lo, FP32
+//   k_ace_conv_tc (mixed mode: the ACE conv blocks of width 48, 144 or 192, the wide SCALE
+//               conv of width 384 or 640, and the site-wise layers that follow them while
+//               their output widths are multiples of 128): the 5th-generation tensor cores.
+//               One CTA of 256 threads (two per row) owns 128 rows (TMEM lanes) and a tile
+//               of N output channels (TMEM columns; the whole width for a normalised block,
+//               else 128 to 192). The K loop runs over (offset d, 8-channel chunk) stages
+//               in a 6-slot shared-memory ring with 4 stages of copies in flight: each
+//               thread gathers its row's 8 input channels, hi or lo part, from the
+//               neighbour site with 16-byte cp.async (zero fill past an open edge),
+//               the pre-split weight tile arrives by one bulk copy per half (hi, lo) on an
+//               mbarrier, and one thread issues the three TF32 products
+//               x_hi W_hi + x_lo W_hi + x_hi W_lo per K=8 step (tcgen05.mma, FP32
+//               accumulation in TMEM) and commits them to the stage's mbarrier. Between two
+//               tensor-core layers the activations are stored already split (hi, lo).
+//               Epilogue per thread = half a row, held in registers: the residual (loaded
+//               while the last MMAs finish), tcgen05.ld of the accumulator in 8-column
+//               chunks, bias, activation, the layer normalisation (mean, then the centred
+//               variance, the two halves combined through shared memory), the split for
+//               the next layer.
+//   k_ace_mma   (mixed mode, the other site-wise layers): mma.sync tensor cores, every
+//               product as three TF32 products of a hi/lo split (x_hi W_hi + x_lo W_hi + x_hi W_lo, FP32
 //               accumulation, about 2^-21 relative per layer). A warp owns 16 rows and
 //               WC warps share a row group's output columns; the A operand is gathered from
 //               the neighbour sites' rows (L1/L2), the weights come as pre-split fragments.
@@ -373,8 +377,8 @@ struct TcShape {
 // Weight tiles of a conv layer in the shared-memory image the MMA reads:
 // [tap d][chunk kc][hi, lo][N rows (output channel) x 8 (input channel)] core-matrix layout;
 // the rows [c0, c0 + n) of a tile are the contiguous bytes [32 c0, 32 (c0 + n)).
-__global__ void k_ace_build_bimg(const float* __restrict__ K, int N, int taps, float* __restrict__ out) {
-  const int KC = N / kTcKC;
+__global__ void k_ace_build_bimg(const float* __restrict__ K, int CI, int N, int taps, float* __restrict__ out) {
+  const int KC = CI / kTcKC;
   const size_t total = (size_t)taps * KC * 2 * N * kTcKC;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(q % kTcKC);
@@ -385,7 +389,7 @@ __global__ void k_ace_build_bimg(const float* __restrict__ K, int N, int taps, f
     r /= 2;
     const int kc = (int)(r % KC);
     const int d = (int)(r / KC);
-    const float w = K[((size_t)d * N + kc * kTcKC + k) * N + n];
+    const float w = K[((size_t)d * CI + kc * kTcKC + k) * N + n];
     uint32_t hi, lo;
     split_tf32(w, hi, lo);
     const size_t tile = (((size_t)d * KC + kc) * 2 + part) * N * kTcKC;
@@ -420,9 +424,12 @@ __global__ void k_ace_embed_split(int N, int h, int per_site, const float* __res
 template <int N, bool LN>
 __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
     Lattice lat, const float* __restrict__ bimg, const float* __restrict__ bias, const float* __restrict__ gam,
-    const float* __restrict__ bet, int act, float eps, int C, int ks, int stencil, int taps,
+    const float* __restrict__ bet, int act, float eps, int C, int CO, int res, int ks, int stencil, int taps,
     const float* __restrict__ in_hi, const float* __restrict__ in_lo, float* __restrict__ out_hi,
     float* __restrict__ out_lo, long long rows, int* __restrict__ err) {
+  // C input channels (K = taps x C), CO output channels (this CTA: [cb, cb + N)); res: add the
+  // input row (C == CO). A normalised block is one tile wide: C == CO == N.
+  if constexpr (LN) C = CO = N;
   using S = TcShape<N>;
   const int KC = C / kTcKC;
   const int STEPS = taps * KC;
@@ -482,10 +489,10 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
       tc::cp_async16_zfill(st + a_off0, in_part + src, inb);
       tc::cp_async16_zfill(st + a_off1, in_part + src + 4, inb);
       if (tid == 0) {
-        const float* w = bimg + ((size_t)id * KC + ikc) * 2 * C * kTcKC + (size_t)cb * kTcKC;
+        const float* w = bimg + ((size_t)id * KC + ikc) * 2 * CO * kTcKC + (size_t)cb * kTcKC;
         tc::mbar_arrive_expect_tx(&full[b], 2 * S::B_BYTES);
         tc::bulk_g2s(st + 2 * S::A_BYTES, w, S::B_BYTES, &full[b]);
-        tc::bulk_g2s(st + 2 * S::A_BYTES + S::B_BYTES, w + C * kTcKC, S::B_BYTES, &full[b]);
+        tc::bulk_g2s(st + 2 * S::A_BYTES + S::B_BYTES, w + CO * kTcKC, S::B_BYTES, &full[b]);
       }
       ++is;
       if (++ikc == KC) {
@@ -536,7 +543,7 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
   // this thread's half of the tile's residual row (independent of the MMAs: loaded under them)
   const int c0 = part * H2;
   float u[H2];
-  {
+  if (LN || res) {  // the normalised conv blocks are residual
     const float* xh = in_hi + (size_t)(valid ? R : 0) * C + cb + c0;
     const float* xl = in_lo + (size_t)(valid ? R : 0) * C + cb + c0;
 #pragma unroll
@@ -548,6 +555,9 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
       u[c + 2] = h4.z + l4.z;
       u[c + 3] = h4.w + l4.w;
     }
+  } else {
+#pragma unroll
+    for (int c = 0; c < H2; ++c) u[c] = 0.f;
   }
   if (!s_abort && tid == 0) {
     const int sl = STEPS - 1;
@@ -596,7 +606,7 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
         else y[e] = u[c + e];
       }
       if (valid) {
-        const size_t o = (size_t)R * C + cb + c0 + c;
+        const size_t o = (size_t)R * CO + cb + c0 + c;
         if (out_lo) {
           uint32_t hi[4], lo[4];
 #pragma unroll
@@ -620,14 +630,15 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
 
 template <int N, bool LN>
 cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, const float* bias, const float* g,
-                        const float* be, int act, float eps, int C, int ks, int stencil, const float* in_hi,
-                        const float* in_lo, float* out_hi, float* out_lo, long long rows, int* err) {
+                        const float* be, int act, float eps, int C, int CO, int res, int ks, int stencil,
+                        const float* in_hi, const float* in_lo, float* out_hi, float* out_lo, long long rows,
+                        int* err) {
   using S = TcShape<N>;
   cudaError_t e =
       cudaFuncSetAttribute(k_ace_conv_tc<N, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)((rows + kTcRows - 1) / kTcRows), (unsigned)(C / N));
-  k_ace_conv_tc<N, LN><<<grid, kTcThreads, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, C, ks, stencil,
+  const dim3 grid((unsigned)((rows + kTcRows - 1) / kTcRows), (unsigned)(CO / N));
+  k_ace_conv_tc<N, LN><<<grid, kTcThreads, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, C, CO, res, ks, stencil,
                                                           stencil_taps(stencil, ks), in_hi, in_lo, out_hi, out_lo,
                                                           rows, err);
   return cudaGetLastError();
@@ -638,26 +649,26 @@ cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, 
 // (four tiles of 160), 3x3 box or the 5x5 plus.
 bool tc_width(int h) { return h == 48 || h == 144 || h == 192; }
 bool tc_wide_width(int h) { return h == 384 || h == 640; }
+// Site-wise layers on tcgen05 (1x1, no residual): input width a multiple of 8, output width a
+// multiple of 128 (tiles of 128 columns, two CTAs per SM).
+bool tc_sitewise(int cin, int cout) { return cin % kTcKC == 0 && cout % 128 == 0; }
 
-cudaError_t launch_conv_tc(const scale_ctx* c, bool ln, int h, int ks, const float* bimg, const float* bias,
-                           const float* g, const float* be, int act, float eps, const float* in_hi,
-                           const float* in_lo, float* out_hi, float* out_lo, long long rows) {
+cudaError_t launch_conv_tc(const scale_ctx* c, bool ln, int cin, int cout, int res, int ks, const float* bimg,
+                           const float* bias, const float* g, const float* be, int act, float eps,
+                           const float* in_hi, const float* in_lo, float* out_hi, float* out_lo, long long rows) {
   const int st = c->arch.stencil;
+#define SCALE_TC(NT, LNV) \
+  run_conv_tc<NT, LNV>(c->stream, c->lat, bimg, bias, g, be, act, eps, cin, cout, res, ks, st, in_hi, in_lo, \
+                       out_hi, out_lo, rows, c->ace_err)
   if (ln) {
-    if (h == 48)
-      return run_conv_tc<48, true>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
-                                   out_lo, rows, c->ace_err);
-    if (h == 144)
-      return run_conv_tc<144, true>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
-                                    out_lo, rows, c->ace_err);
-    return run_conv_tc<192, true>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
-                                  out_lo, rows, c->ace_err);
+    if (cout == 48) return SCALE_TC(48, true);
+    if (cout == 144) return SCALE_TC(144, true);
+    return SCALE_TC(192, true);
   }
-  if (h == 384)
-    return run_conv_tc<192, false>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
-                                   out_lo, rows, c->ace_err);
-  return run_conv_tc<160, false>(c->stream, c->lat, bimg, bias, g, be, act, eps, h, ks, st, in_hi, in_lo, out_hi,
-                                 out_lo, rows, c->ace_err);
+  if (ks > 1 && cout == 384) return SCALE_TC(192, false);
+  if (ks > 1 && cout == 640) return SCALE_TC(160, false);
+  return SCALE_TC(128, false);
+#undef SCALE_TC
 }
 
 // Slater matrix rows of the occupied orbitals in ascending order (FP64 output):
@@ -818,6 +829,16 @@ bool launch_mma_layer(cudaStream_t st, const Lattice& lat, const MmaPlan& p, boo
   return true;
 }
 
+// Layers that run on tcgen05 when the tensor-core path is on: the conv layers (checked at
+// creation), then the site-wise layers up to the first one of an unsupported shape. Between
+// two of them the activations stay split (hi, lo); the rest run on the mma.sync kernels.
+bool tc_layer(const scale_ctx* c, int l) {
+  if (!c->ace_tc) return false;
+  for (int j = c->arch.n_conv; j <= l; ++j)
+    if (!tc_sitewise(ace_width_in(c->arch, j), ace_width_out(c->arch, j)) || c->arch.residual[j]) return false;
+  return true;
+}
+
 template <typename T>
 cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64) {
   const AceNet<T> net = make_ace_net<T>(c);
@@ -841,11 +862,13 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
     const bool conv = l < net.n_conv;
     bool done = false;
     if constexpr (sizeof(T) == 4) {
-      if (split) {  // conv block on tcgen05; the last one writes plain FP32 rows
+      if (split && tc_layer(c, l)) {  // on tcgen05; split output when the next layer is too
         const float* bimg = (const float*)((const char*)c->ace_frag + frag_off);
-        float* olo = l + 1 < net.n_conv ? b + total : nullptr;
-        const cudaError_t e = launch_conv_tc(c, net.ln_g[l] != nullptr, c->h, net.ks[l], bimg, net.bias[l], net.ln_g[l],
-                                             net.ln_b[l], net.act, (float)net.eps, a, a + total, b, olo, rows);
+        const long long tin = rows * net.cin[l], tout = rows * net.cout[l];
+        float* olo = (l + 1 < c->L && tc_layer(c, l + 1)) ? b + tout : nullptr;
+        const cudaError_t e =
+            launch_conv_tc(c, net.ln_g[l] != nullptr, net.cin[l], net.cout[l], c->arch.residual[l], net.ks[l], bimg,
+                           net.bias[l], net.ln_g[l], net.ln_b[l], net.act, (float)net.eps, a, a + tin, b, olo, rows);
         if (e != cudaSuccess) return e;
         split = olo != nullptr;
         done = true;
@@ -914,10 +937,10 @@ cudaError_t launch_ace_build(scale_ctx* c) {
   size_t off = 0;
   for (int l = 0; l < c->L; ++l) {
     const int taps = stencil_taps(net.stencil, net.ks[l]);
-    if (c->ace_tc && l < net.n_conv) {  // the tcgen05 weight-tile image
+    if (tc_layer(c, l)) {  // the tcgen05 weight-tile image
       const size_t n = (size_t)taps * 2 * net.cin[l] * net.cout[l];
       const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
-      k_ace_build_bimg<<<blocks, 256, 0, c->stream>>>(net.kernel[l], net.cout[l], taps,
+      k_ace_build_bimg<<<blocks, 256, 0, c->stream>>>(net.kernel[l], net.cin[l], net.cout[l], taps,
                                                        (float*)((char*)c->ace_frag + off));
       off += frag_layer_bytes(c->arch, l);
       continue;

@@ -74,6 +74,27 @@ def test_ace_mixed_8x8(name):
     _check(f"{name} E_loc / term scale", e / scale, e_o / scale, cond, 1e-4, 1e3)
 
 
+@pytest.mark.parametrize("B", [3, 16])
+def test_ace_mixed_sitewise_tensor_core_chain(B):
+    """Site-wise layers of width 128 after the conv blocks: both run on the same tensor-core
+    kernel as the blocks (48 -> 128, then 128 -> 128, one 128-column tile each, no residual),
+    the activations passed between them as (hi, lo) halves; B = 3 ends the rows inside a
+    128-row tile."""
+    pb = I.workload("ace8x8").replace(h_mlp=128)
+    ctx, ora, occ, st = setup(pb, B, 1257, 5707, scale=0.05)
+    cond = conditioning(ora, occ)
+    la, sg = ctx.log_psi()
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    la_o, sg_o = ora.log_psi(occ)
+    good = cond < 1e3
+    assert (sg[good] == sg_o[good]).all()
+    _check(f"ace8x8 site-wise 128 B={B} log|psi|", la, la_o, cond, 1e-4, 1e3, min_good=0)
+    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora.local_energy(occ)
+    scale = np.maximum(eloc_term_scale(ora, occ), 1.0)
+    _check(f"ace8x8 site-wise 128 B={B} E_loc / term scale", e / scale, e_o / scale, cond, 1e-4, 1e3, min_good=0)
+
+
 def test_ace_mixed_generic_width():
     """A width without a tensor-core shape (h = 40) runs the FP32 CUDA-core layers."""
     pb = I.workload("ace8x8").replace(h=40, h_mlp=40, n_conv=4, n_layers=5, ksize=[3] * 4 + [1],
