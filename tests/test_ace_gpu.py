@@ -107,18 +107,23 @@ def test_ace_mixed_generic_width():
 
 
 def test_ace_mixed_16x16_table_shape():
-    """Table tab:model ACE (16 blocks at h = 144, two site-wise layers at 256) on the 16x16
-    torus: log|psi| of 8 samples and the local energy of 1 (the oracle recomputes every
-    psi(n') in full, about a second each)."""
+    """Table tab:model ACE (16 blocks at h = 144, two site-wise layers at 256, all on the
+    tensor cores) on the 16x16 torus: log|psi| of 8 samples; and the local energies of 2
+    walkers on an 8x8 torus (14 + 14) with the same network shape (the oracle recomputes
+    every psi(n') in full, a fifth of a second each at 8x8, a second at 16x16)."""
     pb = I.workload("ace16x16")
     ctx, ora, occ, st = setup(pb, 8, 1253, 5703, scale=0.02)
     cond = conditioning(ora, occ)
     la = ctx.log_psi()[0].cpu().numpy()
     la_o, _ = ora.log_psi(occ)
     _check("ace16x16 log|psi|", la, la_o, cond, 1e-4, 1e4, min_good=2)
-    e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
-    e_o, _ = ora.local_energy(occ[:1])
-    _check("ace16x16 E_loc", e[:1], e_o, cond[:1], 1e-4, 1e4, min_good=0)
+    p8 = pb.replace(Lx=8, Ly=8, n_up=14, n_dn=14)
+    ctx8, ora8, occ8, _ = setup(p8, 2, 1258, 5708, scale=0.02)
+    cond8 = conditioning(ora8, occ8)
+    e = ctx8.local_energy(Bd.PATH_FULL).cpu().numpy()
+    e_o, _ = ora8.local_energy(occ8)
+    scale = np.maximum(eloc_term_scale(ora8, occ8), 1.0)
+    _check("ACE Table shape 8x8 E_loc / term scale", e / scale, e_o / scale, cond8, 1e-4, 1e3, min_good=0)
 
 
 def test_ace_symmetry_projection():
