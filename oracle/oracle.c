@@ -812,15 +812,18 @@ static void grad_one(const ora_model *m, const int8_t *occ, double *g, double *H
     for (int q = 0; q < N * h; ++q) dIn[q] = m->residual[l] ? dH[q] : 0.0;
     for (int i = 0; i < N; ++i) {
       for (int c = 0; c < h; ++c) g[off.bias[l] + c] += dZ[(int64_t)i * h + c];
+      int tap = 0; /* index of the offset among the stencil's taps, row-major over the box */
       for (int ky = 0; ky < k; ++ky)
         for (int kx = 0; kx < k; ++kx) {
+          if (!in_stencil(m, k, kx - r, ky - r)) continue;
+          const int d = tap++;
           int j = site_offset(m, i, kx - r, ky - r);
           if (j < 0) continue;
-          const int64_t wo = off.kernel[l] + (int64_t)(ky * k + kx) * h * h;
+          const int64_t wo = off.kernel[l] + (int64_t)d * h * h;
           for (int ci = 0; ci < h; ++ci)
             for (int co = 0; co < h; ++co) {
               g[wo + (int64_t)ci * h + co] += in[(int64_t)j * h + ci] * dZ[(int64_t)i * h + co];
-              dIn[(int64_t)j * h + ci] += K[(int64_t)(ky * k + kx) * h * h + (int64_t)ci * h + co] * dZ[(int64_t)i * h + co];
+              dIn[(int64_t)j * h + ci] += K[(int64_t)d * h * h + (int64_t)ci * h + co] * dZ[(int64_t)i * h + co];
             }
         }
     }
@@ -835,7 +838,7 @@ static void grad_one(const ora_model *m, const int8_t *occ, double *g, double *H
 int ora_grad_logpsi(const ora_model *m, int B, const int8_t *occ, double *grad) {
   const int N = m->Lx * m->Ly, h = m->h, Ne = m->n_up + m->n_dn, L = m->n_layers;
   const int64_t P = ora_param_count(m);
-  if (m->family != 0 || m->stencil != 0) return -1; /* the backward pass covers the SCALE family */
+  if (m->family != 0) return -1; /* the backward pass covers the SCALE family (either stencil) */
 #pragma omp parallel
   {
     double *H = (double *)malloc(sizeof(double) * (int64_t)(L + 1) * N * h);

@@ -323,6 +323,35 @@ def test_gradient_matches_central_differences():
         np.testing.assert_allclose(g[:, q], fd, rtol=2e-5, atol=2e-7)
 
 
+@pytest.mark.parametrize("pbc", [(1, 1), (0, 1)])
+def test_gradient_plus_stencil_central_differences(pbc):
+    """The backward pass with SCALE-L's 13-site plus stencil (weights stored for the taps
+    only, row-major over the 5x5 box) vs central differences: every tap of the first
+    kernel (the four arms' tips included), the site-wise layer, bias, embedding and
+    projection, on the torus and on a cylinder with open x edges."""
+    pb = I.workload("scale_plus6x6").replace(pbc_x=pbc[0], pbc_y=pbc[1], n_layers=3, ksize=[5, 1, 1],
+                                             residual=[1, 0, 0])
+    m = _model(pb, seed=1238, scale=0.3)
+    occ = I.random_configs(pb, 2, 5682)
+    g = m.grad_logpsi(occ)
+    off = I.param_offsets(pb)
+    h = pb.h
+    k0 = off["kernel0"][0]
+    idx = [k0 + d * h * h + (d % h) * h + (3 * d) % h for d in range(13)]
+    idx += [off["kernel1"][0] + 5, off["kernel2"][0] + h * h - 1, off["bias0"][0] + 1, off["bias2"][0] + 3,
+            off["embed"][0] + 4 * h * 7 + int(occ[0, 7]) * h + 2, off["proj_b"][0] + 5, off["proj_w"][0] + 11]
+    eps = 1e-6
+    for q in idx:
+        p1 = m.params.copy(); p1[q] += eps
+        p2 = m.params.copy(); p2[q] -= eps
+        l1, _ = m.with_params(p1).log_psi(occ)
+        l2, _ = m.with_params(p2).log_psi(occ)
+        fd = (l1 - l2) / (2 * eps)
+        np.testing.assert_allclose(g[:, q], fd, rtol=2e-5, atol=2e-7)
+    # a weight of a tap a box stencil would have (dx = 2, dy = 1) does not exist: 13 taps
+    assert off["bias0"][0] - k0 == 13 * h * h
+
+
 def test_projection_bias_gradient_closed_form():
     """d log|det Phi| / d proj_b[s*Ne+k] = sum over spin-s rows a of (Phi^-1)[k][a]."""
     pb = I.workload("hubbard4x4")
