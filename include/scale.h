@@ -146,7 +146,7 @@ typedef struct {
   double ln_eps;          /* ACE: epsilon of the layer normalisation (>= 0) */
   int32_t stencil;        /* SCALE_STENCIL_*; the SCALE family's cached update takes layer 0 as a
                              1x1 or 3x3 box or the 5x5 plus (disk), other shapes run by full
-                             recompute; scale_grad_logpsi needs the box */
+                             recompute; scale_grad_logpsi takes either stencil */
 } scale_arch;
 
 typedef struct {
@@ -259,7 +259,8 @@ scale_status scale_refresh(scale_ctx *ctx, int32_t force_all);
 /* Per-sample gradients d log|psi| / d theta, grad [B][P] float64 (flat parameter
  * layout): d log|det Phi| / d Phi = Phi^-T, back through the projection, every layer and
  * the embedding (hand-written backward). recompute = 1 keeps only every ceil(sqrt(L))-th
- * layer input and recomputes the rest (for deep stacks that exceed the scratch). */
+ * layer input and recomputes the rest (for deep stacks that exceed the scratch).
+ * SCALE family only (either stencil); ACE and the wide shapes return SCALE_EUNSUPPORTED. */
 scale_status scale_grad_logpsi(scale_ctx *ctx, double *grad, int32_t recompute);
 
 /* Counters since creation (host struct). Synchronises the context's stream. */

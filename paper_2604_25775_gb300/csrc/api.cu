@@ -506,8 +506,8 @@ scale_status scale_grad_logpsi(scale_ctx* c, double* grad, int32_t recompute) {
   scale_status s = check_loaded(c);
   if (s != SCALE_OK) return s;
   if (!grad) return SCALE_EINVAL;
-  if (c->ace || c->arch.stencil != SCALE_STENCIL_BOX) {
-    c->err = "the per-sample gradient covers the SCALE family with the box stencil";
+  if (c->ace) {
+    c->err = "the per-sample gradient covers the SCALE family";
     return SCALE_EUNSUPPORTED;
   }
   SCALE_TRY(c, launch_grad(c, grad, recompute));

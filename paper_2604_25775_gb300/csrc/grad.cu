@@ -4,7 +4,8 @@
 //   proj_b[s*Ne+k]     += sum_{slots a of spin s} Binv[a][k]
 //   proj_w[c][s*Ne+k]  += sum_{slots a of spin s} H(L)_{i_a}[c] Binv[a][k]
 //   dH(L)_i[c]          = sum_{s: (s,i) occupied} Pt[s][slot(s,i)][c]     (Pt = W_s Binv)
-//   layer l (out = res*in + act(z), z = b + sum_d K[d]^T in_{i+d}):
+//   layer l (out = res*in + act(z), z = b + sum_d K[d]^T in_{i+d}, d over the stencil's taps:
+//   the k x k box, or its offsets within L2 distance (k-1)/2, weights stored per tap):
 //     dz = dout * act'(z); db = sum_i dz_i; dK[d][ci][co] = sum_i in_{i+d}[ci] dz_i[co]
 //     din_j = res*dout_j + sum_d K[d] dz_{j-d}
 //   embedding row E_i[n_i] += dH(0)_i.
@@ -31,11 +32,14 @@ __global__ void k_fwd_layer(Lattice lat, Net<T> net, int l, const int8_t* __rest
   const int k = net.ksize[l], r = (k - 1) / 2;
   const int8_t* ob = occ + (size_t)b * N;
   T z = net.bias[l][c];
+  int d = 0;  // tap index, row-major over the box
   for (int ky = 0; ky < k; ++ky)
     for (int kx = 0; kx < k; ++kx) {
+      if (!stencil_in(net.stencil, k, kx - r, ky - r)) continue;
+      const int t = d++;
       const int j = site_off(lat, i, kx - r, ky - r);
       if (j < 0) continue;
-      const T* w = net.kernel[l] + (size_t)(ky * k + kx) * h * h + c;
+      const T* w = net.kernel[l] + (size_t)t * h * h + c;
       const T* x = (l == 0) ? net.embed + ((size_t)(net.per_site ? j * 4 : 0) + (ob[j] & 3)) * h
                             : in + ((size_t)b * N + j) * h;
       for (int ci = 0; ci < h; ++ci) z += x[ci] * w[(size_t)ci * h];
@@ -107,14 +111,16 @@ __global__ void k_grad_dz(Lattice lat, Net<T> net, int l, const T* __restrict__ 
 
 // dK[d][ci][co] = sum_i in_{i+d}[ci] dz_i[co]
 template <typename T>
-__global__ void k_grad_kernel(Lattice lat, Net<T> net, int l, const int8_t* __restrict__ occ, const T* __restrict__ in,
-                              const T* __restrict__ dz, int64_t off_k, int64_t P, double* __restrict__ grad) {
+__global__ void k_grad_kernel(Lattice lat, Net<T> net, int l, int taps, const int8_t* __restrict__ occ,
+                              const T* __restrict__ in, const T* __restrict__ dz, int64_t off_k, int64_t P,
+                              double* __restrict__ grad) {
   const int b = blockIdx.y;
-  const int N = lat.N, h = net.h, k = net.ksize[l], r = (k - 1) / 2;
+  const int N = lat.N, h = net.h, k = net.ksize[l];
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= k * k * h * h) return;
+  if (q >= taps * h * h) return;
   const int d = q / (h * h), rem = q - d * h * h, ci = rem / h, co = rem - ci * h;
-  const int dx = d % k - r, dy = d / k - r;
+  int dx, dy;
+  stencil_tap(net.stencil, k, d, dx, dy);
   const int8_t* ob = occ + (size_t)b * N;
   double acc = 0.0;
   for (int i = 0; i < N; ++i) {
@@ -137,11 +143,14 @@ __global__ void k_grad_din(Lattice lat, Net<T> net, int l, const T* __restrict__
   if (q >= N * h) return;
   const int j = q / h, ci = q - j * h;
   T acc = net.resid[l] ? dout[(size_t)b * N * h + q] : T(0);
+  int d = 0;  // tap index, row-major over the box
   for (int ky = 0; ky < k; ++ky)
     for (int kx = 0; kx < k; ++kx) {
+      if (!stencil_in(net.stencil, k, kx - r, ky - r)) continue;
+      const int t = d++;
       const int i = site_off(lat, j, -(kx - r), -(ky - r));  // site i with i + d = j
       if (i < 0) continue;
-      const T* w = net.kernel[l] + (size_t)(ky * k + kx) * h * h + (size_t)ci * h;
+      const T* w = net.kernel[l] + (size_t)t * h * h + (size_t)ci * h;
       const T* g = dz + ((size_t)b * N + i) * h;
       for (int co = 0; co < h; ++co) acc += w[co] * g[co];
     }
@@ -208,9 +217,11 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
   // offsets
   int64_t off = (int64_t)(c->arch.per_site_embed ? N : 1) * 4 * h;
   int64_t offK[kMaxLayers], offB[kMaxLayers];
+  int taps[kMaxLayers];
   for (int l = 0; l < L; ++l) {
+    taps[l] = stencil_taps(net.stencil, net.ksize[l]);
     offK[l] = off;
-    off += (int64_t)net.ksize[l] * net.ksize[l] * h * h;
+    off += (int64_t)taps[l] * h * h;
     offB[l] = off;
     off += h;
   }
@@ -245,9 +256,9 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
       const T* lin = (l == 0) ? nullptr : (l == l0 ? ck + (size_t)seg * slab : segH + (size_t)(l - l0) * slab);
       k_grad_dz<T><<<B, 256, 0, c->stream>>>(c->lat, net, l, dcur, segZ + (size_t)(l - l0) * slab, dZ, offB[l], c->P,
                                              grad);
-      const int kq = net.ksize[l] * net.ksize[l] * h * h;
-      k_grad_kernel<T><<<dim3((kq + 127) / 128, B), 128, 0, c->stream>>>(c->lat, net, l, c->occ, lin, dZ, offK[l],
-                                                                          c->P, grad);
+      const int kq = taps[l] * h * h;
+      k_grad_kernel<T><<<dim3((kq + 127) / 128, B), 128, 0, c->stream>>>(c->lat, net, l, taps[l], c->occ, lin, dZ,
+                                                                          offK[l], c->P, grad);
       k_grad_din<T><<<gridL, 128, 0, c->stream>>>(c->lat, net, l, dcur, dZ, dnext);
       std::swap(dcur, dnext);
     }

@@ -67,3 +67,27 @@ def test_grad_central_differences_gpu():
             c2.close()
         fd = (vals[0] - vals[1]) / (2 * h)
         np.testing.assert_allclose(g[:, q], fd, rtol=2e-5, atol=2e-7)
+
+
+@pytest.mark.parametrize("variant", ["torus_fp64", "open_fp64", "mixed"])
+def test_grad_plus_stencil(variant):
+    """SCALE-L's 13-site plus stencil in layer 0 (weights per tap): gradients against the
+    oracle's backward pass, FP64 within 1e-10 and mixed within 1e-4 of each sample's largest
+    entry."""
+    pb = I.workload("scale_plus6x6")
+    if variant == "open_fp64":
+        pb = pb.replace(pbc_x=0, tp=-0.2)
+    elif variant == "mixed":
+        pb = pb.replace(precision=I.PREC_MIXED)
+    ctx, ora, occ, st = setup(pb, 24, 1273, 5723, scale=0.3)
+    g = ctx.grad_logpsi().cpu().numpy()
+    g_o = ora.grad_logpsi(occ)
+    cond = conditioning(ora, occ)
+    tol, cond_ok = (1e-4, 1e3) if variant == "mixed" else (1e-10, 1e6)
+    good = cond < cond_ok
+    assert good.sum() >= 4
+    scale = np.maximum(np.abs(g_o[good]).max(axis=1, keepdims=True), 1.0)
+    err = (np.abs(g[good] - g_o[good]) / scale).max()
+    print(f"grad plus stencil {variant}: max rel err {err:.3e}")
+    assert err <= tol
+
