@@ -336,7 +336,7 @@ Net<T> make_net(scale_ctx* c) {
   for (int l = 0; l < c->L; ++l) {
     n.ksize[l] = c->arch.ksize[l];
     n.resid[l] = c->arch.residual[l];
-    n.kernel[l] = base + p;
+    n.kernel[l] = base + p;  // [taps][h][h]: the stencil's taps in row-major box order
     p += (int64_t)stencil_taps(c->arch.stencil, n.ksize[l]) * c->h * c->h;
     n.bias[l] = base + p;
     p += c->h;

@@ -87,7 +87,7 @@ struct Net {
   int ksize[kMaxLayers];
   int resid[kMaxLayers];
   const T* embed;                // [Ns][4][h]
-  const T* kernel[kMaxLayers];   // [taps][h][h], taps in row-major box order
+  const T* kernel[kMaxLayers];   // [k][k][h][h]
   const T* bias[kMaxLayers];     // [h]
   const T* proj_w;               // [h][2Ne]
   const T* proj_b;               // [2Ne]
