@@ -125,9 +125,9 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   const size_t P = (size_t)param_count(s, a);
   const size_t k0 = a->ksize[0];
   const bool ace = a->family != SCALE_FAMILY_SCALE;
-  // ACE / wide activations: the (hi, lo) halves of the widest layer (tensor-core layers keep
-  // their rows split between them)
-  const size_t hmax = ace ? 2 * std::max<size_t>(h, (size_t)ace_width_out(*a, a->n_layers - 1)) : h;
+  // ACE / wide activations: the widest layer, in mixed precision as (hi, lo) halves
+  // (tensor-core layers keep their rows split between them)
+  const size_t hmax = ace ? (T == 4 ? 2 : 1) * std::max<size_t>(h, (size_t)ace_width_out(*a, a->n_layers - 1)) : h;
   size_t t = 0;
   t += P * 8 + (T == 4 ? P * 4 : 0);
   t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0) + 2 * N * Ne * T;
@@ -295,7 +295,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   if (!c->fp64) A(&c->M0_32, 2 * N * Ne * 4);
   A((char**)&c->M0b, 2 * N * Ne * T);
   const bool ace = c->ace;
-  const size_t hmax = ace ? 2 * (size_t)c->hmax : h;  // the (hi, lo) halves of the widest layer
+  const size_t hmax = ace ? (c->fp64 ? 1 : 2) * (size_t)c->hmax : h;  // mixed: (hi, lo) halves
   A((char**)&c->KE, ace ? 16 : Ns * 4 * stencil_taps(arch->stencil, c->k0) * h * T);
   A(&c->bonds, std::max<size_t>(bonds.size(), 2) * 4);
   A(&c->occ, B * N);
