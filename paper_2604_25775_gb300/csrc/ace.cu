@@ -426,14 +426,16 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
     Lattice lat, const float* __restrict__ bimg, const float* __restrict__ bias, const float* __restrict__ gam,
     const float* __restrict__ bet, int act, float eps, int C, int CO, int res, int ks, int stencil, int taps,
     const float* __restrict__ in_hi, const float* __restrict__ in_lo, float* __restrict__ out_hi,
-    float* __restrict__ out_lo, long long rows, int* __restrict__ err) {
+    float* __restrict__ out_lo, long long row0, long long rows, int* __restrict__ err) {
   // C input channels (K = taps x C), CO output channels (this CTA: [cb, cb + N)); res: add the
   // input row (C == CO). A normalised block is one tile wide: C == CO == N.
   if constexpr (LN) C = CO = N;
   using S = TcShape<N>;
   const int KC = C / kTcKC;
   const int STEPS = taps * KC;
-  const int cb = blockIdx.y * N;  // first output column of this CTA
+  // Grid (column tile, row tile): the CO / N column tiles of the same 128 rows are adjacent
+  // in launch order and run side by side, so all but the first read the rows from L2.
+  const int cb = blockIdx.x * N;  // first output column of this CTA
   constexpr int H2 = N / 2;  // epilogue columns per thread
   constexpr uint32_t IDESC = tc::idesc_tf32<kTcRows, N>();
   extern __shared__ unsigned char smem_raw[];
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
   __shared__ float s_sum[2][kTcRows], s_sq[2][kTcRows];  // per-half row sums for the normalisation
   const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcRows - 1), part = tid >> 7;
   const int Ns = lat.N;
-  const long long R = (long long)blockIdx.x * kTcRows + row;
+  const long long R = row0 + (long long)blockIdx.y * kTcRows + row;
   const bool valid = R < rows;
   const long long cfg = valid ? R / Ns : 0;
   const int site = valid ? (int)(R - cfg * Ns) : 0;
@@ -637,11 +639,17 @@ cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, 
   cudaError_t e =
       cudaFuncSetAttribute(k_ace_conv_tc<N, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)((rows + kTcRows - 1) / kTcRows), (unsigned)(CO / N));
-  k_ace_conv_tc<N, LN><<<grid, kTcThreads, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, C, CO, res, ks, stencil,
-                                                          stencil_taps(stencil, ks), in_hi, in_lo, out_hi, out_lo,
-                                                          rows, err);
-  return cudaGetLastError();
+  // rows [row0, rows) per launch, at most 65535 row tiles (the grid's y limit) each
+  const long long tiles = (rows + kTcRows - 1) / kTcRows;
+  for (long long t0 = 0; t0 < tiles; t0 += 65535) {
+    const dim3 grid((unsigned)(CO / N), (unsigned)std::min<long long>(65535, tiles - t0));
+    k_ace_conv_tc<N, LN><<<grid, kTcThreads, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, C, CO, res, ks,
+                                                            stencil, stencil_taps(stencil, ks), in_hi, in_lo,
+                                                            out_hi, out_lo, t0 * kTcRows, rows, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Conv layers on tcgen05: ACE blocks of width 48, 144 or 192 (3x3 box, one column tile,
