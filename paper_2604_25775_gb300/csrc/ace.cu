@@ -20,7 +20,8 @@
 //               their output widths are multiples of 128): the 5th-generation tensor cores.
 //               One CTA of 256 threads (two per row) owns 128 rows (TMEM lanes) and a tile
 //               of N output channels (TMEM columns; the whole width for a normalised block,
-//               else 128 to 192). The K loop runs over (offset d, 8-channel chunk) stages
+//               else 128 to 192); the column tiles of the same rows are adjacent in the
+//               grid, so they share the gathered rows through L2. The K loop runs over (offset d, 8-channel chunk) stages
 //               in a 6-slot shared-memory ring with 4 stages of copies in flight: each
 //               thread gathers its row's 8 input channels, hi or lo part, from the
 //               neighbour site with 16-byte cp.async (zero fill past an open edge),
