@@ -129,13 +129,14 @@ typedef struct {
                              (about 2^-16 per layer instead of 2^-21).
                              The tensor-core path needs the SCALE layout and h in
                              {16, 32, 64}; otherwise the layers run in FP32 FMA.
-                             ACE and wide shapes: MIXED runs the layers as the same
-                             three TF32 products, on tcgen05 for the conv blocks of
-                             width 48, 144 or 192, the wide conv of width 384 or 640
-                             (3x3 box or 5x5 plus) and the site-wise layers after them
-                             whose widths are multiples of 128; on mma.sync for the
-                             other layers that have an mma.sync fragment shape; in FP32
-                             FMA otherwise. Slater matrices and LU stay FP64. */
+                             ACE and wide shapes: when every layer has an mma.sync
+                             fragment shape, MIXED runs the layers as the same three
+                             TF32 products, on tcgen05 for the conv blocks of width 48,
+                             144 or 192, the wide conv of width 384 or 640 (3x3 box or
+                             5x5 plus) and the site-wise layers after them whose widths
+                             are multiples of 128, on mma.sync for the rest; otherwise
+                             every layer runs in FP32 FMA. Slater matrices and LU stay
+                             FP64. */
   int32_t refresh_every;  /* FP64 re-factorisation of Phi every this many commits (>= 1);
                              counters start staggered at load (sample b at b mod
                              refresh_every) so refreshes spread evenly over calls */
