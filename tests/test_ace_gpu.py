@@ -26,7 +26,8 @@ def _check(name, gpu, ora, cond, tol, cond_ok, min_good=1):
     print(f"{name}: n={len(err)} good={good.sum()} max_err(good)={err[good].max() if good.any() else 0:.3e} "
           f"max_err={err.max():.3e}")
     assert good.sum() >= min_good
-    assert err[good].max() <= tol
+    if good.any():
+        assert err[good].max() <= tol
     assert np.all(err <= np.maximum(tol, cond * c * unit))
 
 
