@@ -410,10 +410,45 @@ def main():
         load_ms, cold_eloc_ms = a.elapsed_time(mid), mid.elapsed_time(b2)
         line["cold"] = {"load_ms": load_ms, "eloc_ms": cold_eloc_ms,
                         "eloc_per_s": B / ((load_ms + cold_eloc_ms) / 1e3)}
-        # full-recompute path on a subset of the same walkers
+        ctx2.close()
+        # Metropolis sweep on the same walkers: hop proposal, rank-r ratio, accept, Woodbury
+        # commit of the accepted moves (random numbers generated on the host beforehand). The
+        # first --sweep-steps are timed; the sweep then continues untimed to 2.5 N steps per
+        # walker, so that the walkers are drawn from |psi|^2 for the comparison below.
+        steps_per_sample = int(2.5 * pb.N)
+        occ_cmp, cmp_from = occ_d, "uniformly random walkers of the workload"
+        if args.sweep_steps > 0:
+            S = args.sweep_steps
+            ctxs = Bd.make_context(pb, params, M0, B)
+            ctxs.scale_load(occ_d)
+            pk, dr, uu = I.metropolis_randoms(pb, B, 4 + max(S, steps_per_sample), 77)
+            pk_d, dr_d, uu_d = (torch.from_numpy(x).cuda() for x in (pk, dr, uu))
+            ctxs.sweep(pk_d[:4].contiguous(), dr_d[:4].contiguous(), uu_d[:4].contiguous())
+            pk_t, dr_t, uu_t = pk_d[4:4 + S].contiguous(), dr_d[4:4 + S].contiguous(), uu_d[4:4 + S].contiguous()
+            torch.cuda.synchronize()
+            a.record()
+            acc_s = ctxs.sweep(pk_t, dr_t, uu_t)
+            b2.record()
+            torch.cuda.synchronize()
+            sw_ms = a.elapsed_time(b2)
+            line["sweep"] = {"walkers": B, "steps": S, "ms": sw_ms,
+                             "walker_steps_per_s": B * S / (sw_ms / 1e3),
+                             "acceptance": float(acc_s.double().mean().item() / S),
+                             "ms_per_sweep_2.5N": sw_ms / S * steps_per_sample,
+                             "steps_per_sweep": steps_per_sample}
+            if steps_per_sample > S:
+                ctxs.sweep(pk_d[4 + S:4 + steps_per_sample].contiguous(), dr_d[4 + S:4 + steps_per_sample].contiguous(),
+                           uu_d[4 + S:4 + steps_per_sample].contiguous())
+            occ_cmp = ctxs.get_occ()
+            cmp_from = f"walkers after {max(S, steps_per_sample)} Metropolis steps each (|psi|^2-distributed)"
+            torch.cuda.synchronize()
+            del pk_d, dr_d, uu_d, pk_t, dr_t, uu_t
+            ctxs.close()
+        # full-recompute path (psi(n) and every psi(n') by a fresh forward and FP64 LU) against
+        # the low-rank path on the same walkers, same GPU and precision mode
         nf = args.full_samples
         ctxf = Bd.make_context(pb, params, M0, nf)
-        ctxf.scale_load(occ_d[:nf].contiguous())
+        ctxf.scale_load(occ_cmp[:nf].contiguous())
         ef = torch.empty(nf, dtype=torch.float64, device="cuda")
         el = torch.empty(nf, dtype=torch.float64, device="cuda")
         ctxf.scale_local_energy(ef, Bd.PATH_FULL)
@@ -425,14 +460,17 @@ def main():
         full_ms = a.elapsed_time(b2)
         ctxf.scale_local_energy(el, Bd.PATH_LOWRANK)
         torch.cuda.synchronize()
-        agree = float(((ef - el).abs() / ef.abs().clamp(min=1.0)).max().item())
+        diff = ((ef - el).abs() / ef.abs().clamp(min=1.0)).cpu().numpy()
         full_rate = nf / (full_ms / 1e3)
         lowrank_rate = B / (eloc_ms / 1e3)
-        line["full_recompute"] = {"walkers": nf, "ms": full_ms, "eloc_per_s": full_rate,
+        line["full_recompute"] = {"walkers": nf, "walkers_from": cmp_from, "ms": full_ms, "eloc_per_s": full_rate,
+                                  "chunk": int(ctxf.scale_get_stats()["full_chunk"]),
+                                  "determinants": "FP64 LU of the mode-precision Slater matrices",
                                   "lowrank_eloc_per_s": lowrank_rate, "speedup_lowrank_vs_full": lowrank_rate / full_rate,
-                                  "max_rel_diff_vs_lowrank": agree}
+                                  "max_rel_diff_vs_lowrank": float(diff.max()),
+                                  "median_rel_diff_vs_lowrank": float(np.median(diff)),
+                                  "frac_within_1e-4": float(np.mean(diff <= 1e-4))}
         ctxf.close()
-        ctx2.close()
         # per-sample gradients on a subset
         ng = 1024
         ctxg = Bd.make_context(pb, params, M0, ng)
@@ -447,30 +485,6 @@ def main():
         line["grad"] = {"walkers": ng, "ms": a.elapsed_time(b2), "params": ctxg.P}
         del g
         ctxg.close()
-        # Metropolis sweep on the same walkers: hop proposal, rank-r ratio, accept, Woodbury
-        # commit of the accepted moves (random numbers generated on the host beforehand)
-        if args.sweep_steps > 0:
-            S = args.sweep_steps
-            ctxs = Bd.make_context(pb, params, M0, B)
-            ctxs.scale_load(occ_d)
-            pk, dr, uu = I.metropolis_randoms(pb, B, 4 + S, 77)
-            pk_d, dr_d, uu_d = (torch.from_numpy(x).cuda() for x in (pk, dr, uu))
-            ctxs.sweep(pk_d[:4].contiguous(), dr_d[:4].contiguous(), uu_d[:4].contiguous())
-            pk_t, dr_t, uu_t = pk_d[4:].contiguous(), dr_d[4:].contiguous(), uu_d[4:].contiguous()
-            torch.cuda.synchronize()
-            a.record()
-            acc_s = ctxs.sweep(pk_t, dr_t, uu_t)
-            b2.record()
-            torch.cuda.synchronize()
-            sw_ms = a.elapsed_time(b2)
-            steps_per_sample = int(2.5 * pb.N)
-            line["sweep"] = {"walkers": B, "steps": S, "ms": sw_ms,
-                             "walker_steps_per_s": B * S / (sw_ms / 1e3),
-                             "acceptance": float(acc_s.double().mean().item() / S),
-                             "ms_per_sweep_2.5N": sw_ms / S * steps_per_sample,
-                             "steps_per_sweep": steps_per_sample}
-            del pk_d, dr_d, uu_d, pk_t, dr_t, uu_t
-            ctxs.close()
         # symmetry projection over the lattice translations: |G| fresh amplitudes per walker;
         # ACE (no cached update: every psi(n') of a local energy is a fresh forward + LU)
         from paper_2604_25775_gb300 import next_bench

@@ -166,6 +166,7 @@ typedef struct {
   double drift_max;        /* largest drift residual seen */
   int32_t batch;           /* samples currently loaded */
   int32_t max_moves;       /* capacity of connected configurations per sample */
+  int32_t full_chunk;      /* configurations per chunk of the full-recompute path */
 } scale_stats;
 
 typedef struct scale_ctx scale_ctx;
@@ -213,9 +214,11 @@ scale_status scale_ratios(scale_ctx *ctx, const int32_t *moves, int32_t M, doubl
  * path SCALE_PATH_LOWRANK: connected configurations enumerated on the device, each ratio a
  *   rank-r determinant against the cached Phi^-1 after an incremental receptive-field
  *   update of the network (needs k_l = 1 for l >= 1).
- * path SCALE_PATH_FULL: every psi(n') by a full network forward and a fresh LU in the
- *   precision of the mode (FP64 mode: FP64; mixed: FP32) -- the comparison path of
- *   Sec. III.A, any layer layout. */
+ * path SCALE_PATH_FULL: psi(n) and every psi(n') by a full network forward in the mode's
+ *   precision and a fresh FP64 LU with partial pivoting -- the comparison path of
+ *   Sec. III.A, any layer layout; nothing cached by the context enters the result. The
+ *   configurations run in chunks sized from memory (up to 4096 per chunk), and the call
+ *   stays asynchronous (the counts of connected configurations never reach the host). */
 scale_status scale_local_energy(scale_ctx *ctx, int32_t path, double *eloc);
 
 /* Apply one accepted move per sample (moves [B][4] int32, kind -1 = reject): Woodbury
@@ -294,9 +297,12 @@ void scale_destroy(scale_ctx *ctx);
  * sample does not fit returns SCALE_EBUDGET. Every call shares that array and leaves its
  * contents behind: calls that overlap on the GPU (other streams or host threads on the same
  * device) race and must be serialised by the caller. The first call on a device looks up the
- * array's device address with that device current (cudaGetSymbolAddress); make that first
- * call before any stream capture. Work is enqueued on cuda_stream (NULL = legacy stream).
- * Per-sample problems as in scale_log_psi (-inf, sign 0). */
+ * array's device address with that device current (cudaGetSymbolAddress) and caches it for
+ * the device's current CUDA context; a call made under another context of the device (after
+ * cudaDeviceReset, or a context the caller made current) looks it up again. Make the first
+ * call on a device, and the first after such a change, before any stream capture. Work is
+ * enqueued on cuda_stream (NULL = legacy stream). SCALE_EUNSUPPORTED for the ACE and wide
+ * families. Per-sample problems as in scale_log_psi (-inf, sign 0). */
 scale_status scale_log_psi_noalloc(const scale_system *sys, const scale_arch *arch, const double *params,
                                    const double *M0, const int8_t *occ, int32_t B, double *logabs,
                                    int32_t *sign, void *cuda_stream);

@@ -5,4 +5,4 @@ The library (csrc/, include/scale.h) evaluates log psi, amplitude ratios, local 
 log-psi gradients of the SCALE convolutional-backflow ansatz (arXiv 2604.25775, Sec. II).
 Importing the package loads nothing; the library is loaded on first use.
 """
-__all__ = ["inputs", "binding", "build", "autograd", "serve"]
+__all__ = ["inputs", "binding", "build", "autograd"]

@@ -57,7 +57,7 @@ class scale_stats(ctypes.Structure):
     _fields_ = [("n_eloc", ctypes.c_int64), ("n_eloc_full", ctypes.c_int64),
                 ("n_commits", ctypes.c_int64), ("n_refresh", ctypes.c_int64),
                 ("n_drift_refresh", ctypes.c_int64), ("drift_max", ctypes.c_double),
-                ("batch", ctypes.c_int32), ("max_moves", ctypes.c_int32)]
+                ("batch", ctypes.c_int32), ("max_moves", ctypes.c_int32), ("full_chunk", ctypes.c_int32)]
 
 
 def library_path() -> str:

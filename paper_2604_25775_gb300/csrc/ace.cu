@@ -122,7 +122,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // H0 rows [C][N][h] from the embedding tables.
 template <typename T>
 __global__ void k_ace_embed(int N, int h, int per_site, const T* __restrict__ embed, const int8_t* __restrict__ occ,
-                            long long total, T* __restrict__ out) {
+                            long long total, T* __restrict__ out, const int* __restrict__ vcfg) {
+  if (vcfg) total = min(total, (long long)*vcfg * N * h);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
     const long long row = q / h;
@@ -140,9 +141,10 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kAceRowsGeneric) k_ace_layer(
     Lattice lat, const T* __restrict__ K, const T* __restrict__ bias, const T* __restrict__ gam,
     const T* __restrict__ bet, int ks, int stencil, int cin, int cout, int res, int act, double eps,
-    const T* __restrict__ in, T* __restrict__ out, long long rows) {
+    const T* __restrict__ in, T* __restrict__ out, long long rows, const int* __restrict__ vcfg) {
   constexpr int MQ = kAceMaxHMlp / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (vcfg) rows = min(rows, (long long)*vcfg * lat.N);
   const long long R = (long long)blockIdx.x * kAceRowsGeneric + warp;
   if (R >= rows) return;  // whole warp
   const int N = lat.N;
@@ -241,12 +243,13 @@ template <int NTW, int WC, bool LN>
 __global__ void __launch_bounds__(256, (NTW > 18 || NTW == 16 ? 1 : 2)) k_ace_mma(
     Lattice lat, const WFrag* __restrict__ frag, const float* __restrict__ bias, const float* __restrict__ gam,
     const float* __restrict__ bet, int ks, int stencil, int cin, int res, int act, float eps,
-    const float* __restrict__ in, float* __restrict__ out, long long rows) {
+    const float* __restrict__ in, float* __restrict__ out, long long rows, const int* __restrict__ vcfg) {
   static_assert(!LN || WC == 1, "the epilogue normalisation needs a row's channels in one warp");
   constexpr int NT = NTW * WC, COUT = 8 * NT, WR = 8 / WC, ROWS = 16 * WR;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int wr = warp / WC, wc = warp % WC;
   const int N = lat.N;
+  if (vcfg) rows = min(rows, (long long)*vcfg * N);
   const long long r0 = (long long)blockIdx.x * ROWS + wr * 16 + g, r1 = r0 + 8;
   const bool v0 = r0 < rows, v1 = r1 < rows;
   const long long c0 = v0 ? r0 / N : 0, c1 = v1 ? r1 / N : 0;
@@ -401,7 +404,8 @@ __global__ void k_ace_build_bimg(const float* __restrict__ K, int CI, int N, int
 // H0 rows split for the tensor cores: out_hi = tf32(E), out_lo = tf32(E - out_hi).
 __global__ void k_ace_embed_split(int N, int h, int per_site, const float* __restrict__ embed,
                                   const int8_t* __restrict__ occ, long long total, float* __restrict__ out_hi,
-                                  float* __restrict__ out_lo) {
+                                  float* __restrict__ out_lo, const int* __restrict__ vcfg) {
+  if (vcfg) total = min(total, (long long)*vcfg * N * h);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
     const long long row = q / h;
@@ -427,7 +431,8 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
     Lattice lat, const float* __restrict__ bimg, const float* __restrict__ bias, const float* __restrict__ gam,
     const float* __restrict__ bet, int act, float eps, int C, int CO, int res, int ks, int stencil, int taps,
     const float* __restrict__ in_hi, const float* __restrict__ in_lo, float* __restrict__ out_hi,
-    float* __restrict__ out_lo, long long row0, long long rows, int* __restrict__ err) {
+    float* __restrict__ out_lo, long long row0, long long rows, int* __restrict__ err,
+    const int* __restrict__ vcfg) {
   // C input channels (K = taps x C), CO output channels (this CTA: [cb, cb + N)); res: add the
   // input row (C == CO). A normalised block is one tile wide: C == CO == N.
   if constexpr (LN) C = CO = N;
@@ -449,6 +454,10 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
   __shared__ float s_sum[2][kTcRows], s_sq[2][kTcRows];  // per-half row sums for the normalisation
   const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcRows - 1), part = tid >> 7;
   const int Ns = lat.N;
+  // rows past the valid configurations of a chunk (vcfg: their count on the device): a tile
+  // that holds none of them leaves before any barrier, mbarrier or TMEM allocation
+  if (vcfg) rows = min(rows, (long long)*vcfg * Ns);
+  if (row0 + (long long)blockIdx.y * kTcRows >= rows) return;
   const long long R = row0 + (long long)blockIdx.y * kTcRows + row;
   const bool valid = R < rows;
   const long long cfg = valid ? R / Ns : 0;
@@ -635,7 +644,7 @@ template <int N, bool LN>
 cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, const float* bias, const float* g,
                         const float* be, int act, float eps, int C, int CO, int res, int ks, int stencil,
                         const float* in_hi, const float* in_lo, float* out_hi, float* out_lo, long long rows,
-                        int* err) {
+                        int* err, const int* vcfg) {
   using S = TcShape<N>;
   cudaError_t e =
       cudaFuncSetAttribute(k_ace_conv_tc<N, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
@@ -646,7 +655,7 @@ cudaError_t run_conv_tc(cudaStream_t st, const Lattice& lat, const float* bimg, 
     const dim3 grid((unsigned)(CO / N), (unsigned)std::min<long long>(65535, tiles - t0));
     k_ace_conv_tc<N, LN><<<grid, kTcThreads, S::SMEM, st>>>(lat, bimg, bias, g, be, act, eps, C, CO, res, ks,
                                                             stencil, stencil_taps(stencil, ks), in_hi, in_lo,
-                                                            out_hi, out_lo, t0 * kTcRows, rows, err);
+                                                            out_hi, out_lo, t0 * kTcRows, rows, err, vcfg);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -664,11 +673,12 @@ bool tc_sitewise(int cin, int cout) { return cin % kTcKC == 0 && cout % 128 == 0
 
 cudaError_t launch_conv_tc(const scale_ctx* c, bool ln, int cin, int cout, int res, int ks, const float* bimg,
                            const float* bias, const float* g, const float* be, int act, float eps,
-                           const float* in_hi, const float* in_lo, float* out_hi, float* out_lo, long long rows) {
+                           const float* in_hi, const float* in_lo, float* out_hi, float* out_lo, long long rows,
+                           const int* vcfg) {
   const int st = c->arch.stencil;
 #define SCALE_TC(NT, LNV) \
   run_conv_tc<NT, LNV>(c->stream, c->lat, bimg, bias, g, be, act, eps, cin, cout, res, ks, st, in_hi, in_lo, \
-                       out_hi, out_lo, rows, c->ace_err)
+                       out_hi, out_lo, rows, c->ace_err, vcfg)
   if (ln) {
     if (cout == 48) return SCALE_TC(48, true);
     if (cout == 144) return SCALE_TC(144, true);
@@ -692,12 +702,13 @@ constexpr int kPhiT = 64, kPhiK = 32;
 template <typename T>
 __global__ void __launch_bounds__(256) k_ace_phi(Lattice lat, AceNet<T> net, int hl, const int8_t* __restrict__ occ,
                                                  const T* __restrict__ HL, const int* __restrict__ err,
-                                                 double* __restrict__ phi) {
+                                                 double* __restrict__ phi, const int* __restrict__ vcfg) {
   extern __shared__ int olist[];  // [2N]
   __shared__ T Xs[kPhiK][kPhiT + 1];
   __shared__ T Ws[kPhiK][kPhiT];
   __shared__ int s_n;
   const int b = blockIdx.z, N = lat.N, Ne = lat.Ne, tid = threadIdx.x;
+  if (vcfg && b >= *vcfg) return;  // whole CTA: past the valid configurations of a chunk
   const int8_t* ob = occ + (size_t)b * N;
   if (tid < 32) {  // one warp lists the occupied orbitals in order
     int n = 0;
@@ -807,18 +818,18 @@ size_t frag_layer_bytes(const scale_arch& a, int l) {
 template <int NTW, int WC, bool LN>
 void run_mma(cudaStream_t st, const Lattice& lat, const WFrag* frag, const float* bias, const float* g,
              const float* be, int ks, int stencil, int cin, int res, int act, float eps, const float* in,
-             float* out, long long rows) {
+             float* out, long long rows, const int* vcfg) {
   constexpr int ROWS = 16 * (8 / WC);
   const long long blocks = (rows + ROWS - 1) / ROWS;
   k_ace_mma<NTW, WC, LN><<<(unsigned)blocks, 256, 0, st>>>(lat, frag, bias, g, be, ks, stencil, cin, res, act, eps,
-                                                            in, out, rows);
+                                                            in, out, rows, vcfg);
 }
 
 bool launch_mma_layer(cudaStream_t st, const Lattice& lat, const MmaPlan& p, bool ln, const WFrag* frag,
                       const float* bias, const float* g, const float* be, int ks, int stencil, int cin, int res,
-                      int act, float eps, const float* in, float* out, long long rows) {
+                      int act, float eps, const float* in, float* out, long long rows, const int* vcfg) {
 #define SCALE_ACE_MMA(NTW, WC, LN) \
-  run_mma<NTW, WC, LN>(st, lat, frag, bias, g, be, ks, stencil, cin, res, act, eps, in, out, rows)
+  run_mma<NTW, WC, LN>(st, lat, frag, bias, g, be, ks, stencil, cin, res, act, eps, in, out, rows, vcfg)
   if (ln) {
     if (p.ntw == 6) SCALE_ACE_MMA(6, 1, true);
     else if (p.ntw == 18) SCALE_ACE_MMA(18, 1, true);
@@ -849,7 +860,7 @@ bool tc_layer(const scale_ctx* c, int l) {
 }
 
 template <typename T>
-cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64) {
+cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg) {
   const AceNet<T> net = make_ace_net<T>(c);
   const int N = c->N;
   const long long rows = (long long)C * N;
@@ -861,11 +872,11 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
   if constexpr (sizeof(T) == 4) {
     if (c->ace_tc) {
       k_ace_embed_split<<<eblocks, 256, 0, c->stream>>>(N, c->h, net.per_site, net.embed, occ, total, a,
-                                                        a + total);
+                                                        a + total, vcfg);
       split = true;
     }
   }
-  if (!split) k_ace_embed<T><<<eblocks, 256, 0, c->stream>>>(N, c->h, net.per_site, net.embed, occ, total, a);
+  if (!split) k_ace_embed<T><<<eblocks, 256, 0, c->stream>>>(N, c->h, net.per_site, net.embed, occ, total, a, vcfg);
   size_t frag_off = 0;
   for (int l = 0; l < c->L; ++l) {
     const bool conv = l < net.n_conv;
@@ -877,7 +888,8 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
         float* olo = (l + 1 < c->L && tc_layer(c, l + 1)) ? b + tout : nullptr;
         const cudaError_t e =
             launch_conv_tc(c, net.ln_g[l] != nullptr, net.cin[l], net.cout[l], c->arch.residual[l], net.ks[l], bimg,
-                           net.bias[l], net.ln_g[l], net.ln_b[l], net.act, (float)net.eps, a, a + tin, b, olo, rows);
+                           net.bias[l], net.ln_g[l], net.ln_b[l], net.act, (float)net.eps, a, a + tin, b, olo, rows,
+                           vcfg);
         if (e != cudaSuccess) return e;
         split = olo != nullptr;
         done = true;
@@ -886,14 +898,14 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
         const WFrag* frag = (const WFrag*)((const char*)c->ace_frag + frag_off);
         done = launch_mma_layer(c->stream, c->lat, p, net.ln_g[l] != nullptr, frag, net.bias[l], net.ln_g[l],
                                 net.ln_b[l], net.ks[l], net.stencil, net.cin[l], c->arch.residual[l], net.act,
-                                (float)net.eps, a, b, rows);
+                                (float)net.eps, a, b, rows, vcfg);
       }
     }
     if (!done) {
       const long long blocks = (rows + kAceRowsGeneric - 1) / kAceRowsGeneric;
       k_ace_layer<T><<<(unsigned)blocks, 32 * kAceRowsGeneric, 0, c->stream>>>(
           c->lat, net.kernel[l], net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l], net.stencil, net.cin[l],
-          net.cout[l], c->arch.residual[l], net.act, net.eps, a, b, rows);
+          net.cout[l], c->arch.residual[l], net.act, net.eps, a, b, rows, vcfg);
     }
     frag_off += frag_layer_bytes(c->arch, l);
     cudaError_t e = cudaGetLastError();
@@ -905,7 +917,7 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64)
   const dim3 pgrid((c->sys.n_up + kPhiT - 1) / kPhiT + (c->sys.n_dn + kPhiT - 1) / kPhiT, (Ne + kPhiT - 1) / kPhiT, C);
   cudaError_t e = cudaFuncSetAttribute(k_ace_phi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * 2 * N));
   if (e != cudaSuccess) return e;
-  k_ace_phi<T><<<pgrid, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, a, c->ace_err, phi64);
+  k_ace_phi<T><<<pgrid, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, a, c->ace_err, phi64, vcfg);
   return cudaGetLastError();
 }
 
@@ -964,11 +976,12 @@ cudaError_t launch_ace_build(scale_ctx* c) {
 }
 
 // Slater matrices (FP64) of C configurations occ[C][N] through the ACE network; the
-// activations go to the context's scratch buffers.
-cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64) {
+// activations go to the context's scratch buffers. vcfg (optional, device): only the first
+// *vcfg configurations are evaluated (the rest of the launch returns at once).
+cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg) {
   if (C <= 0) return cudaSuccess;
-  if (c->fp64) return ace_forward_t<double>(c, occ, C, phi64);
-  return ace_forward_t<float>(c, occ, C, phi64);
+  if (c->fp64) return ace_forward_t<double>(c, occ, C, phi64, vcfg);
+  return ace_forward_t<float>(c, occ, C, phi64, vcfg);
 }
 
 }  // namespace scale

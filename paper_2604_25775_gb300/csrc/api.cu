@@ -113,7 +113,15 @@ std::vector<int32_t> make_bonds(const Lattice& lat, int* nb_nn, int* nb_nnn) {
 struct Sizes {
   size_t T, total;
   int cap;
+  int full_chunk;  // configurations per full-recompute chunk
+  size_t fc;       // entries of the chunk-sized scratch: max(max_batch, full_chunk)
 };
+
+// The full-recompute path evaluates its configurations in chunks whose scratch (FP64 Slater
+// matrix, two activation buffers, packed occupations) stays within about 1 GiB, at most 4096
+// configurations: enough determinant CTAs to fill every SM whatever the context's batch.
+constexpr size_t kFullChunkBytes = size_t(1) << 30;
+constexpr int kFullChunkMax = 4096;
 
 Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   Sizes z{};
@@ -128,6 +136,10 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   // ACE / wide activations: the widest layer, in mixed precision as (hi, lo) halves
   // (tensor-core layers keep their rows split between them)
   const size_t hmax = ace ? (T == 4 ? 2 : 1) * std::max<size_t>(h, (size_t)ace_width_out(*a, a->n_layers - 1)) : h;
+  const size_t per_cfg = Ne * Ne * 8 + 2 * N * hmax * T + N + 4 * 4;
+  z.full_chunk = (int)std::max<size_t>(1, std::min<size_t>(kFullChunkMax, kFullChunkBytes / per_cfg));
+  z.fc = std::max<size_t>((size_t)B, (size_t)z.full_chunk);
+  const size_t FC = z.fc;
   size_t t = 0;
   t += P * 8 + (T == 4 ? P * 4 : 0);
   t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0) + 2 * N * Ne * T;
@@ -135,15 +147,16 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   t += (nb_nn + nb_nnn) * 2 * 4;
   t += (size_t)B * (N + Ne * 4 + 2 * N * 4);
   t += ace ? 32 : (size_t)B * N * h * T * 2;  // z0, HL
-  t += (size_t)B * N * hmax * T * 2;          // act_a, act_b
+  t += FC * N * hmax * T * 2;                 // act_a, act_b
   t += ace ? 16 : (size_t)B * Ne * Ne * T;    // Binv
   t += ace ? 16 : (size_t)B * 2 * Ne * h * T; // Pt
   t += (size_t)B * (8 + 4 + 4 + 4 + 8 + 4 + 4 + 8 + 4 + 8);
-  t += (size_t)B * Ne * Ne * 8;            // Phi64
+  t += FC * Ne * Ne * 8;                   // Phi64
   t += ace ? 16 : (size_t)B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T;  // commit scratch
   if (ace && T == 4) t += ace_frag_bytes(*a);
-  t += (size_t)B * (N + 4 + 8 + 4);        // full-path chunk
-  t += (size_t)B * z.cap * (8 + 8 + 16);   // full-path coefficients, terms, moves
+  t += FC * (N + 4 + 8 + 4 + 4);          // full-path chunk: occupations, owner, log|psi|, sign, list
+  t += (size_t)B * z.cap * (8 + 16);       // full-path coefficients, moves
+  t += (size_t)B * (z.cap + 1) * (8 + 4);  // full-path log|psi| and sign of every entry
   t += (size_t)(B + 1) * 8 + 64;
   z.total = t;
   return z;
@@ -178,7 +191,8 @@ void free_all(scale_ctx* c) {
   void* ptrs[] = {c->params64, c->params32, c->M0_64, c->M0_32, c->M0b, c->KE, c->bonds, c->occ, c->orb_of_slot,
                   c->slot_of_orb, c->z0, c->HL, c->Binv, c->Pt, c->logabs, c->sign_slot, c->status,
                   c->commits, c->drift, c->Phi64, c->act_a, c->act_b, c->list, c->list_count, c->stat_dev,
-                  c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_terms, c->full_moves,
+                  c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_la_all, c->full_sg_all,
+                  c->full_list, c->full_vcount, c->full_moves,
                   c->commit_scratch, c->la_tmp, c->sg_tmp, c->full_la, c->full_sg, c->full_diag,
                   c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag, c->ace_err};
   for (void* p : ptrs)
@@ -281,8 +295,9 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   c->ace_tc = c->ace_mma && ace_tc_shapes(*arch);
   std::vector<int32_t> bonds = make_bonds(c->lat, &c->nb_nn, &c->nb_nnn);
   c->max_moves = 2 * (c->nb_nn + c->nb_nnn) + (sys->model == SCALE_MODEL_TJ ? c->nb_nn : 0);
-  c->full_chunk = max_batch;
+  c->full_chunk = sz.full_chunk;
   const size_t B = max_batch, N = c->N, Ne = c->Ne, h = c->h, T = c->fp64 ? 8 : 4;
+  const size_t FC = sz.fc;
   const size_t Ns = arch->per_site_embed ? N : 1;
   const size_t cap = std::max(1, c->max_moves);
   cudaError_t e = cudaSuccess;
@@ -310,9 +325,9 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A(&c->status, B * 4);
   A(&c->commits, B * 4);
   A(&c->drift, B * 8);
-  A(&c->Phi64, B * Ne * Ne * 8);
-  A((char**)&c->act_a, B * N * hmax * T);
-  A((char**)&c->act_b, B * N * hmax * T);
+  A(&c->Phi64, FC * Ne * Ne * 8);
+  A((char**)&c->act_a, FC * N * hmax * T);
+  A((char**)&c->act_b, FC * N * hmax * T);
   A(&c->list, B * 4);
   A(&c->list_count, 16);
   A(&c->stat_dev, 4 * 8);
@@ -320,15 +335,18 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A((char**)&c->commit_scratch, ace ? 16 : B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T);
   A(&c->la_tmp, B * 8);
   A(&c->sg_tmp, B * 4);
-  A(&c->full_occ, B * N);
-  A(&c->full_owner, B * 4);
-  A(&c->full_la, B * 8);
-  A(&c->full_sg, B * 4);
+  A(&c->full_occ, FC * N);
+  A(&c->full_owner, FC * 4);
+  A(&c->full_list, FC * 4);
+  A(&c->full_vcount, 16);
+  A(&c->full_la, FC * 8);
+  A(&c->full_sg, FC * 4);
   A(&c->full_diag, B * 8);
   A(&c->full_offsets, (B + 1) * 8);
   A(&c->full_coeff, B * cap * 8);
-  A(&c->full_terms, B * cap * 8);
   A(&c->full_moves, B * cap * 16);
+  A(&c->full_la_all, B * (cap + 1) * 8);
+  A(&c->full_sg_all, B * (cap + 1) * 4);
   if (c->use_mma) A((char**)&c->wfrag, (size_t)c->L * (c->hpad / 8) * (c->hpad / 8) * 32 * 16);
   if (c->ace_mma) A((char**)&c->ace_frag, ace_frag_bytes(*arch));
   if (c->ace) A(&c->ace_err, 16);
@@ -350,6 +368,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
     return SCALE_ECUDA;
   }
   c->stats.max_moves = c->max_moves;
+  c->stats.full_chunk = c->full_chunk;
   *out = c;
   return SCALE_OK;
 }

@@ -590,12 +590,4 @@ cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32
   return run_gj<double, double, false, 8, 256>(c->stream, A, n, B, list, (double*)nullptr, logabs, sign, status);
 }
 
-// Determinant only, FP32 working precision (full-recompute path in mixed mode).
-cudaError_t launch_det_f32(scale_ctx* c, float* mats, int n, int B, double* logabs, int32_t* sign) {
-  if (B <= 0) return cudaSuccess;
-  if (n > 448) return run_gj<float, float, false, 8, 512>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
-  if (B < 4 * 152) return run_gj<float, float, false, 16>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
-  return run_gj<float, float, false, 16, 256>(c->stream, mats, n, B, nullptr, (float*)nullptr, logabs, sign, nullptr);
-}
-
 }  // namespace scale

@@ -135,12 +135,24 @@ __global__ void k_slots(Lattice lat, const int8_t* __restrict__ occ, const int32
   }
 }
 
+// The orbital projection in FP64 (weights, bias and reference orbitals of the FP64 parameter
+// copy): the Slater matrix entries are formed in FP64 from the features of either mode.
+struct Proj64 {
+  int h;
+  const double* proj_w;  // [h][2Ne]
+  const double* proj_b;  // [2Ne]
+  const double* M0;      // [2N][Ne]
+};
+
 // Slater matrix in ascending orbital order (Sec. II.B "Orbital Projection"):
 //   Phi[a][k] = M0[o_a][k] + proj_b[s*Ne+k] + sum_c H(L)_i[c] proj_w[c][s*Ne+k],
-// o_a = s*N + i the a-th occupied orbital. Computed in T, stored as TO.
-template <typename T, typename TO>
-__global__ void k_phi(Lattice lat, Net<T> net, const int8_t* __restrict__ occ, const int32_t* __restrict__ list,
-                      const T* __restrict__ HL, TO* __restrict__ phi, int B, const int32_t* __restrict__ count) {
+// o_a = s*N + i the a-th occupied orbital, in FP64 from features H(L) of type TH (mixed mode:
+// the FP32 network output). The full-recompute path divides two such determinants, so an
+// FP32 rounding of the entries would not cancel in the ratio as the low-rank update's
+// differences do.
+template <typename TH>
+__global__ void k_phi(Lattice lat, Proj64 net, const int8_t* __restrict__ occ, const int32_t* __restrict__ list,
+                      const TH* __restrict__ HL, double* __restrict__ phi, int B, const int32_t* __restrict__ count) {
   extern __shared__ int sm[];
   const int nrows = count ? min(*count, B) : B;
   for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
@@ -151,20 +163,20 @@ __global__ void k_phi(Lattice lat, Net<T> net, const int8_t* __restrict__ occ, c
   int* olist = sm;
   int* tmp = sm + 2 * N;
   const int n = occupied_list(occ + (size_t)b * N, N, olist, tmp);
-  TO* P = phi + (size_t)b * Ne * Ne;
+  double* P = phi + (size_t)b * Ne * Ne;
   if (n != Ne) {  // invalid sample: leave a zero matrix (singular)
-    for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = TO(0);
+    for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) P[q] = 0.0;
     continue;
   }
-  const T* Hb = HL + (size_t)b * N * h;
+  const TH* Hb = HL + (size_t)b * N * h;
   for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) {
     const int a = q / Ne, k = q - a * Ne;
     const int o = olist[a], s = o / N, i = o - s * N;
-    T v = net.M0[(size_t)o * Ne + k] + net.proj_b[s * Ne + k];
-    const T* w = net.proj_w + s * Ne + k;
-    const T* x = Hb + (size_t)i * h;
-    for (int c = 0; c < h; ++c) v += x[c] * w[(size_t)c * 2 * Ne];
-    P[q] = (TO)v;
+    double v = net.M0[(size_t)o * Ne + k] + net.proj_b[s * Ne + k];
+    const double* w = net.proj_w + s * Ne + k;
+    const TH* x = Hb + (size_t)i * h;
+    for (int c = 0; c < h; ++c) v += (double)x[c] * w[(size_t)c * 2 * Ne];
+    P[q] = v;
   }
   }
 }
@@ -356,7 +368,7 @@ template Net<float> make_net<float>(scale_ctx*);
 namespace {
 template <typename T>
 cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, bool keep_cache,
-                      double* phi_out, void* phi_f32, const int32_t* count) {
+                      double* phi_out, const int32_t* count) {
   const Net<T> net = make_net<T>(c);
   const int N = c->N, h = c->h;
   // with a compacted list (count on the device) the kernels loop over its entries from a
@@ -394,10 +406,12 @@ cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* lis
   }
   const size_t smem = sizeof(int) * (2 * N + 257);
   const int Bphi = count ? std::min(B, 1024) : B;
-  if (phi_out)
-    k_phi<T, double><<<Bphi, 256, smem, c->stream>>>(c->lat, net, occ, list, in, phi_out, B, count);
-  if (phi_f32)
-    k_phi<T, float><<<Bphi, 256, smem, c->stream>>>(c->lat, net, occ, list, in, (float*)phi_f32, B, count);
+  if (phi_out) {
+    // FP64 projection parameters: the flat FP64 vector at the offsets of make_net
+    const int64_t off_w = (const T*)net.proj_w - (c->fp64 ? (const T*)c->params64 : (const T*)c->params32);
+    const Proj64 p64{c->h, c->params64 + off_w, c->params64 + off_w + (int64_t)c->h * 2 * c->Ne, c->M0_64};
+    k_phi<T><<<Bphi, 256, smem, c->stream>>>(c->lat, p64, occ, list, in, phi_out, B, count);
+  }
   return cudaGetLastError();
 }
 }  // namespace
@@ -407,18 +421,21 @@ cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t
                            double* phi_out, const int32_t* count) {
   if (c->ace) {  // ACE: no cached features; whole batches only (no list)
     if (list || count || !phi_out) return cudaErrorInvalidValue;
-    return launch_ace_forward(c, occ, B, phi_out);
+    return launch_ace_forward(c, occ, B, phi_out, nullptr);
   }
-  if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, nullptr, count);
-  return forward_t<float>(c, occ, B, list, keep_cache, phi_out, nullptr, count);
+  if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, count);
+  return forward_t<float>(c, occ, B, list, keep_cache, phi_out, count);
 }
 
-// Forward for the full-recompute path: Slater matrices of B configurations into phi
-// (double in FP64 mode, float in mixed mode); features go to the scratch buffers.
-cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, void* phi) {
-  if (c->ace) return launch_ace_forward(c, occ, B, (double*)phi);  // FP64 Slater matrices
-  if (c->fp64) return forward_t<double>(c, occ, B, nullptr, false, (double*)phi, nullptr, nullptr);
-  return forward_t<float>(c, occ, B, nullptr, false, nullptr, phi, nullptr);
+// Forward for the full-recompute path: FP64 Slater matrices of B packed configurations into
+// phi [B][Ne][Ne] (the network in the mode's precision); features go to the scratch buffers.
+// Entries with list[g] < 0 are skipped (SCALE family); the ACE and wide networks evaluate
+// the first *vcount configurations (the valid entries of a chunk form a prefix).
+cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, const int32_t* vcount,
+                               double* phi) {
+  if (c->ace) return launch_ace_forward(c, occ, B, phi, vcount);
+  if (c->fp64) return forward_t<double>(c, occ, B, list, false, phi, nullptr);
+  return forward_t<float>(c, occ, B, list, false, phi, nullptr);
 }
 
 cudaError_t launch_slots(scale_ctx* c, const int8_t* occ, int B) {

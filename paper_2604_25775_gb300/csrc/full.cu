@@ -1,14 +1,26 @@
-// full.cu -- the full-recompute comparison path (Sec. III.A): every connected amplitude
-// psi(n') by a fresh network forward and a fresh LU of Phi(n'), the O(N^4) route that the
-// low-rank update replaces. Same enumeration order as the low-rank path.
+// full.cu -- the full-recompute comparison path (Sec. III.A): psi(n) and every connected
+// amplitude psi(n') by a fresh network forward and a fresh LU of the Slater matrix, the
+// O(N^4) route that the low-rank update replaces. Same enumeration order as the low-rank
+// path. Nothing cached by the context enters the result: psi(n) is recomputed alongside its
+// connected configurations.
 //
 // Matrix elements here are in the ascending-orbital convention, with the Jordan-Wigner
 // signs explicit:
 //   hop      c+_{dst,s} c_{src,s}:  -t (-1)^(occupied orbitals strictly between)
 //   exchange (J/2) S+_i S-_j = -(J/2)(c+_{i up} c_{j up})(c+_{j dn} c_{i dn}):
 //            -(J/2) (-1)^(k_up + k_dn), k_s = occupied spin-s orbitals strictly between.
+//
+// Precision: the network and the Slater matrix in the mode's precision (as at load), every
+// determinant by the FP64 LU with partial pivoting. An FP32 LU of a 224 x 224 Slater matrix
+// would carry cond(Phi) x 2^-24 relative error in each amplitude, far above the mixed-mode
+// tolerance on the ill-conditioned matrices of random configurations.
+//
+// Scheduling: every call is asynchronous. Sample b owns count[b] + 1 entries (entry 0 is n
+// itself, entry m >= 1 its (m-1)-th connected configuration); a device-side exclusive scan
+// gives their global offsets, and the host walks the entries in fixed-size chunks up to the
+// capacity B * (max_moves + 1). Chunk positions past the device-side total are marked -1 in
+// the chunk's list, and every kernel of the chunk skips them, so the host never reads a count.
 #include <algorithm>
-#include <vector>
 
 #include "scale_internal.cuh"
 
@@ -89,14 +101,53 @@ __global__ void k_enum(Lattice lat, const int8_t* __restrict__ occ, const int32_
   count[b] = min(n, cap);
 }
 
-// Packed configurations n' for global indices [g0, g0 + G): owner sample by binary search
-// over the offsets.
+// offsets[b] = sum_{b' < b} (count[b'] + 1), offsets[B] = the total: one CTA, each thread
+// scans a contiguous run of samples, then a scan over the threads' sums.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_offsets(int B, const int32_t* __restrict__ count,
+                                                          int64_t* __restrict__ offsets) {
+  __shared__ int64_t part[kScanThreads + 1];
+  const int tid = threadIdx.x;
+  const int per = (B + kScanThreads - 1) / kScanThreads;
+  const int b0 = min(B, tid * per), b1 = min(B, b0 + per);
+  int64_t s = 0;
+  for (int b = b0; b < b1; ++b) s += (int64_t)count[b] + 1;
+  part[tid] = s;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the 1024 partial sums
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    const int64_t v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int64_t run = part[tid] - s;  // exclusive prefix of this thread's run
+  for (int b = b0; b < b1; ++b) {
+    offsets[b] = run;
+    run += (int64_t)count[b] + 1;
+  }
+  if (tid == kScanThreads - 1) offsets[B] = part[tid];
+}
+
+// Chunk entries [g0, g0 + G): the owning sample by binary search over the offsets, its
+// configuration (entry 0: n itself; entry m: n with move m-1 applied) packed into xp[g],
+// owner[g] = b * (cap + 1) + m and list[g] = g; positions past the total get list[g] = -1.
+// *vcount = the number of valid positions (a prefix of the chunk).
 __global__ void k_build_xprime(int N, int B, int cap, const int8_t* __restrict__ occ,
                                const int32_t* __restrict__ moves, const int64_t* __restrict__ offsets, int64_t g0,
-                               int G, int8_t* __restrict__ xp, int32_t* __restrict__ owner) {
+                               int G, int8_t* __restrict__ xp, int32_t* __restrict__ owner,
+                               int32_t* __restrict__ list, int32_t* __restrict__ vcount) {
   const int g = blockIdx.x;
   if (g >= G) return;
+  if (g == 0 && threadIdx.x == 0) *vcount = (int32_t)max((int64_t)0, min((int64_t)G, offsets[B] - g0));
   const int64_t gg = g0 + g;
+  if (gg >= offsets[B]) {
+    if (threadIdx.x == 0) {
+      list[g] = -1;
+      owner[g] = -1;
+    }
+    return;
+  }
   int lo = 0, hi = B;  // offsets[lo] <= gg < offsets[lo+1]
   while (hi - lo > 1) {
     const int mid = (lo + hi) / 2;
@@ -104,44 +155,62 @@ __global__ void k_build_xprime(int N, int B, int cap, const int8_t* __restrict__
   }
   const int b = lo;
   const int m = (int)(gg - offsets[b]);
-  const int32_t* mv = moves + ((size_t)b * cap + m) * 4;
   const int8_t* x = occ + (size_t)b * N;
   int8_t* y = xp + (size_t)g * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) y[i] = x[i];
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int src = mv[1], dst = mv[2], s = mv[3];
-    if (mv[0] == 0) {
-      y[src] = (int8_t)(x[src] & ~(1 << s));
-      y[dst] = (int8_t)(x[dst] | (1 << s));
-    } else {
-      y[src] = x[dst];
-      y[dst] = x[src];
+    if (m > 0) {
+      const int32_t* mv = moves + ((size_t)b * cap + (m - 1)) * 4;
+      const int src = mv[1], dst = mv[2], s = mv[3];
+      if (mv[0] == 0) {
+        y[src] = (int8_t)(x[src] & ~(1 << s));
+        y[dst] = (int8_t)(x[dst] | (1 << s));
+      } else {
+        y[src] = x[dst];
+        y[dst] = x[src];
+      }
     }
-    owner[g] = b * cap + m;
+    owner[g] = b * (cap + 1) + m;
+    list[g] = g;
   }
 }
 
-// term[b][m] = coeff * psi(n')/psi(n) from the two log-determinants.
-__global__ void k_terms(int G, int cap, const int32_t* __restrict__ owner, const double* __restrict__ coeff,
-                        const double* __restrict__ la_x, const int32_t* __restrict__ sg_x,
-                        const double* __restrict__ la_p, const int32_t* __restrict__ sg_p,
-                        double* __restrict__ terms) {
+// Scatter the chunk's determinants to their entries: la_all / sg_all [B][cap + 1].
+__global__ void k_scatter_dets(int G, const int32_t* __restrict__ owner, const double* __restrict__ la,
+                               const int32_t* __restrict__ sg, double* __restrict__ la_all,
+                               int32_t* __restrict__ sg_all) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
   const int idx = owner[g];
-  const int b = idx / cap;
-  double v = 0.0;
-  if (sg_p[g] != 0 && sg_x[b] != 0) v = coeff[idx] * (double)(sg_p[g] * sg_x[b]) * exp(la_p[g] - la_x[b]);
-  terms[idx] = v;
+  if (idx < 0) return;
+  la_all[idx] = la[g];
+  sg_all[idx] = sg[g];
 }
 
+// E_loc[b] = diag + sum_m coeff[m] psi(n'_m)/psi(n), fixed order; psi(n) = 0 gives NaN.
 __global__ void k_reduce_terms(int B, int cap, const int32_t* __restrict__ count, const double* __restrict__ diag,
-                               const double* __restrict__ terms, double* __restrict__ eloc) {
+                               const double* __restrict__ coeff, const double* __restrict__ la_all,
+                               const int32_t* __restrict__ sg_all, double* __restrict__ eloc) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  const size_t base = (size_t)b * (cap + 1);
+  const int n = count[b];
   double e = diag[b];
-  for (int m = 0; m < count[b]; ++m) e += terms[(size_t)b * cap + m];
+  if (isnan(e)) {  // invalid sample (status): no entries were evaluated
+    eloc[b] = e;
+    return;
+  }
+  const double la0 = la_all[base];
+  const int sg0 = sg_all[base];
+  if (sg0 == 0) {
+    eloc[b] = CUDART_NAN;
+    return;
+  }
+  for (int m = 0; m < n; ++m) {
+    const int sg = sg_all[base + 1 + m];
+    if (sg != 0) e += coeff[(size_t)b * cap + m] * (double)(sg * sg0) * exp(la_all[base + 1 + m] - la0);
+  }
   eloc[b] = e;
 }
 
@@ -153,36 +222,25 @@ cudaError_t launch_eloc_full(scale_ctx* c, double* eloc) {
   k_enum<<<B, 32, 0, c->stream>>>(c->lat, c->occ, c->bonds, c->nb_nn, c->nb_nnn, c->status, cap, c->full_moves,
                                   c->full_coeff, c->move_count, c->full_diag);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // log|psi(n)| and sign in the ascending convention
-  if ((e = launch_logpsi_out(c, c->la_tmp, c->sg_tmp)) != cudaSuccess) return e;
-  std::vector<int32_t> cnt(B);
-  if ((e = cudaMemcpyAsync(cnt.data(), c->move_count, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, c->stream)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
-  std::vector<int64_t> off(B + 1, 0);
-  for (int b = 0; b < B; ++b) off[b + 1] = off[b] + cnt[b];
-  if ((e = cudaMemcpyAsync(c->full_offsets, off.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice,
-                           c->stream)) != cudaSuccess)
-    return e;
-  const int64_t total = off[B];
+  k_offsets<<<1, kScanThreads, 0, c->stream>>>(B, c->move_count, c->full_offsets);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int64_t bound = (int64_t)B * (cap + 1);  // the device-side total is at most this
   const int chunk = c->full_chunk;
-  for (int64_t g0 = 0; g0 < total; g0 += chunk) {
-    const int G = (int)std::min<int64_t>(chunk, total - g0);
+  for (int64_t g0 = 0; g0 < bound; g0 += chunk) {
+    const int G = (int)std::min<int64_t>(chunk, bound - g0);
     k_build_xprime<<<G, 128, 0, c->stream>>>(N, B, cap, c->occ, c->full_moves, c->full_offsets, g0, G, c->full_occ,
-                                            c->full_owner);
+                                            c->full_owner, c->full_list, c->full_vcount);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_forward_phi(c, c->full_occ, G, c->Phi64)) != cudaSuccess) return e;
-    if (c->fp64 || c->ace)  // ACE: FP64 determinants in both modes
-      e = launch_gj(c, c->Phi64, Ne, G, nullptr, false, true, nullptr, c->full_la, c->full_sg, nullptr);
-    else
-      e = launch_det_f32(c, reinterpret_cast<float*>(c->Phi64), Ne, G, c->full_la, c->full_sg);
-    if (e != cudaSuccess) return e;
-    k_terms<<<(G + 255) / 256, 256, 0, c->stream>>>(G, cap, c->full_owner, c->full_coeff, c->la_tmp, c->sg_tmp,
-                                                    c->full_la, c->full_sg, c->full_terms);
+    if ((e = launch_forward_phi(c, c->full_occ, G, c->full_list, c->full_vcount, c->Phi64)) != cudaSuccess) return e;
+    if ((e = launch_gj(c, c->Phi64, Ne, G, c->full_list, false, true, nullptr, c->full_la, c->full_sg, nullptr)) !=
+        cudaSuccess)
+      return e;
+    k_scatter_dets<<<(G + 255) / 256, 256, 0, c->stream>>>(G, c->full_owner, c->full_la, c->full_sg, c->full_la_all,
+                                                           c->full_sg_all);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_reduce_terms<<<(B + 255) / 256, 256, 0, c->stream>>>(B, cap, c->move_count, c->full_diag, c->full_terms, eloc);
+  k_reduce_terms<<<(B + 255) / 256, 256, 0, c->stream>>>(B, cap, c->move_count, c->full_diag, c->full_coeff,
+                                                         c->full_la_all, c->full_sg_all, eloc);
   return cudaGetLastError();
 }
 

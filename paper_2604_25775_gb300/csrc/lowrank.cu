@@ -1,11 +1,11 @@
 // lowrank.cu -- local energies and amplitude ratios by the cached-network + rank-r
 // determinant update of Sec. II.C, and the projector P_s = W_s Phi^-1 it relies on.
 //
-// One CTA per sample. Connected configurations are enumerated on the device in a fixed
-// order (NN bonds, then NNN bonds, each with spin up then down; then t-J exchanges on NN
-// bonds), compacted chunk by chunk, and handed to the warps (one move per warp at a time,
-// move.cuh). Per-move contributions are summed in enumeration order, so E_loc does not
-// depend on scheduling.
+// One CTA per sample. Connected configurations are enumerated on the device in the fixed
+// order of eloc_common.cuh, compacted chunk by chunk, and handed to the warps (one move per
+// warp at a time, move.cuh). Per-move contributions are summed in enumeration order, so E_loc
+// does not depend on scheduling. (Mixed precision at the tensor-core widths runs the batched
+// kernel of eloc_tc.cu instead.)
 //
 // Matrix elements in slot order (a moved electron keeps its determinant row):
 //   hop     -t (NN) / -t' (NNN) times det R   (its Jordan-Wigner sign and the row
@@ -16,78 +16,13 @@
 // particle-hole transformed Hubbard model U sum_i n_up (1 - n_dn).
 #include <algorithm>
 
-#include "move.cuh"
+#include "eloc_common.cuh"
 
 namespace scale {
 
 namespace {
 
 constexpr int kWarps = 8;
-
-struct MoveDesc {
-  int kind, src, dst, spin;
-};
-
-struct LowrankArgs {
-  Lattice lat;
-  int k0;
-  const int8_t* occ;
-  const int32_t* slot_of_orb;
-  const void* z0;
-  const void* HL;
-  const void* Binv;
-  const void* Pt;
-  const int32_t* bonds;
-  int nb_nn, nb_nnn;
-  const int32_t* status;
-  double* out;           // eloc [B] or ratio [B][M]
-  int32_t* move_count;   // [B] (eloc only)
-  const int32_t* moves;  // explicit moves [B][M][4] (ratios only)
-  int M;
-  MlpFrags mf;
-  const int32_t* list;   // optional: CTA i handles sample list[i]
-};
-
-// Candidate id -> move (kind -1 when not allowed in the current configuration) and its
-// coefficient class: 0 NN hop (-t), 1 NNN hop (-t'), 2 exchange (-J/2).
-__device__ __forceinline__ MoveDesc candidate(const LowrankArgs& a, const int8_t* occ, int id, int* cls) {
-  MoveDesc m{-1, 0, 0, 0};
-  const int nb = a.nb_nn + a.nb_nnn;
-  if (id < 2 * nb) {
-    const int q = id >> 1, s = id & 1;
-    const int i = a.bonds[2 * q], j = a.bonds[2 * q + 1];
-    const int oi = occ[i], oj = occ[j];
-    const bool hi = (oi >> s) & 1, hj = (oj >> s) & 1;
-    if (hi == hj) return m;
-    const int src = hi ? i : j, dst = hi ? j : i;
-    if (a.lat.model == SCALE_MODEL_TJ && occ[dst] != 0) return m;
-    m.kind = 0;
-    m.src = src;
-    m.dst = dst;
-    m.spin = s;
-    *cls = (q < a.nb_nn) ? 0 : 1;
-    return m;
-  }
-  const int q = id - 2 * nb;
-  const int i = a.bonds[2 * q], j = a.bonds[2 * q + 1];
-  const int oi = occ[i], oj = occ[j];
-  if ((oi == 1 && oj == 2) || (oi == 2 && oj == 1)) {
-    m.kind = 1;
-    m.src = i;
-    m.dst = j;
-    m.spin = 0;
-    *cls = 2;
-  }
-  return m;
-}
-
-// Moves of one chunk are kept packed in shared memory: bits 0-11 src, 12-23 dst (N <= 4096),
-// 24 spin, 25 kind, 26-27 coefficient class.
-constexpr int kMoveChunk = 1024;
-__device__ __forceinline__ uint32_t pack_move(const MoveDesc& m, int cls) {
-  return (uint32_t)m.src | ((uint32_t)m.dst << 12) | ((uint32_t)m.spin << 24) | ((uint32_t)m.kind << 25) |
-         ((uint32_t)cls << 26);
-}
 
 // WARPS warps per sample; the sample's cached rows (Binv, Pt, z0, H(L)) are read through
 // L1/L2, shared memory holds the per-warp move scratch and the move list.
@@ -117,26 +52,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net) 
   for (int i = tid; i < N; i += blockDim.x) occ_s[i] = a.occ[(size_t)b * N + i];
   for (int o = tid; o < 2 * N; o += blockDim.x) slot_s[o] = a.slot_of_orb[(size_t)b * 2 * N + o];
   __syncthreads();
-  if (tid == 0) {
-    double d = 0.0;
-    if (a.lat.model == SCALE_MODEL_HUBBARD) {
-      int nd = 0;
-      for (int i = 0; i < N; ++i) nd += occ_s[i] == 3;
-      d = a.lat.U * nd;
-    } else if (a.lat.model == SCALE_MODEL_HUBBARD_PH) {
-      int nu = 0;  // sites with an up particle and no (transformed) down particle
-      for (int i = 0; i < N; ++i) nu += occ_s[i] == 1;
-      d = a.lat.U * nu;
-    } else {
-      for (int q = 0; q < a.nb_nn; ++q) {
-        const int i = a.bonds[2 * q], j = a.bonds[2 * q + 1];
-        const double szi = 0.5 * ((occ_s[i] & 1) - ((occ_s[i] >> 1) & 1));
-        const double szj = 0.5 * ((occ_s[j] & 1) - ((occ_s[j] >> 1) & 1));
-        d += a.lat.J * szi * szj;
-      }
-    }
-    s_diag = d;
-  }
+  if (tid == 0) s_diag = diag_energy(a, occ_s);
   SampleView<T> sv;
   sv.occ = occ_s;
   sv.slot_of_orb = slot_s;
@@ -146,32 +62,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net) 
   sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
   MoveScratch<T, H>& ms = ms_all[warp];
 
-  const int nb = a.nb_nn + a.nb_nnn;
-  const int ncand = 2 * nb + ((a.lat.model == SCALE_MODEL_TJ && a.lat.J != 0.0) ? a.nb_nn : 0);
+  const int ncand = candidate_count(a);
   double total = 0.0;  // thread 0
   int nmoves = 0;
   for (int cs = 0; cs < ncand; cs += kMoveChunk) {
     const int ce = min(ncand, cs + kMoveChunk);
     // enumerate and compact the allowed moves of this chunk (enumeration order)
-    int nm = 0;
-    for (int sub = cs; sub < ce; sub += WARPS * 32) {
-      const int id = sub + tid;
-      int cls = 0;
-      MoveDesc m{-1, 0, 0, 0};
-      if (id < ce) m = candidate(a, occ_s, id, &cls);
-      const bool valid = m.kind >= 0;
-      const unsigned bal = __ballot_sync(0xffffffffu, valid);
-      if (lane == 0) warp_cnt[warp] = __popc(bal);
-      __syncthreads();
-      int off = 0, tot = 0;
-      for (int w = 0; w < WARPS; ++w) {
-        if (w < warp) off += warp_cnt[w];
-        tot += warp_cnt[w];
-      }
-      if (valid) mlist[nm + off + __popc(bal & ((1u << lane) - 1u))] = pack_move(m, cls);
-      nm += tot;
-      __syncthreads();
-    }
+    const int nm = enumerate_chunk<WARPS>(a, occ_s, cs, ce, mlist, warp_cnt);
     if (tid == 0) s_next = 0;
     __syncthreads();
     // warps take the next move as they finish the previous one
@@ -182,20 +79,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net) 
       if (mi >= nm) break;
       const uint32_t pm = mlist[mi];
       if (lane == 0) {
-        ms.src = (int)(pm & 0xfffu);
-        ms.dst = (int)((pm >> 12) & 0xfffu);
-        ms.spin = (int)((pm >> 24) & 1u);
-        ms.kind = (int)((pm >> 25) & 1u);
+        const MoveDesc m = unpack_move(pm);
+        ms.src = m.src;
+        ms.dst = m.dst;
+        ms.spin = m.spin;
+        ms.kind = m.kind;
       }
       __syncwarp();
       move_features<T, H>(a.lat, net, a.k0, sv, a.mf, ms);
       const int r = move_matrix<T, H>(a.lat, net, sv, ms);
       const T det = (r < 0) ? T(CUDART_NAN) : warp_det<T, H>(ms, r);
-      if (lane == 0) {
-        const uint32_t cls = (pm >> 26) & 3u;
-        const double cf = cls == 0 ? -a.lat.t : (cls == 1 ? -a.lat.tp : -0.5 * a.lat.J);
-        contrib[mi] = cf * (double)det;
-      }
+      if (lane == 0) contrib[mi] = move_coeff(a.lat, pm) * (double)det;
       __syncwarp();
     }
     __syncthreads();
@@ -348,24 +242,6 @@ size_t ratio_smem(int N) {
   return sizeof(MoveScratch<T, H>) * kWarps + sizeof(int32_t) * 2 * N + N + 16;
 }
 
-LowrankArgs make_args(scale_ctx* c) {
-  LowrankArgs a{};
-  a.lat = c->lat;
-  a.k0 = c->k0;
-  a.occ = c->occ;
-  a.slot_of_orb = c->slot_of_orb;
-  a.z0 = c->z0;
-  a.HL = c->HL;
-  a.Binv = c->Binv;
-  a.Pt = c->Pt;
-  a.bonds = c->bonds;
-  a.nb_nn = c->nb_nn;
-  a.nb_nnn = c->nb_nnn;
-  a.status = c->status;
-  a.mf.wf = c->use_mma ? (const WFrag*)c->wfrag : nullptr;
-  a.mf.kind = c->arch.precision == SCALE_PREC_MIXED_BF16 ? kBF16 : kTF32;
-  return a;
-}
 
 template <typename T, int H, int WARPS>
 cudaError_t eloc_launch(scale_ctx* c, const LowrankArgs& a, int n) {

@@ -5,7 +5,8 @@
 //      the later layers are site-wise, so S does not grow;
 //   3. new features on S: layer-0 pre-activation z0' = z0 + sum over (t, d) of
 //      KE[t][n'_t][d] - KE[t][n_t][d], then the residual / activation and the site-wise
-//      layers (BF16 tensor cores in mixed mode, FP64 FMA in FP64 mode);
+//      layers (tensor cores in mixed mode: three TF32 products of a hi/lo split by default,
+//      three BF16 products as an option; FP64 FMA in FP64 mode);
 //   4. the electrons on S after the move, each with its determinant row (slot) c_a and new
 //      orbital o'_a; the rank-r matrix of Eq. SMW with U = the changed rows,
 //        R[a][b] = M'[o'_a] . Binv[c_b]
@@ -56,7 +57,8 @@ struct SampleView {
   const T* Pt;                 // [2][Ne][h]
 };
 
-// Site-wise layer weights as BF16 hi/lo mma fragments (mixed mode); null in FP64 mode.
+// Site-wise layer weights as hi/lo mma fragments, TF32 or BF16 by `kind` (mixed mode); null
+// in FP64 mode.
 struct MlpFrags {
   const WFrag* wf;
   int kind;  // kTF32 or kBF16

@@ -16,9 +16,14 @@
 // Nothing in it needs to start at zero: every word a call reads was written earlier in the
 // same call.
 //
-// The device address of the array is looked up once per device, on the first call made
-// with that device current (cudaGetSymbolAddress); make that first call outside any stream
+// The device address of the array is looked up once per CUDA context: on the first call made
+// with a device current, and again on the first call after that device's context changed
+// (cudaDeviceReset, or a caller that made another context of the device current). The cache
+// is keyed on the context's process-unique ID, so an address from a destroyed context is never
+// reused. Make that first call on a device (and the first after a reset) outside any stream
 // capture.
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -33,7 +38,38 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;  // ID of the context the address belongs to
+  void* ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
+
+// ID of the current CUDA context (driver entry points fetched through the runtime, so the
+// library needs no link against the driver library). false when there is none yet or the
+// driver lacks the calls.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+bool current_ctx_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {  // under g_mu
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)f;
+  }
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -57,12 +93,18 @@ extern "C" scale_status scale_log_psi_noalloc(const scale_system* sys, const sca
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long id = 0;
+    bool known = current_ctx_id(&id);
+    if (!known || !g_scratch[dev].ptr || g_scratch[dev].ctx_id != id) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SCALE_ECUDA;
-      g_scratch_ptr[dev] = p;
+      if (!known) known = current_ctx_id(&id);  // the lookup made the device's context current
+      // without a context ID the address is looked up again on every call
+      g_scratch[dev] = known ? ScratchAddr{id, p} : ScratchAddr{0, nullptr};
+      base = (unsigned char*)p;
+    } else {
+      base = (unsigned char*)g_scratch[dev].ptr;
     }
-    base = (unsigned char*)g_scratch_ptr[dev];
   }
   // a host-side context whose device pointers all point into the static array or at the
   // caller's buffers
@@ -101,9 +143,10 @@ extern "C" scale_status scale_log_psi_noalloc(const scale_system* sys, const sca
   // per-sample part
   const size_t per = align256(N * h * T) * 2 + align256(Ne * Ne * 8) + align256(Ne * 4) + align256(2 * N * 4) +
                      align256(8) + 3 * align256(4);
-  if (off + per > kNoAllocBytes) return SCALE_EBUDGET;
   // nine per-sample buffers, each rounded up to 256 bytes once per chunk
+  if (off + per + 9 * 256 > kNoAllocBytes) return SCALE_EBUDGET;
   const int chunk = (int)std::min<size_t>((kNoAllocBytes - off - 9 * 256) / per, 65535);
+  if (chunk < 1) return SCALE_EBUDGET;
   if (!c.fp64) {
     k_convert_na<float, double><<<256, 256, 0, c.stream>>>(params, c.params32, (size_t)P);
     k_convert_na<float, double><<<256, 256, 0, c.stream>>>(M0, c.M0_32, 2 * N * Ne);

@@ -152,7 +152,7 @@ struct scale_ctx {
   bool lowrank_ok = false;  // SCALE layer layout (k_l = 1 for l >= 1)
   bool use_mma = false;     // mixed mode, SCALE layout, h in {16, 32, 64}: site-wise layers on tensor cores
   int hpad = 16;            // channel capacity of the per-warp scratch (16, 32 or 64)
-  void* wfrag = nullptr;    // BF16 hi/lo mma fragments of the site-wise layers
+  void* wfrag = nullptr;    // hi/lo mma fragments (TF32, or BF16 as an option) of the site-wise layers
   int64_t P = 0;
   int B_max = 0, B = 0;
   int max_moves = 0;
@@ -197,21 +197,25 @@ struct scale_ctx {
   void* commit_scratch = nullptr;  // [B][3*32*Ne + 2*32*kMaxH] T
   double* la_tmp = nullptr;     // [B] log|psi| scratch (ascending)
   int32_t* sg_tmp = nullptr;    // [B]
-  double* full_la = nullptr;    // [chunk]
-  int32_t* full_sg = nullptr;   // [chunk]
+  double* full_la = nullptr;    // [FC] chunk determinants (FC = max(max_batch, full_chunk))
+  int32_t* full_sg = nullptr;   // [FC]
   double* full_diag = nullptr;  // [B]
   int64_t* full_offsets = nullptr;  // [B+1] device copy of the packed offsets
   void* grad_scratch = nullptr;
   size_t grad_scratch_bytes = 0;
   int32_t* move_count = nullptr;  // [B] connected configurations last enumerated
 
-  // full-recompute path scratch
+  // full-recompute path scratch (a chunk is full_chunk configurations, sized from memory and
+  // not from max_batch; the chunk buffers hold FC = max(max_batch, full_chunk) entries)
   int full_chunk = 0;
-  int8_t* full_occ = nullptr;      // [chunk][N]
-  int32_t* full_owner = nullptr;   // [chunk]
-  double* full_coeff = nullptr;    // [chunk]
-  double* full_terms = nullptr;    // [B][max_moves]
+  int8_t* full_occ = nullptr;      // [FC][N]
+  int32_t* full_owner = nullptr;   // [FC] entry index b * (max_moves + 1) + m, or -1
+  int32_t* full_list = nullptr;    // [FC] g for a valid chunk position, -1 past the total
+  int32_t* full_vcount = nullptr;  // [1] valid positions of the current chunk
+  double* full_coeff = nullptr;    // [B][max_moves]
   int32_t* full_moves = nullptr;   // [B][max_moves][4]
+  double* full_la_all = nullptr;   // [B][max_moves + 1] log|psi| of n (m = 0) and its n'
+  int32_t* full_sg_all = nullptr;  // [B][max_moves + 1]
 
   // ACE family (full-recompute network, no cached update)
   bool ace = false;
@@ -251,7 +255,7 @@ size_t ace_frag_bytes(const scale_arch& a);
 bool ace_mma_shapes(const scale_arch& a);
 bool ace_tc_shapes(const scale_arch& a);
 cudaError_t launch_ace_build(scale_ctx* c);
-cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64);
+cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg = nullptr);
 
 // kernels (launch wrappers), each enqueued on ctx->stream
 // count (optional, device): sample_list is compacted, its first *count entries are used
@@ -280,8 +284,8 @@ cudaError_t launch_grad(scale_ctx* c, double* grad, int recompute);
 cudaError_t refresh_samples(scale_ctx* c, bool force_all, bool counters_due = true);
 cudaError_t launch_mark_refresh(scale_ctx* c, bool force_all, bool counters_due);
 cudaError_t launch_slots_list(scale_ctx* c, const int32_t* list, int B);
-cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, void* phi);
-cudaError_t launch_det_f32(scale_ctx* c, float* mats, int n, int B, double* logabs, int32_t* sign);
+cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, const int32_t* vcount,
+                               double* phi);
 
 template <typename T>
 Net<T> make_net(scale_ctx* c);

@@ -59,3 +59,12 @@ def test_invalid_descriptors_rejected_on_host():
     for pb in bad:
         assert Bd.scale_param_count(pb) == -1
         assert Bd.scale_footprint_bytes(pb, 4) == 0
+
+
+def test_package_star_import():
+    """Every name the package lists in __all__ exists (a star import succeeds)."""
+    import paper_2604_25775_gb300 as pkg
+    ns = {}
+    exec("from paper_2604_25775_gb300 import *", ns)
+    for name in pkg.__all__:
+        assert name in ns, name

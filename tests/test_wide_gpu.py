@@ -71,25 +71,27 @@ def test_scale_l_table_widths():
     cond = conditioning(ora, occ)
     la = ctx.log_psi()[0].cpu().numpy()
     la_o, _ = ora.log_psi(occ)
-    _check("scale_l16x16 log|psi|", la, la_o, cond, 1e-4, 1e4, min_good=0)
+    _check("scale_l16x16 log|psi|", la, la_o, cond, 1e-4, 1e4, min_good=1)
     p8 = pb.replace(Lx=8, Ly=8, n_up=28, n_dn=28)
     ctx8, ora8, occ8, _ = setup(p8, 2, 1263, 5713, scale=0.02)
     cond8 = conditioning(ora8, occ8)
     e = ctx8.local_energy(Bd.PATH_FULL).cpu().numpy()
     e_o, _ = ora8.local_energy(occ8)
     scale = np.maximum(eloc_term_scale(ora8, occ8), 1.0)
-    _check("SCALE-L widths 8x8 E_loc / term scale", e / scale, e_o / scale, cond8, 1e-4, 1e3, min_good=0)
+    _check("SCALE-L widths 8x8 E_loc / term scale", e / scale, e_o / scale, cond8, 1e-4, 1e3, min_good=1)
 
 
 def test_scale_xl_table_widths():
     """Table tab:model SCALE-XL (32x32, conv 640 and site-wise 4 x 1280 on the tensor cores):
-    log|psi| of 2 samples (the oracle takes about ten seconds per amplitude)."""
+    log|psi| of 2 samples (the oracle takes about ten seconds per amplitude). Both have
+    cond(Phi) of about 1.5e6 (uniformly random 32x32 configurations); log|psi| is in the
+    hundreds, so the 1e-4 relative bound is asserted on both (band 1e7)."""
     pb = I.workload("scale_xl32x32")
     ctx, ora, occ, st = setup(pb, 2, 1264, 5714, scale=0.02)
     cond = conditioning(ora, occ)
     la = ctx.log_psi()[0].cpu().numpy()
     la_o, _ = ora.log_psi(occ)
-    _check("scale_xl32x32 log|psi|", la, la_o, cond, 1e-4, 1e4, min_good=0)
+    _check("scale_xl32x32 log|psi|", la, la_o, cond, 1e-4, 1e7, min_good=2)
 
 
 def test_wide_rejects_cached_update_entry_points():
@@ -108,8 +110,8 @@ def test_wide_open_ragged_single():
     cond = conditioning(ora, occ)
     la = ctx.log_psi()[0].cpu().numpy()
     la_o, _ = ora.log_psi(occ)
-    _check("scale_l8x8 open single log|psi|", la, la_o, cond, 1e-4, 1e3, min_good=0)
+    _check("scale_l8x8 open single log|psi|", la, la_o, cond, 1e-4, 1e3, min_good=1)
     e = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
     e_o, _ = ora.local_energy(occ)
     scale = np.maximum(eloc_term_scale(ora, occ), 1.0)
-    _check("scale_l8x8 open single E_loc / term scale", e / scale, e_o / scale, cond, 1e-4, 1e3, min_good=0)
+    _check("scale_l8x8 open single E_loc / term scale", e / scale, e_o / scale, cond, 1e-4, 1e3, min_good=1)

@@ -39,3 +39,39 @@ def test_noalloc_matches_context_path(name, B, tol):
         assert torch.equal(torch.isfinite(la), fin) and not fin[-1]
         assert (la[fin] - la_ref[fin]).abs().max().item() <= tol
     ctx.close()
+
+
+def test_noalloc_rejects_oversized_shape_and_other_families():
+    """A shape whose single sample does not fit the fixed array is refused with SCALE_EBUDGET
+    before any work is queued (64x64, 1792 + 1792 electrons: one FP64 Slater matrix is 103 MB,
+    the array 64 MiB), and the ACE family, which has no working set in the array, with
+    SCALE_EUNSUPPORTED; an ordinary call still succeeds afterwards."""
+    import torch
+    big = I.workload("hubbard16x16").replace(Lx=64, Ly=64, n_up=1792, n_dn=1792)
+    for pb, status in ((big, Bd.EBUDGET), (I.workload("ace4x4"), Bd.EUNSUPPORTED)):
+        params = torch.zeros(I.param_count(pb), dtype=torch.float64, device="cuda")
+        M0 = torch.zeros((2 * pb.N, pb.Ne), dtype=torch.float64, device="cuda")
+        occ = torch.zeros((1, pb.N), dtype=torch.int8, device="cuda")
+        la = torch.empty(1, dtype=torch.float64, device="cuda")
+        sg = torch.empty(1, dtype=torch.int32, device="cuda")
+        with pytest.raises(Bd.ScaleError) as e:
+            Bd.scale_log_psi_noalloc(pb, params, M0, occ, la, sg)
+        assert e.value.status == status
+        del params, M0
+    pb = I.workload("hubbard4x4")
+    pseed, cseed = I.workload_seeds("hubbard4x4")
+    params = torch.from_numpy(I.random_params(pb, pseed)).cuda()
+    M0 = torch.from_numpy(I.plane_wave_M0(pb)).cuda()
+    occ = torch.from_numpy(I.random_configs(pb, 8, cseed)).cuda()
+    la = torch.empty(8, dtype=torch.float64, device="cuda")
+    sg = torch.empty(8, dtype=torch.int32, device="cuda")
+    Bd.scale_log_psi_noalloc(pb, params, M0, occ, la, sg)
+    ctx = Bd.Context(pb, 8)
+    ctx.scale_set_params(params, M0)
+    ctx.scale_load(occ)
+    la_ref, sg_ref = ctx.log_psi()
+    torch.cuda.synchronize()
+    fin = torch.isfinite(la_ref)
+    assert fin.any() and torch.equal(sg, sg_ref) and torch.equal(torch.isfinite(la), fin)
+    assert (la[fin] - la_ref[fin]).abs().max().item() <= 1e-10
+    ctx.close()
