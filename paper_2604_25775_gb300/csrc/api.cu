@@ -154,6 +154,7 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   t += FC * Ne * Ne * 8;                   // Phi64
   t += ace ? 16 : (size_t)B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T;  // commit scratch
   if (ace && T == 4) t += ace_frag_bytes(*a);
+  if (!ace && T == 4 && h == 32) t += (size_t)(a->n_layers - 1) * 2 * h * h * 4;  // tensor-core weight image
   t += FC * (N + 4 + 8 + 4 + 4);          // full-path chunk: occupations, owner, log|psi|, sign, list
   t += (size_t)B * z.cap * (8 + 16);       // full-path coefficients, moves
   t += (size_t)B * (z.cap + 1) * (8 + 4);  // full-path log|psi| and sign of every entry
@@ -194,7 +195,7 @@ void free_all(scale_ctx* c) {
                   c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_la_all, c->full_sg_all,
                   c->full_list, c->full_vcount, c->full_moves,
                   c->commit_scratch, c->la_tmp, c->sg_tmp, c->full_la, c->full_sg, c->full_diag,
-                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag, c->ace_err};
+                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag, c->ace_err, c->et_wimg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -349,7 +350,18 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A(&c->full_sg_all, B * (cap + 1) * 4);
   if (c->use_mma) A((char**)&c->wfrag, (size_t)c->L * (c->hpad / 8) * (c->hpad / 8) * 32 * 16);
   if (c->ace_mma) A((char**)&c->ace_frag, ace_frag_bytes(*arch));
-  if (c->ace) A(&c->ace_err, 16);
+  A(&c->ace_err, 16);  // error word of the tensor-core kernels (bounded waits)
+  {
+    // the batched tensor-core local-energy kernel: its slot size and whether its plan fits
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int rows = c->lowrank_ok ? et_rows_per_move(c, bonds) : 0;
+    if (et_supported(c, rows, optin)) {
+      c->et_rows = rows;
+      A((char**)&c->et_wimg, et_wimg_bytes(c));
+    }
+  }
   if (e != cudaSuccess) {
     free_all(c);
     delete c;
@@ -360,7 +372,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stat_dev, 0, 32, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->drift, 0, B * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->commits, 0, B * 4, c->stream);
-  if (e == cudaSuccess && c->ace_err) e = cudaMemsetAsync(c->ace_err, 0, 16, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ace_err, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     free_all(c);
@@ -391,6 +403,7 @@ scale_status scale_set_params(scale_ctx* c, const double* params, const double* 
   }
   SCALE_TRY(c, launch_build_ke(c));
   SCALE_TRY(c, launch_build_wfrag(c));
+  SCALE_TRY(c, launch_build_et(c));
   if (c->fp64) {
     const Net<double> n = make_net<double>(c);
     k_m0b<double><<<512, 256, 0, c->stream>>>(n.M0, n.proj_b, c->N, c->Ne, (double*)c->M0b);

@@ -300,12 +300,16 @@ cudaError_t project_t(scale_ctx* c, int B, const int32_t* list, const int32_t* c
    : (c)->hpad == 32 ? ((c)->fp64 ? FN<double, 32>(__VA_ARGS__) : FN<float, 32>(__VA_ARGS__)) \
                      : ((c)->fp64 ? FN<double, 64>(__VA_ARGS__) : FN<float, 64>(__VA_ARGS__)))
 
+// Mixed precision at 32 channels runs the batched tensor-core kernel (eloc_tc.cu); every
+// other shape the per-warp kernel above.
 cudaError_t launch_eloc_lowrank(scale_ctx* c, double* eloc) {
+  if (c->et_wimg) return launch_eloc_tc(c, eloc, nullptr, c->B);
   return SCALE_DISPATCH_H(c, eloc_t, c, eloc, nullptr, c->B);
 }
 
 // E_loc of the listed samples only (outputs indexed by sample).
 cudaError_t launch_eloc_lowrank_list(scale_ctx* c, const int32_t* list, int n, double* eloc) {
+  if (c->et_wimg) return launch_eloc_tc(c, eloc, list, n);
   return SCALE_DISPATCH_H(c, eloc_t, c, eloc, list, n);
 }
 

@@ -504,38 +504,43 @@ __device__ __forceinline__ int warp_pivot(const T (*R)[kRMax + 1], int k, int r)
   }
 }
 
-// Step 5: det of ms.R (r x r) by LU with partial pivoting, lane j owning column j; the
-// pivot search is a warp argmax over the rows, one reciprocal per column.
-// R is destroyed. Returns the determinant (same value in all lanes).
-template <typename T, int H>
-__device__ T warp_det(MoveScratch<T, H>& ms, int r) {
+// Step 5: det of R (r x r, r <= kRMax) by LU with partial pivoting, lane j owning column j;
+// the pivot search is a warp argmax over the rows, one reciprocal per column. R is destroyed.
+// Returns the determinant (same value in all lanes).
+template <typename T>
+__device__ T warp_det_R(T (*R)[kRMax + 1], int r) {
   const int lane = threadIdx.x & 31;
   T det = T(1);
   for (int k = 0; k < r; ++k) {
-    const int p = warp_pivot<T>(ms.R, k, r);
+    const int p = warp_pivot<T>(R, k, r);
     if (p != k) {
       if (lane < r) {
-        const T t = ms.R[k][lane];
-        ms.R[k][lane] = ms.R[p][lane];
-        ms.R[p][lane] = t;
+        const T t = R[k][lane];
+        R[k][lane] = R[p][lane];
+        R[p][lane] = t;
       }
       det = -det;
     }
     __syncwarp();
-    const T pv = ms.R[k][k];
+    const T pv = R[k][k];
     det *= pv;
     if (pv == T(0)) return T(0);
     const T inv = recip(pv);
     // multipliers in column k (lane i > k), then the trailing update (lane j > k)
-    if (lane > k && lane < r) ms.R[lane][k] *= inv;
+    if (lane > k && lane < r) R[lane][k] *= inv;
     __syncwarp();
     if (lane > k && lane < r) {
-      const T u = ms.R[k][lane];
-      for (int i = k + 1; i < r; ++i) ms.R[i][lane] -= ms.R[i][k] * u;
+      const T u = R[k][lane];
+      for (int i = k + 1; i < r; ++i) R[i][lane] -= R[i][k] * u;
     }
     __syncwarp();
   }
   return det;
+}
+
+template <typename T, int H>
+__device__ T warp_det(MoveScratch<T, H>& ms, int r) {
+  return warp_det_R<T>(ms.R, r);
 }
 
 // Parity of the number of occupied orbitals strictly between o1 and o2 (Jordan-Wigner

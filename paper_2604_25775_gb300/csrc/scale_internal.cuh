@@ -22,6 +22,7 @@
 #include <math_constants.h>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/scale.h"
 
@@ -101,8 +102,7 @@ struct Net {
 //            + 21844z^13/6081075 - 929569z^15/638512875 + ...
 // for |z| < 0.5 (the first omitted term is below 1e-8 relative there), and from
 // tanh|z| = (1 - e^{-2|z|}) / (1 + e^{-2|z|}) above (no cancellation once |z| >= 0.5).
-__device__ __forceinline__ float tanh_f32(float z) {
-  const float a = fabsf(z);
+__device__ __forceinline__ float tanh_f32_small(float z) {  // the series branch, |z| < 0.5
   const float s = z * z;
   float p = -929569.f / 638512875.f;
   p = fmaf(p, s, 21844.f / 6081075.f);
@@ -111,7 +111,11 @@ __device__ __forceinline__ float tanh_f32(float z) {
   p = fmaf(p, s, -17.f / 315.f);
   p = fmaf(p, s, 2.f / 15.f);
   p = fmaf(p, s, -1.f / 3.f);
-  const float small = fmaf(z * s, p, z);
+  return fmaf(z * s, p, z);
+}
+__device__ __forceinline__ float tanh_f32(float z) {
+  const float a = fabsf(z);
+  const float small = tanh_f32_small(z);
   float e;  // e^{-2|z|} = 2^{|z| (-2 log2 e)}, one multiply into the hardware base-2 exponential
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(a * -2.8853900817779268f));
   const float big = copysignf(__fdividef(1.f - e, 1.f + e), z);
@@ -151,6 +155,8 @@ struct scale_ctx {
   bool fp64 = true;
   bool lowrank_ok = false;  // SCALE layer layout (k_l = 1 for l >= 1)
   bool use_mma = false;     // mixed mode, SCALE layout, h in {16, 32, 64}: site-wise layers on tensor cores
+  void* et_wimg = nullptr;  // batched tensor-core local energies (eloc_tc.cu): weight image, or null
+  int et_rows = 0;          // rows per move slot of that kernel (largest affected set)
   int hpad = 16;            // channel capacity of the per-warp scratch (16, 32 or 64)
   void* wfrag = nullptr;    // hi/lo mma fragments (TF32, or BF16 as an option) of the site-wise layers
   int64_t P = 0;
@@ -289,5 +295,12 @@ cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, const int
 
 template <typename T>
 Net<T> make_net(scale_ctx* c);
+
+// batched tensor-core local energies (eloc_tc.cu)
+int et_rows_per_move(const scale_ctx* c, const std::vector<int32_t>& bonds);
+size_t et_wimg_bytes(const scale_ctx* c);
+bool et_supported(const scale_ctx* c, int rows_per_move, int smem_optin);
+cudaError_t launch_build_et(scale_ctx* c);
+cudaError_t launch_eloc_tc(scale_ctx* c, double* eloc, const int32_t* list, int n);
 
 }  // namespace scale

@@ -274,6 +274,37 @@ def test_full_path_is_asynchronous():
     assert np.array_equal(out.cpu().numpy(), e_ref, equal_nan=True)
 
 
+@pytest.mark.parametrize("variant", ["torus", "tp", "tj", "open_silu", "shared_embed", "ph", "k1",
+                                     "sitewise_residual", "plus"])
+def test_local_energy_tensor_core_batched_8x8(variant):
+    """The batched tensor-core local-energy kernel (mixed precision, 32 channels: the site-wise
+    layers of all moves on tcgen05, move warps for S, R and det R) on 8x8 shapes that vary each
+    of its parts: NNN hops (14-row move slots), t-J exchanges, open edges with SiLU, a shared
+    embedding, the particle-hole model, a 1x1 first layer (2-row slots, 64 moves per batch),
+    residual site-wise layers (the layer input read back from TMEM) and SCALE-L's 13-site plus
+    stencil (18-row slots). Against the oracle at 1e-4 (cond < 1e3), and bit-identical on a
+    second call."""
+    base = I.workload("hubbard8x8").replace(h=32)
+    pb = {
+        "torus": base,
+        "tp": base.replace(tp=-0.25),
+        "tj": base.replace(model=I.MODEL_TJ, U=0.0, J=0.4),
+        "open_silu": base.replace(pbc_x=0, pbc_y=0, act=I.ACT_SILU, tp=0.1),
+        "shared_embed": base.replace(per_site_embed=0),
+        "ph": base.replace(model=I.MODEL_HUBBARD_PH, U=-4.0, n_dn=36),
+        "k1": base.replace(ksize=[1, 1, 1, 1]),
+        "sitewise_residual": base.replace(residual=[1, 1, 1, 1]),
+        "plus": base.replace(ksize=[5, 1, 1, 1], stencil=I.STENCIL_DISK),
+    }[variant]
+    ctx, ora, occ, st = setup(pb, 64, 1240, 5690)
+    cond = conditioning(ora, occ)
+    e1 = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    e2 = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    assert np.array_equal(e1, e2, equal_nan=True)
+    e_o, _ = ora.local_energy(occ)
+    _check(f"tensor-core batched 8x8 {variant}", e1, e_o, cond, MIXED_TOL, 1e3, min_good=1)
+
+
 def test_zero_backflow_closed_form_on_gpu():
     """All weights zero: E_loc = E0 + U * D exactly (both paths)."""
     pb = I.workload("hubbard8x8").replace(precision=I.PREC_FP64)
