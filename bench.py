@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--full-samples", type=int, default=128)
     ap.add_argument("--cpu-samples", type=int, default=48)
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--sweep-steps", type=int, default=64)
     ap.add_argument("--sym-walkers", type=int, default=1024)
     ap.add_argument("--ace-walkers", type=int, default=16)
@@ -411,6 +411,22 @@ def main():
         line["cold"] = {"load_ms": load_ms, "eloc_ms": cold_eloc_ms,
                         "eloc_per_s": B / ((load_ms + cold_eloc_ms) / 1e3)}
         ctx2.close()
+        # the same local energies with the batched tensor-core kernel (site-wise layers of all
+        # moves on tcgen05; arch.lowrank_kernel = SCALE_LOWRANK_BATCHED)
+        ctxb = Bd.make_context(pb.replace(lowrank_kernel=I.LOWRANK_BATCHED), params, M0, B)
+        ctxb.scale_load(occ_d)
+        eb = torch.empty(B, dtype=torch.float64, device="cuda")
+        ctxb.scale_local_energy(eb)
+        torch.cuda.synchronize()
+        a.record()
+        ctxb.scale_local_energy(eb)
+        b2.record()
+        torch.cuda.synchronize()
+        bt_ms = a.elapsed_time(b2)
+        ctxb.close()
+        line["lowrank_batched_kernel"] = {"eloc_ms": bt_ms, "eloc_per_s": B / (bt_ms / 1e3),
+                                          "warp_kernel_eloc_ms": eloc_ms,
+                                          "note": "same walkers as the cold load; the per-warp kernel is the default"}
         # Metropolis sweep on the same walkers: hop proposal, rank-r ratio, accept, Woodbury
         # commit of the accepted moves (random numbers generated on the host beforehand). The
         # first --sweep-steps are timed; the sweep then continues untimed to 2.5 N steps per
@@ -496,13 +512,12 @@ def main():
             line["wide"] = next_bench.run_wide(args.wide_walkers)
         # the cached update with SCALE-L's plus stencil (bench network otherwise)
         line["plus_stencil"] = next_bench.run_plus(B)
-        # serving: open-loop Poisson sweep-step requests over mixed chains, continuous batching
-        if args.serve_seconds > 0:
+        # serving: open-loop Poisson local-energy requests over mixed chains (8x8, 16x16, 32x32,
+        # Hubbard and t-J, 64..4096 walkers), continuous batching, at 0.3 / 0.6 / 0.9 of the
+        # measured capacity
+        if args.serve_requests > 0:
             from paper_2604_25775_gb300 import serve_bench
-            sv = serve_bench.run(duration_s=args.serve_seconds)
-            line["serve"] = {k: sv[k] for k in ("p50_ms", "p99_ms", "throughput_eloc_per_s", "capacity_eloc_per_s",
-                                                "offered_load", "requests", "open_p50_ms", "open_p99_ms",
-                                                "resident_max_gb", "classes", "chains")}
+            line["serve"] = serve_bench.run(requests_per_load=args.serve_requests)
         # CPU oracle baseline on a bounded sample
         from oracle import oracle as O
         m = O.Model(pb, params, M0)

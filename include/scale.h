@@ -61,7 +61,8 @@ typedef enum {
   SCALE_EBUDGET = 3,      /* request does not fit the HBM budget */
   SCALE_ECUDA = 4,        /* a CUDA call failed (text in scale_last_error) */
   SCALE_ETIMEOUT = 5,     /* a bounded wait ran out */
-  SCALE_EUNSUPPORTED = 6  /* valid but not supported by this library (see text) */
+  SCALE_EUNSUPPORTED = 6, /* valid but not supported by this library (see text) */
+  SCALE_ECANCELED = 7     /* a server request was cancelled before it ran */
 } scale_status;
 
 /* SCALE_MODEL_HUBBARD_PH: the Hubbard model after the particle-hole transformation of the
@@ -155,7 +156,17 @@ typedef struct {
   int32_t stencil;        /* SCALE_STENCIL_*; the SCALE family's cached update takes layer 0 as a
                              1x1 or 3x3 box or the 5x5 plus (disk), other shapes run by full
                              recompute; scale_grad_logpsi takes either stencil */
+  int32_t lowrank_kernel; /* kernel of the low-rank local energies: SCALE_LOWRANK_WARP (0, the
+                             default) or SCALE_LOWRANK_BATCHED (1, mixed precision at 32
+                             channels only; SCALE_EUNSUPPORTED otherwise) */
 } scale_arch;
+
+/* Low-rank local-energy kernels. WARP: one warp per connected configuration, the site-wise
+ * layers of its affected sites on mma.sync tiles. BATCHED: the affected-site rows of all
+ * moves of a walker packed into 128-row tiles and the site-wise layers run on tcgen05 (A
+ * operand in Tensor Memory), move warps for the rest; the same results within the mixed-mode
+ * tolerance. */
+enum { SCALE_LOWRANK_WARP = 0, SCALE_LOWRANK_BATCHED = 1 };
 
 typedef struct {
   int64_t n_eloc;          /* local energies produced (low-rank path) */
@@ -167,6 +178,8 @@ typedef struct {
   int32_t batch;           /* samples currently loaded */
   int32_t max_moves;       /* capacity of connected configurations per sample */
   int32_t full_chunk;      /* configurations per chunk of the full-recompute path */
+  int32_t wait_timeouts;   /* nonzero once a bounded wait of a tensor-core kernel ran out (its
+                              outputs were NaN); cleared by reading */
 } scale_stats;
 
 typedef struct scale_ctx scale_ctx;
@@ -274,6 +287,14 @@ scale_status scale_refresh(scale_ctx *ctx, int32_t force_all);
  * SCALE family only (either stencil); ACE and the wide shapes return SCALE_EUNSUPPORTED. */
 scale_status scale_grad_logpsi(scale_ctx *ctx, double *grad, int32_t recompute);
 
+/* Test hook for the failure path of the tensor-core kernels (not a construct of the paper):
+ * what = 1 makes the next local-energy call of a context that runs the batched tensor-core
+ * kernel (mixed precision, 32 channels) leave the first hand-off between its warp roles
+ * unsignalled, so that the bounded wait on it runs out: the affected walkers' E_loc come back
+ * NaN and scale_get_stats reports wait_timeouts; no fault, trap or hang. One-shot; what = 0
+ * clears it. SCALE_EUNSUPPORTED for contexts that do not run that kernel. */
+scale_status scale_test_inject(scale_ctx *ctx, int32_t what);
+
 /* Counters since creation (host struct). Synchronises the context's stream. */
 scale_status scale_get_stats(scale_ctx *ctx, scale_stats *out_host);
 
@@ -372,8 +393,17 @@ scale_status scale_server_create(const scale_server_cfg *cfg, scale_server **out
 scale_status scale_server_submit(scale_server *srv, const scale_request *req, uint64_t *ticket);
 
 /* Wait at most timeout_us for a ticket; SCALE_ETIMEOUT if it is still pending (the ticket
- * stays valid). On completion fills *out and releases the ticket. */
+ * stays valid and its request keeps running). On completion fills *out and releases the
+ * ticket. */
 scale_status scale_server_poll(scale_server *srv, uint64_t ticket, scale_result *out, int32_t timeout_us);
+
+/* Cancel a request that has not started: an ELOC / STEP / LOGPSI / CLOSE request still waiting
+ * for its chain or its class's next batch, or an OPEN still waiting for admission. The ticket
+ * completes at once with status SCALE_ECANCELED (poll it to release it; out_host is not
+ * written, a cancelled STEP commits nothing); a cancelled OPEN makes the chain's later requests
+ * fail with SCALE_EINVAL. SCALE_EINVAL when the ticket is unknown, already on the GPU or done
+ * (such a request runs to completion). Never blocks on the GPU. */
+scale_status scale_server_cancel(scale_server *srv, uint64_t ticket);
 
 /* Resident footprint, its maximum so far, batches and requests processed. */
 scale_status scale_server_stats(scale_server *srv, scale_server_stats_t *out);

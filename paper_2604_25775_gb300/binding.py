@@ -19,7 +19,7 @@ _lock = threading.Lock()
 _lib = None
 MAX_LAYERS = 32
 
-OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT, EUNSUPPORTED = range(7)
+OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT, EUNSUPPORTED, ECANCELED = range(8)
 PATH_LOWRANK, PATH_FULL = 0, 1
 SAMPLE_BAD_COUNT, SAMPLE_DOUBLE_OCC, SAMPLE_SINGULAR, SAMPLE_DRIFT = 1, 2, 4, 8
 
@@ -27,7 +27,7 @@ EXPORTED = [
     "scale_param_count", "scale_footprint_bytes", "scale_create", "scale_set_params", "scale_load",
     "scale_log_psi", "scale_get_occ", "scale_ratios", "scale_local_energy", "scale_commit",
     "scale_refresh", "scale_grad_logpsi", "scale_get_stats", "scale_last_error", "scale_destroy",
-    "scale_sweep", "scale_log_psi_sym",
+    "scale_sweep", "scale_log_psi_sym", "scale_test_inject",
 ]
 
 
@@ -50,14 +50,15 @@ class scale_arch(ctypes.Structure):
                 ("refresh_every", ctypes.c_int32), ("drift_tol", ctypes.c_double),
                 ("ksize", ctypes.c_int32 * MAX_LAYERS), ("residual", ctypes.c_int32 * MAX_LAYERS),
                 ("family", ctypes.c_int32), ("n_conv", ctypes.c_int32), ("h_mlp", ctypes.c_int32),
-                ("ln_eps", ctypes.c_double), ("stencil", ctypes.c_int32)]
+                ("ln_eps", ctypes.c_double), ("stencil", ctypes.c_int32), ("lowrank_kernel", ctypes.c_int32)]
 
 
 class scale_stats(ctypes.Structure):
     _fields_ = [("n_eloc", ctypes.c_int64), ("n_eloc_full", ctypes.c_int64),
                 ("n_commits", ctypes.c_int64), ("n_refresh", ctypes.c_int64),
                 ("n_drift_refresh", ctypes.c_int64), ("drift_max", ctypes.c_double),
-                ("batch", ctypes.c_int32), ("max_moves", ctypes.c_int32), ("full_chunk", ctypes.c_int32)]
+                ("batch", ctypes.c_int32), ("max_moves", ctypes.c_int32), ("full_chunk", ctypes.c_int32),
+                ("wait_timeouts", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -92,7 +93,8 @@ def load_library(build: bool = True):
                                ("scale_grad_logpsi", [V, V, ctypes.c_int32]),
                                ("scale_get_stats", [V, P(scale_stats)]),
                                ("scale_sweep", [V, ctypes.c_int32, V, V, V, V]),
-                               ("scale_log_psi_sym", [V, ctypes.c_int32, V, V, V, V])):
+                               ("scale_log_psi_sym", [V, ctypes.c_int32, V, V, V, V]),
+                               ("scale_test_inject", [V, ctypes.c_int32])):
                 fn = getattr(lib, name)
                 fn.restype = ctypes.c_int
                 fn.argtypes = args
@@ -114,6 +116,7 @@ def make_descriptors(pb: I.Problem):
         a.residual[l] = int(pb.residual[l])
     a.family, a.n_conv, a.h_mlp, a.ln_eps = pb.family, pb.n_conv, pb.h_mlp, pb.ln_eps
     a.stencil = pb.stencil
+    a.lowrank_kernel = pb.lowrank_kernel
     return s, a
 
 
@@ -242,6 +245,9 @@ class Context:
         self.scale_log_psi_sym(perms, chi, la, sg)
         return la, sg
 
+    def scale_test_inject(self, what=1):
+        self._check(self.lib.scale_test_inject(self.h, what))
+
     def scale_refresh(self, force_all=True):
         self._check(self.lib.scale_refresh(self.h, 1 if force_all else 0))
 
@@ -334,7 +340,7 @@ EXPORTED += ["scale_log_psi_noalloc"]
 
 SRV_OPEN, SRV_ELOC, SRV_STEP, SRV_LOGPSI, SRV_CLOSE = range(5)
 EXPORTED += ["scale_server_create", "scale_server_submit", "scale_server_poll", "scale_server_stats",
-             "scale_server_destroy"]
+             "scale_server_destroy", "scale_server_cancel"]
 
 
 class scale_server_cfg(ctypes.Structure):
@@ -370,6 +376,8 @@ def _server_lib():
         lib.scale_server_submit.argtypes = [V, P(scale_request), P(ctypes.c_uint64)]
         lib.scale_server_poll.restype = ctypes.c_int
         lib.scale_server_poll.argtypes = [V, ctypes.c_uint64, P(scale_result), ctypes.c_int32]
+        lib.scale_server_cancel.restype = ctypes.c_int
+        lib.scale_server_cancel.argtypes = [V, ctypes.c_uint64]
         lib.scale_server_stats.restype = ctypes.c_int
         lib.scale_server_stats.argtypes = [V, P(scale_server_stats_t)]
         lib.scale_server_destroy.restype = None
@@ -445,6 +453,14 @@ class Server:
             raise ScaleError(st, "scale_server_poll failed")
         self._keep.pop(ticket, None)
         return r.status, r.latency_us
+
+    def cancel(self, ticket: int) -> bool:
+        """scale_server_cancel: True when the request was still queued and is now cancelled
+        (poll it to release it: status ECANCELED), False when it had started or finished."""
+        st = self.lib.scale_server_cancel(self.h, ticket)
+        if st not in (OK, EINVAL):
+            raise ScaleError(st, "scale_server_cancel failed")
+        return st == OK
 
     def stats(self) -> dict:
         s = scale_server_stats_t()

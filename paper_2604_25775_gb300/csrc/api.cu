@@ -64,6 +64,8 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
   if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED && a->precision != SCALE_PREC_MIXED_BF16)
     return fail("unknown precision");
   if (a->refresh_every < 1) return fail("refresh_every must be >= 1");
+  if (a->lowrank_kernel != SCALE_LOWRANK_WARP && a->lowrank_kernel != SCALE_LOWRANK_BATCHED)
+    return fail("unknown low-rank kernel");
   for (int l = 0; l < a->n_layers; ++l) {
     const int k = a->ksize[l];
     if (k < 1 || k > 7 || (k % 2) == 0) {
@@ -154,7 +156,7 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   t += FC * Ne * Ne * 8;                   // Phi64
   t += ace ? 16 : (size_t)B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T;  // commit scratch
   if (ace && T == 4) t += ace_frag_bytes(*a);
-  if (!ace && T == 4 && h == 32) t += (size_t)(a->n_layers - 1) * 2 * h * h * 4;  // tensor-core weight image
+  if (a->lowrank_kernel == SCALE_LOWRANK_BATCHED) t += (size_t)(a->n_layers - 1) * 2 * h * h * 4;  // weight image
   t += FC * (N + 4 + 8 + 4 + 4);          // full-path chunk: occupations, owner, log|psi|, sign, list
   t += (size_t)B * z.cap * (8 + 16);       // full-path coefficients, moves
   t += (size_t)B * (z.cap + 1) * (8 + 4);  // full-path log|psi| and sign of every entry
@@ -357,7 +359,12 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int rows = c->lowrank_ok ? et_rows_per_move(c, bonds) : 0;
-    if (et_supported(c, rows, optin)) {
+    if (arch->lowrank_kernel == SCALE_LOWRANK_BATCHED) {
+      if (!et_supported(c, rows, optin)) {
+        free_all(c);
+        delete c;
+        return SCALE_EUNSUPPORTED;
+      }
       c->et_rows = rows;
       A((char**)&c->et_wimg, et_wimg_bytes(c));
     }
@@ -546,10 +553,23 @@ scale_status scale_grad_logpsi(scale_ctx* c, double* grad, int32_t recompute) {
   return SCALE_OK;
 }
 
+scale_status scale_test_inject(scale_ctx* c, int32_t what) {
+  if (!c || what < 0 || what > 1) return SCALE_EINVAL;
+  if (!c->et_wimg) {
+    c->err = "the batched tensor-core local-energy kernel does not run for this context";
+    return SCALE_EUNSUPPORTED;
+  }
+  c->et_inject = what;
+  return SCALE_OK;
+}
+
 scale_status scale_get_stats(scale_ctx* c, scale_stats* out) {
   if (!c || !out) return SCALE_EINVAL;
   double host[4];
+  int32_t timeouts = 0;
   SCALE_TRY(c, cudaMemcpyAsync(host, c->stat_dev, sizeof host, cudaMemcpyDeviceToHost, c->stream));
+  SCALE_TRY(c, cudaMemcpyAsync(&timeouts, c->ace_err, sizeof timeouts, cudaMemcpyDeviceToHost, c->stream));
+  SCALE_TRY(c, cudaMemsetAsync(c->ace_err, 0, sizeof timeouts, c->stream));
   SCALE_TRY(c, cudaStreamSynchronize(c->stream));
   *out = c->stats;
   out->drift_max = host[0];
@@ -558,6 +578,7 @@ scale_status scale_get_stats(scale_ctx* c, scale_stats* out) {
   out->n_commits = cnt[0];
   out->n_refresh = cnt[1];
   out->n_drift_refresh = cnt[2];
+  out->wait_timeouts = timeouts;
   return SCALE_OK;
 }
 

@@ -2,19 +2,19 @@
 // site-wise layers (Eq. MLP) of all connected configurations batched onto the 5th-generation
 // tensor cores. Mixed precision, 32 channels.
 //
-// One CTA of 20 warps per walker. The warps take two roles and hand batches of moves to each
+// One CTA of 16 warps per walker. The warps take two roles and hand batches of moves to each
 // other through shared memory and mbarriers:
 //   move warps (12): for each move of a batch, the affected sites S (Eq. neighbor) and the
 //     layer-0 output rows  x_s = E_s[n'_s] + act(z0_s + sum of layer-0 table deltas)  in the
 //     move's slot of a batch buffer (one row per site of S); once the site-wise layers have
 //     run, the rank-r matrix R of Eq. SMW from the new features H'(L), the projector
 //     Pt = W Phi^-1 and the cached inverse, and det R;
-//   MLP warps (8): the site-wise layers on the batch's 256 rows (two MMA tiles of 128 rows):
+//   MLP warps (4): the site-wise layers on the batch's 256 rows (two MMA tiles of 128 rows):
 //     tcgen05.mma kind::tf32 with the activations as the A operand in Tensor Memory (hi and lo
 //     halves of a TF32 split), each layer's hi/lo weight tiles as the B operand in shared
 //     memory, three products per K step (hi*hi + lo*hi + hi*lo) accumulated in FP32 in TMEM,
 //     and the epilogue (bias, activation, split of the next layer's input) in registers with
-//     one thread per row and 16 of its 32 channels.
+//     one thread per row.
 // Two batch buffers alternate: the move warps stage batch g+1 and finish batch g-1 while the
 // MLP warps run batch g. The contribution of every move is stored by its enumeration index and
 // the chunk's sum is taken in that order, so E_loc does not depend on the scheduling.
@@ -33,7 +33,8 @@ namespace {
 
 constexpr int kEtH = 32;                 // channels
 constexpr int kEtLd = kEtH + 4;          // row stride of the batch buffers (floats)
-constexpr int kEtMlpWarps = 8;
+constexpr int kEtMlpWarps = 4;        // one per TMEM lane quarter: thread = row, all channels
+constexpr int kEtCols = kEtH * 4 / kEtMlpWarps;  // channels of a row per MLP thread
 constexpr int kEtWork = 12;
 constexpr int kEtWarps = kEtMlpWarps + kEtWork;
 constexpr int kEtThreads = 32 * kEtWarps;
@@ -90,6 +91,7 @@ struct EtArgs {
   int rpm;            // rows per move slot: the largest affected set of any move
   int mb;             // moves per batch
   int* err;           // set when a bounded wait ran out
+  int inject;         // test hook: the first batch's hand-off to the MLP warps is not signalled
 };
 
 // Byte offset of element (n, k) of an [N x 8] tf32 tile in the K-major core-matrix layout
@@ -137,11 +139,12 @@ __device__ __forceinline__ void et_act(int act, float (&z)[NV]) {
   }
 }
 
-// Split 16 values into TF32 hi and lo halves and store them to TMEM columns hi_col, lo_col of
-// the warp's 32 lanes (no wait).
-__device__ __forceinline__ void et_store_split(uint32_t hi_addr, uint32_t lo_addr, const float (&x)[16]) {
+// Split NV values into TF32 hi and lo halves and store them to consecutive TMEM columns from
+// hi_addr and lo_addr, for the warp's 32 lanes (no wait).
+template <int NV>
+__device__ __forceinline__ void et_store_split(uint32_t hi_addr, uint32_t lo_addr, const float (&x)[NV]) {
 #pragma unroll
-  for (int h8 = 0; h8 < 2; ++h8) {
+  for (int h8 = 0; h8 < NV / 8; ++h8) {
     uint32_t hi[8], lo[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) split_tf32(x[8 * h8 + j], hi[j], lo[j]);
@@ -153,38 +156,48 @@ __device__ __forceinline__ void et_store_split(uint32_t hi_addr, uint32_t lo_add
 // Determinant of R (r <= 16): lane i holds row i in registers; each step takes the largest
 // |value| of column k among the unused rows (ties to the lowest row) as pivot, broadcasts its
 // row and eliminates column k from the other unused rows. The rows are never swapped; the sign
-// of the pivot order is the parity of the unused rows below each pivot.
+// of the pivot order is the parity of the unused rows below each pivot. The steps are expanded
+// by template recursion so that every register index is a compile-time constant.
+struct EtLu {
+  float det;
+  int parity;
+  unsigned unused;
+  bool zero;
+};
+
+template <int K>
+__device__ __forceinline__ void et_lu_step(float (&v)[16], int r, EtLu& st) {
+  if (K < r && !st.zero) {  // uniform
+    const int lane = threadIdx.x & 31;
+    const bool cand = (st.unused >> lane) & 1u;
+    const unsigned key = cand ? __float_as_uint(fabsf(v[K])) : 0u;
+    const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+    st.zero = mx == 0u;  // column K vanishes on every unused row
+    const int p = (__ffs(__ballot_sync(0xffffffffu, cand && key == mx)) - 1) & 31;
+    const float pv = __shfl_sync(0xffffffffu, v[K], p);
+    st.det *= pv;
+    st.parity ^= __popc(st.unused & ((1u << p) - 1u)) & 1;
+    st.unused &= ~(1u << p);
+    const bool upd = (st.unused >> lane) & 1u;
+    const float f = upd ? v[K] * recip(pv) : 0.f;
+#pragma unroll
+    for (int j = K + 1; j < 16; ++j) {
+      const float pj = __shfl_sync(0xffffffffu, v[j], p);
+      if (upd) v[j] = fmaf(-f, pj, v[j]);
+    }
+  }
+  if constexpr (K + 1 < 16) et_lu_step<K + 1>(v, r, st);
+}
+
 __device__ __forceinline__ float et_det16(const float (*R)[kRMax + 1], int r) {
   const int lane = threadIdx.x & 31;
   float v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = (lane < r && j < r) ? R[lane][j] : 0.f;
-  unsigned unused = r >= 32 ? 0xffffffffu : ((1u << r) - 1u);
-  float det = 1.f;
-  int parity = 0;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    if (k >= r) break;
-    const bool cand = (unused >> lane) & 1u;
-    const unsigned key = cand ? __float_as_uint(fabsf(v[k])) : 0u;
-    const unsigned mx = __reduce_max_sync(0xffffffffu, key);
-    if (mx == 0u) return 0.f;  // column k vanishes on every unused row
-    const int p = __ffs(__ballot_sync(0xffffffffu, cand && key == mx)) - 1;
-    const float pv = __shfl_sync(0xffffffffu, v[k], p);
-    det *= pv;
-    parity ^= __popc(unused & ((1u << p) - 1u)) & 1;
-    unused &= ~(1u << p);
-    const bool upd = (unused >> lane) & 1u;
-    const float f = upd ? v[k] * recip(pv) : 0.f;
-#pragma unroll
-    for (int j = k + 1; j < 16; ++j) {
-      if (j < r) {
-        const float pj = __shfl_sync(0xffffffffu, v[j], p);
-        if (upd) v[j] = fmaf(-f, pj, v[j]);
-      }
-    }
-  }
-  return parity ? -det : det;
+  EtLu st{1.f, 0, r >= 32 ? 0xffffffffu : ((1u << r) - 1u), false};
+  et_lu_step<0>(v, r, st);
+  if (st.zero) return 0.f;
+  return st.parity ? -st.det : st.det;
 }
 
 struct EtShared {
@@ -217,16 +230,18 @@ __device__ __forceinline__ void et_issue(uint32_t tmem, const float* wimg, int m
 }
 
 // MLP warps: the site-wise layers of the chunk's batches g0 .. g0 + nb - 1.
+// Phase counters per MMA tile mt = 0, 1 (scalars, so that they stay in registers).
 struct EtMlpState {
-  uint32_t dcnt[2];   // completed phases of dbar[mt] seen by this thread
-  uint32_t acnt[2];   // completed phases of abar[mt] seen by the issuing thread
-  uint32_t issued[2]; // commits issued (issuing thread)
+  uint32_t d0, d1;  // completed phases of dbar[mt] seen by this thread
+  uint32_t a0, a1;  // completed phases of abar[mt] seen by the issuing thread
+  uint32_t i0, i1;  // commits issued (issuing thread)
 };
 
 __device__ void et_mlp(const Net<float>& net, const EtShared& sh, int* err, const float* wimg, float* bbuf,
                        uint32_t tmem, int g0, int nb, EtMlpState& st) {
+  constexpr int HC = kEtCols;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q = warp & 3, col0 = (warp >> 2) * 16;
+  const int q = warp & 3, col0 = (warp >> 2) * HC;
   const uint32_t lrow = (uint32_t)(32 * q) << 16;
   const bool issuer = threadIdx.x == 0;
   const int L = net.L;
@@ -239,12 +254,12 @@ __device__ void et_mlp(const Net<float>& net, const EtShared& sh, int* err, cons
     }
     float* B = bbuf + (size_t)buf * kEtRows * kEtLd;
     // layer-1 input: the staged rows, split into the A halves of both tiles
-#pragma unroll
+#pragma unroll 1
     for (int mt = 0; mt < 2; ++mt) {
       const float4* row = reinterpret_cast<const float4*>(B + (size_t)(mt * 128 + 32 * q + lane) * kEtLd + col0);
-      float x[16];
+      float x[HC];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < HC / 4; ++u) {
         const float4 v = row[u];
         x[4 * u] = v.x;
         x[4 * u + 1] = v.y;
@@ -252,7 +267,7 @@ __device__ void et_mlp(const Net<float>& net, const EtShared& sh, int* err, cons
         x[4 * u + 3] = v.w;
       }
       const uint32_t base = tmem + lrow + mt * kEtTileCols;
-      et_store_split(base + kEtH + col0, base + 2 * kEtH + col0, x);
+      et_store_split<HC>(base + kEtH + col0, base + 2 * kEtH + col0, x);
     }
     tc::tmem_wait_st();
     tc::fence_before_sync();
@@ -260,14 +275,14 @@ __device__ void et_mlp(const Net<float>& net, const EtShared& sh, int* err, cons
     tc::mbar_arrive(&sh.abar[1]);
     if (issuer) {
       for (int mt = 0; mt < 2; ++mt) {
-        if (!tc::mbar_wait(&sh.abar[mt], st.acnt[mt] & 1u, kEtPolls)) {
+        if (!tc::mbar_wait(&sh.abar[mt], (mt ? st.a1 : st.a0) & 1u, kEtPolls)) {
           et_abort(sh, err);
           return;
         }
-        ++st.acnt[mt];
+        if (mt) ++st.a1; else ++st.a0;
         tc::fence_after_sync();
         et_issue(tmem, wimg, mt, 1, &sh.dbar[mt]);
-        ++st.issued[mt];
+        if (mt) ++st.i1; else ++st.i0;
       }
     }
     for (int l = 1; l < L; ++l) {
@@ -275,56 +290,55 @@ __device__ void et_mlp(const Net<float>& net, const EtShared& sh, int* err, cons
       const bool res = net.resid[l] != 0;
 #pragma unroll 1
       for (int mt = 0; mt < 2; ++mt) {
-        if (!tc::mbar_wait(&sh.dbar[mt], st.dcnt[mt] & 1u, kEtPolls)) {
+        if (!tc::mbar_wait(&sh.dbar[mt], (mt ? st.d1 : st.d0) & 1u, kEtPolls)) {
           et_abort(sh, err);
           return;
         }
-        ++st.dcnt[mt];
+        if (mt) ++st.d1; else ++st.d0;
         tc::fence_after_sync();
         const uint32_t base = tmem + lrow + mt * kEtTileCols;
-        uint32_t d0[8], d1[8], h0[8], h1[8], o0[8], o1[8];
-        tc::tmem_ld8_nowait(base + col0, d0);
-        tc::tmem_ld8_nowait(base + col0 + 8, d1);
-        if (res) {  // the layer's input, hi + lo
-          tc::tmem_ld8_nowait(base + kEtH + col0, h0);
-          tc::tmem_ld8_nowait(base + kEtH + col0 + 8, h1);
-          tc::tmem_ld8_nowait(base + 2 * kEtH + col0, o0);
-          tc::tmem_ld8_nowait(base + 2 * kEtH + col0 + 8, o1);
-        }
-        tc::tmem_wait_ld();
-        float y[16];
+        float y[HC];
+        {
+          uint32_t d[HC / 8][8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          y[j] = __uint_as_float(d0[j]) + __ldg(bias + j);
-          y[8 + j] = __uint_as_float(d1[j]) + __ldg(bias + 8 + j);
-        }
-        et_act<16>(net.act, y);
-        if (res) {
+          for (int u = 0; u < HC / 8; ++u) tc::tmem_ld8_nowait(base + col0 + 8 * u, d[u]);
+          tc::tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            y[j] += __uint_as_float(h0[j]) + __uint_as_float(o0[j]);
-            y[8 + j] += __uint_as_float(h1[j]) + __uint_as_float(o1[j]);
+          for (int u = 0; u < HC / 8; ++u)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) y[8 * u + j] = __uint_as_float(d[u][j]) + __ldg(bias + 8 * u + j);
+        }
+        et_act<HC>(net.act, y);
+        if (res) {  // the layer's input, hi + lo, read back from the A columns
+#pragma unroll
+          for (int u = 0; u < HC / 8; ++u) {
+            uint32_t h[8], o[8];
+            tc::tmem_ld8_nowait(base + kEtH + col0 + 8 * u, h);
+            tc::tmem_ld8_nowait(base + 2 * kEtH + col0 + 8 * u, o);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) y[8 * u + j] += __uint_as_float(h[j]) + __uint_as_float(o[j]);
           }
         }
         if (l + 1 < L) {  // the next layer's A operand
-          et_store_split(base + kEtH + col0, base + 2 * kEtH + col0, y);
+          et_store_split<HC>(base + kEtH + col0, base + 2 * kEtH + col0, y);
           tc::tmem_wait_st();
           tc::fence_before_sync();
           tc::mbar_arrive(&sh.abar[mt]);
           if (issuer) {
-            if (!tc::mbar_wait(&sh.abar[mt], st.acnt[mt] & 1u, kEtPolls)) {
+            if (!tc::mbar_wait(&sh.abar[mt], (mt ? st.a1 : st.a0) & 1u, kEtPolls)) {
               et_abort(sh, err);
               return;
             }
-            ++st.acnt[mt];
+            if (mt) ++st.a1; else ++st.a0;
             tc::fence_after_sync();
             et_issue(tmem, wimg, mt, l + 1, &sh.dbar[mt]);
-            ++st.issued[mt];
+            if (mt) ++st.i1; else ++st.i0;
           }
         } else {  // H'(L): the final features of the row
           float4* row = reinterpret_cast<float4*>(B + (size_t)(mt * 128 + 32 * q + lane) * kEtLd + col0);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) row[u] = make_float4(y[4 * u], y[4 * u + 1], y[4 * u + 2], y[4 * u + 3]);
+          for (int u = 0; u < HC / 4; ++u) row[u] = make_float4(y[4 * u], y[4 * u + 1], y[4 * u + 2], y[4 * u + 3]);
         }
       }
     }
@@ -363,61 +377,46 @@ __device__ void et_stage(const LowrankArgs& a, const Net<float>& net, const int8
   }
   if (lane == 0) mt.nS = nS;
   __syncwarp();
-  // z0 of the sites of S
-#pragma unroll 1
-  for (int s0 = 0; s0 < nS; s0 += 6) {
-    float z[6];
-#pragma unroll
-    for (int u = 0; u < 6; ++u) {
-      const int s = s0 + u;
-      z[u] = s < nS ? __ldg(z0b + (size_t)mt.site[s] * kEtH + c) : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < 6; ++u)
-      if (s0 + u < nS) rows[(s0 + u) * kEtLd + c] = z[u];
-  }
-  // layer-0 table deltas: pair p adds KE[t][n'_t][d] - KE[t][n_t][d] to the row of its site
+  // one round of loads: z0 of the sites of S, the layer-0 table deltas of every (touched site,
+  // tap) pair (KE[t][n'_t][d] - KE[t][n_t][d], added to the row of its site) and the residual
+  // embedding rows; then the rows are assembled in shared memory
   const int ts_src = net.per_site ? m.src : 0, ts_dst = net.per_site ? m.dst : 0;
-#pragma unroll 1
-  for (int p0 = 0; p0 < npairs; p0 += 9) {
-    float dv[9];
-    int dr[9];
+  float z[kSMax], e[kSMax], dv[26];
 #pragma unroll
-    for (int u = 0; u < 9; ++u) {
-      const int p = p0 + u;
-      const int rp = __shfl_sync(0xffffffffu, ps, p & 31);
-      dr[u] = p < npairs ? rp : -1;
-      dv[u] = 0.f;
-      if (dr[u] >= 0) {
-        const bool fs = p < kk;
-        const int d = fs ? p : p - kk;
-        const int ts = fs ? ts_src : ts_dst, nn = fs ? n_src_new : n_dst_new, no = fs ? n_src_old : n_dst_old;
-        dv[u] = __ldg(net.KE + (((size_t)ts * 4 + nn) * kk + d) * kEtH + c) -
-                __ldg(net.KE + (((size_t)ts * 4 + no) * kk + d) * kEtH + c);
-      }
+  for (int s = 0; s < kSMax; ++s) {
+    const bool on = s < nS;
+    const int site = on ? mt.site[s] : 0;
+    z[s] = on ? __ldg(z0b + (size_t)site * kEtH + c) : 0.f;
+    e[s] = (on && net.resid[0]) ? __ldg(net.embed + ((size_t)(net.per_site ? site * 4 : 0) + mt.nnew[s]) * kEtH + c)
+                                : 0.f;
+  }
+#pragma unroll
+  for (int p = 0; p < 26; ++p) {
+    const int rp = __shfl_sync(0xffffffffu, ps, p);
+    dv[p] = 0.f;
+    if (p < npairs && rp >= 0) {
+      const bool fs = p < kk;
+      const int d = fs ? p : p - kk;
+      const int ts = fs ? ts_src : ts_dst, nn = fs ? n_src_new : n_dst_new, no = fs ? n_src_old : n_dst_old;
+      dv[p] = __ldg(net.KE + (((size_t)ts * 4 + nn) * kk + d) * kEtH + c) -
+              __ldg(net.KE + (((size_t)ts * 4 + no) * kk + d) * kEtH + c);
     }
+  }
 #pragma unroll
-    for (int u = 0; u < 9; ++u)
-      if (dr[u] >= 0) rows[dr[u] * kEtLd + c] += dv[u];
+  for (int s = 0; s < kSMax; ++s)
+    if (s < nS) rows[s * kEtLd + c] = z[s];
+#pragma unroll
+  for (int p = 0; p < 26; ++p) {
+    const int rp = __shfl_sync(0xffffffffu, ps, p);
+    if (p < npairs && rp >= 0) rows[rp * kEtLd + c] += dv[p];
   }
   // residual embedding + activation
-#pragma unroll 1
-  for (int s0 = 0; s0 < nS; s0 += 6) {
-    float z[6], e[6];
 #pragma unroll
-    for (int u = 0; u < 6; ++u) {
-      const int s = s0 + u;
-      const bool on = s < nS;
-      z[u] = on ? rows[s * kEtLd + c] : 0.f;
-      e[u] = (on && net.resid[0])
-                 ? __ldg(net.embed + ((size_t)(net.per_site ? mt.site[s] * 4 : 0) + mt.nnew[s]) * kEtH + c)
-                 : 0.f;
-    }
-    et_act<6>(net.act, z);
+  for (int s = 0; s < kSMax; ++s) z[s] = s < nS ? rows[s * kEtLd + c] : 0.f;
+  et_act<kSMax>(net.act, z);
 #pragma unroll
-    for (int u = 0; u < 6; ++u)
-      if (s0 + u < nS) rows[(s0 + u) * kEtLd + c] = e[u] + z[u];
-  }
+  for (int s = 0; s < kSMax; ++s)
+    if (s < nS) rows[s * kEtLd + c] = e[s] + z[s];
 }
 
 // Move warp, after the site-wise layers: R of Eq. SMW and det R for one move. rows holds the
@@ -469,38 +468,77 @@ __device__ float et_finish(const LowrankArgs& a, const Net<float>& net, const in
   bad = __any_sync(0xffffffffu, bad);
   __syncwarp();
   if (r > kRMax || bad) return CUDART_NAN_F;
-  // H'(L) - H(L) in place
-#pragma unroll 1
-  for (int s0 = 0; s0 < nS; s0 += 6) {
-    float hl[6];
+  // one round of loads: H(L) of the sites of S and, for r <= 16, 16 channels of Pt[up][c_b] and
+  // Pt[down][c_b] for the lane's column b = lane % 16 (half lane / 16)
+  const int bb = lane & 15, hc = lane >> 4;
+  float hl[kSMax], pu[16], pd[16];
 #pragma unroll
-    for (int u = 0; u < 6; ++u) {
-      const int s = s0 + u;
-      hl[u] = s < nS ? __ldg(HLb + (size_t)mt.site[s] * kEtH + lane) : 0.f;
+  for (int s = 0; s < kSMax; ++s) hl[s] = s < nS ? __ldg(HLb + (size_t)mt.site[s] * kEtH + lane) : 0.f;
+  if (r <= 16) {
+    const int sb = sc.slot[bb < r ? bb : 0];
+    const float4* pu4 = reinterpret_cast<const float4*>(Ptb + (size_t)sb * kEtH + 16 * hc);
+    const float4* pd4 = reinterpret_cast<const float4*>(Ptb + ((size_t)Ne + sb) * kEtH + 16 * hc);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 x = __ldg(pu4 + u), y = __ldg(pd4 + u);
+      pu[4 * u] = x.x; pu[4 * u + 1] = x.y; pu[4 * u + 2] = x.z; pu[4 * u + 3] = x.w;
+      pd[4 * u] = y.x; pd[4 * u + 1] = y.y; pd[4 * u + 2] = y.z; pd[4 * u + 3] = y.w;
     }
-#pragma unroll
-    for (int u = 0; u < 6; ++u)
-      if (s0 + u < nS) rows[(s0 + u) * kEtLd + lane] -= hl[u];
   }
-  __syncwarp();
-  // electrons that kept their orbital: R[a][b] = delta_ab + (H'(L) - H(L))_{s_a} . Pt[s(a)][c_b],
-  // one entry (a, b) per lane at a time
-  const int rr = r * r;
-  for (int q = lane; q < rr; q += 32) {
-    const int aa = q / r, bb = q - aa * r;
-    if (sc.moved[aa]) continue;
-    const float4* x = reinterpret_cast<const float4*>(rows + sc.sidx[aa] * kEtLd);
-    const float4* p = reinterpret_cast<const float4*>(Ptb + ((size_t)(aa >= r_up ? Ne : 0) + sc.slot[bb]) * kEtH);
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  // H'(L) - H(L) in place (the moved electrons' rows add H(L) back below)
 #pragma unroll
-    for (int u = 0; u < kEtH / 4; ++u) {
-      const float4 xv = x[u], pv = __ldg(p + u);
-      s0 = fmaf(xv.x, pv.x, s0);
-      s1 = fmaf(xv.y, pv.y, s1);
-      s2 = fmaf(xv.z, pv.z, s2);
-      s3 = fmaf(xv.w, pv.w, s3);
+  for (int s = 0; s < kSMax; ++s)
+    if (s < nS) rows[s * kEtLd + lane] -= hl[s];
+  __syncwarp();
+  // electrons that kept their orbital: R[a][b] = delta_ab + (H'(L) - H(L))_{s_a} . Pt[s(a)][c_b].
+  // r <= 16: lane (b, half) runs over the rows a with its Pt registers; the halves meet in one
+  // shuffle. Larger r: one entry (a, b) per lane at a time.
+  if (r <= 16) {
+    for (int aa = 0; aa < r; ++aa) {
+      if (sc.moved[aa]) continue;  // uniform
+      const float4* x4 = reinterpret_cast<const float4*>(rows + sc.sidx[aa] * kEtLd + 16 * hc);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      if (aa < r_up) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 xv = x4[u];
+          s0 = fmaf(xv.x, pu[4 * u], s0);
+          s1 = fmaf(xv.y, pu[4 * u + 1], s1);
+          s2 = fmaf(xv.z, pu[4 * u + 2], s2);
+          s3 = fmaf(xv.w, pu[4 * u + 3], s3);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 xv = x4[u];
+          s0 = fmaf(xv.x, pd[4 * u], s0);
+          s1 = fmaf(xv.y, pd[4 * u + 1], s1);
+          s2 = fmaf(xv.z, pd[4 * u + 2], s2);
+          s3 = fmaf(xv.w, pd[4 * u + 3], s3);
+        }
+      }
+      const float part = (s0 + s1) + (s2 + s3);
+      const float tot = part + __shfl_xor_sync(0xffffffffu, part, 16);
+      if (hc == 0 && bb < r) sc.R[aa][bb] = (aa == bb ? 1.f : 0.f) + tot;
     }
-    sc.R[aa][bb] = (aa == bb ? 1.f : 0.f) + ((s0 + s1) + (s2 + s3));
+  } else {
+    const int rr = r * r;
+    for (int q = lane; q < rr; q += 32) {
+      const int aa = q / r, bq = q - aa * r;
+      if (sc.moved[aa]) continue;
+      const float4* x = reinterpret_cast<const float4*>(rows + sc.sidx[aa] * kEtLd);
+      const float4* p = reinterpret_cast<const float4*>(Ptb + ((size_t)(aa >= r_up ? Ne : 0) + sc.slot[bq]) * kEtH);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+      for (int u = 0; u < kEtH / 4; ++u) {
+        const float4 xv = x[u], pv = __ldg(p + u);
+        s0 = fmaf(xv.x, pv.x, s0);
+        s1 = fmaf(xv.y, pv.y, s1);
+        s2 = fmaf(xv.z, pv.z, s2);
+        s3 = fmaf(xv.w, pv.w, s3);
+      }
+      sc.R[aa][bq] = (aa == bq ? 1.f : 0.f) + ((s0 + s1) + (s2 + s3));
+    }
   }
   // moved electrons: R[a][b] = (M0 + b)[o'_a] . Binv[c_b] + H'(L)_{s_a} . Pt[s(a)][c_b]; lanes over
   // the Ne entries of the first dot and the channels of the second, one warp sum per column
@@ -562,7 +600,7 @@ __device__ void et_work(const LowrankArgs& a, const Net<float>& net, const EtArg
       const int m0 = tb * t.mb, mc = min(t.mb, nm - m0);
       for (int j = w; j < mc; j += kEtWork) et_stage(a, net, occ_s, z0b, mlist[m0 + j], B + (size_t)j * t.rpm * kEtLd, M[j]);
       __syncwarp();
-      tc::mbar_arrive(&sh.full[buf]);
+      if (!(t.inject && gg == 0)) tc::mbar_arrive(&sh.full[buf]);
     }
     if (tb >= 1) {
       const int gp = g0 + tb - 1, buf = gp & 1;
@@ -645,7 +683,7 @@ __global__ void __launch_bounds__(kEtThreads, 1) k_eloc_tc(LowrankArgs a, Net<fl
   const float* HLb = (const float*)a.HL + (size_t)b * N * kEtH;
   const float* Binvb = (const float*)a.Binv + (size_t)b * Ne * Ne;
   const float* Ptb = (const float*)a.Pt + (size_t)b * 2 * Ne * kEtH;
-  EtMlpState st{{0u, 0u}, {0u, 0u}, {0u, 0u}};
+  EtMlpState st{0u, 0u, 0u, 0u, 0u, 0u};
   const int ncand = candidate_count(a);
   double total = 0.0;  // thread 0
   int nmoves = 0;
@@ -676,7 +714,8 @@ __global__ void __launch_bounds__(kEtThreads, 1) k_eloc_tc(LowrankArgs a, Net<fl
   // after an early exit, MMAs may still be in flight: wait (bounded) for every commit
   if (tid == 0 && s_abort) {
     for (int mt = 0; mt < 2; ++mt)
-      if (st.issued[mt] > st.dcnt[mt]) tc::mbar_wait(&sh.dbar[mt], (st.issued[mt] - 1) & 1u, kEtPolls);
+      if ((mt ? st.i1 : st.i0) > (mt ? st.d1 : st.d0))
+        tc::mbar_wait(&sh.dbar[mt], ((mt ? st.i1 : st.i0) - 1) & 1u, kEtPolls);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -740,7 +779,9 @@ cudaError_t launch_eloc_tc(scale_ctx* c, double* eloc, const int32_t* list, int 
   a.out = eloc;
   a.move_count = c->move_count;
   a.list = list;
-  EtArgs t{(const float*)c->et_wimg, c->L - 1, c->et_rows, std::min(kEtMaxMoves, kEtRows / c->et_rows), c->ace_err};
+  EtArgs t{(const float*)c->et_wimg, c->L - 1, c->et_rows, std::min(kEtMaxMoves, kEtRows / c->et_rows), c->ace_err,
+           c->et_inject};
+  c->et_inject = 0;  // one-shot
   const EtLayout lay(t.nsw, c->N);
   const size_t smem = lay.total + 128;
   cudaError_t e = cudaFuncSetAttribute(k_eloc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -127,7 +127,6 @@ __device__ __forceinline__ T act_fn(int act, T z) {
   if (act == SCALE_ACT_TANH) return tanh(z);
   return z / (T(1) + exp(-z));
 }
-
 // Activation of the tensor-core layers (FP32): own tanh, SiLU through the FP32 exp.
 __device__ __forceinline__ float act_fast(int act, float z) {
   if (act == SCALE_ACT_TANH) return tanh_f32(z);
@@ -157,6 +156,7 @@ struct scale_ctx {
   bool use_mma = false;     // mixed mode, SCALE layout, h in {16, 32, 64}: site-wise layers on tensor cores
   void* et_wimg = nullptr;  // batched tensor-core local energies (eloc_tc.cu): weight image, or null
   int et_rows = 0;          // rows per move slot of that kernel (largest affected set)
+  int et_inject = 0;        // test hook: leave the next launch's first hand-off unsignalled
   int hpad = 16;            // channel capacity of the per-warp scratch (16, 32 or 64)
   void* wfrag = nullptr;    // hi/lo mma fragments (TF32, or BF16 as an option) of the site-wise layers
   int64_t P = 0;

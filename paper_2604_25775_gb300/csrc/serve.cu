@@ -456,6 +456,30 @@ scale_status scale_server_poll(scale_server* s, uint64_t ticket, scale_result* o
   return SCALE_OK;
 }
 
+scale_status scale_server_cancel(scale_server* s, uint64_t ticket) {
+  if (!s) return SCALE_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->tickets.find((int64_t)ticket);
+  if (it == s->tickets.end() || it->second->done) return SCALE_EINVAL;
+  Ticket* t = it->second;
+  auto drop = [&](std::deque<Ticket*>& q) {
+    auto f = std::find(q.begin(), q.end(), t);
+    if (f == q.end()) return false;
+    q.erase(f);
+    return true;
+  };
+  // queued for routing, for admission, or in its class's queue; a request already in a
+  // batch is in none of them
+  bool found = drop(s->incoming) || drop(s->admit);
+  for (size_t ci = 0; !found && ci < s->cls.size(); ++ci) found = drop(s->cls[ci].queue);
+  if (!found) return SCALE_EINVAL;
+  t->status = SCALE_ECANCELED;
+  t->done = true;
+  t->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - t->t_submit).count();
+  s->cv_done.notify_all();
+  return SCALE_OK;
+}
+
 scale_status scale_server_stats(scale_server* s, scale_server_stats_t* out) {
   if (!s || !out) return SCALE_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);

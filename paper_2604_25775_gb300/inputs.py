@@ -45,6 +45,9 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_MIXED_BF16 = 2
 
+LOWRANK_WARP = 0     # low-rank local-energy kernels of the library (same results)
+LOWRANK_BATCHED = 1
+
 MOVE_NONE = -1
 MOVE_HOP = 0
 MOVE_EXCHANGE = 1
@@ -79,6 +82,7 @@ class Problem:
     h_mlp: int = 0        # ACE: width of the site-wise layers (0 = h)
     ln_eps: float = 1e-5  # ACE: layer-normalisation epsilon
     stencil: int = STENCIL_BOX
+    lowrank_kernel: int = 0  # LOWRANK_WARP or LOWRANK_BATCHED (a kernel choice of the library)
 
     @property
     def N(self) -> int:

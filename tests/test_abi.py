@@ -48,6 +48,7 @@ def test_invalid_descriptors_rejected_on_host():
         I.workload("hubbard_ph8x8").replace(tp=-0.2),    # PHT keeps its form on NN bonds only
         I.workload("hubbard4x4").replace(model=3),       # unknown model
         I.workload("hubbard4x4").replace(family=2),      # unknown network family
+        I.workload("hubbard4x4").replace(lowrank_kernel=2),  # unknown low-rank kernel
         I.workload("ace4x4").replace(n_conv=0),          # ACE without conv blocks
         I.workload("ace4x4").replace(h=300),             # ACE conv width above 256
         I.workload("ace4x4").replace(residual=[1, 1, 0, 0, 0]),  # ACE conv block without residual

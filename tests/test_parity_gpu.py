@@ -284,7 +284,7 @@ def test_local_energy_tensor_core_batched_8x8(variant):
     residual site-wise layers (the layer input read back from TMEM) and SCALE-L's 13-site plus
     stencil (18-row slots). Against the oracle at 1e-4 (cond < 1e3), and bit-identical on a
     second call."""
-    base = I.workload("hubbard8x8").replace(h=32)
+    base = I.workload("hubbard8x8").replace(h=32, lowrank_kernel=I.LOWRANK_BATCHED)
     pb = {
         "torus": base,
         "tp": base.replace(tp=-0.25),
@@ -303,6 +303,24 @@ def test_local_energy_tensor_core_batched_8x8(variant):
     assert np.array_equal(e1, e2, equal_nan=True)
     e_o, _ = ora.local_energy(occ)
     _check(f"tensor-core batched 8x8 {variant}", e1, e_o, cond, MIXED_TOL, 1e3, min_good=1)
+
+
+def test_batched_kernel_16x16_sampled():
+    """The batched tensor-core kernel on the 16x16 workload (1024 walkers): 16 sampled outputs
+    against the oracle in the strict band, and the whole batch against the per-warp kernel."""
+    pb = I.workload("hubbard16x16")
+    pseed, cseed = I.workload_seeds("hubbard16x16")
+    ctx_w, ora, occ, st = setup(pb, 1024, pseed, cseed)
+    ctx_b, _, _, _ = setup(pb.replace(lowrank_kernel=I.LOWRANK_BATCHED), 1024, pseed, cseed)
+    ew = ctx_w.local_energy().cpu().numpy()
+    eb = ctx_b.local_energy().cpu().numpy()
+    pick = np.sort(np.random.default_rng(2).choice(1024, 16, replace=False))
+    cond = conditioning(ora, occ[pick])
+    e_o, _ = ora.local_energy(occ[pick])
+    _check("16x16 batched kernel (sampled)", eb[pick], e_o, cond, MIXED_TOL, 1e4, min_good=3)
+    d = rel_err(eb, ew)
+    print(f"16x16 batched vs per-warp kernel: median {np.median(d):.2e} max {d.max():.2e}")
+    assert np.median(d) <= 1e-5
 
 
 def test_zero_backflow_closed_form_on_gpu():

@@ -102,3 +102,37 @@ def test_oversized_open_rejected():
         srv.open(0, I.random_configs(classes[0][0], 64, 1))
     assert ex.value.status == Bd.EBUDGET
     srv.destroy()
+
+
+def test_poll_timeout_then_completion_and_cancel():
+    """A poll whose bound runs out returns SCALE_ETIMEOUT while the request keeps running, and a
+    later poll collects it; its local energies equal a plain context's. A request still waiting
+    behind its chain's running request is cancelled: the ticket completes with SCALE_ECANCELED
+    and its output is left untouched, the chain's next request runs normally, and a finished
+    (released) ticket cannot be cancelled."""
+    import torch
+    pb = I.workload("hubbard16x16")
+    params, M0 = I.random_params(pb, 52), I.plane_wave_M0(pb)
+    B = 2048
+    occ = I.random_configs(pb, B, 17)
+    srv = Bd.Server([(pb, params, M0, B)])
+    chain = srv.open(0, occ)
+    assert srv.poll(chain, 600_000_000)[0] == Bd.OK
+    e1, e2, e3 = np.zeros(B), np.full(B, 7.0), np.zeros(B)
+    t1 = srv.eloc(chain, e1)  # milliseconds on the GPU
+    t2 = srv.eloc(chain, e2)  # one request per chain per batch: waits behind t1
+    assert srv.poll(t1, 1) is None  # a one-microsecond bound runs out; t1 keeps running
+    assert srv.cancel(t2)
+    r2 = srv.poll(t2, 1_000_000)
+    assert r2 is not None and r2[0] == Bd.ECANCELED
+    r1 = srv.poll(t1, 600_000_000)
+    assert r1 is not None and r1[0] == Bd.OK
+    assert not srv.cancel(t1)  # released by its poll
+    assert (e2 == 7.0).all()
+    t3 = srv.eloc(chain, e3)
+    assert srv.poll(t3, 600_000_000)[0] == Bd.OK
+    np.testing.assert_array_equal(e1, e3)
+    srv.destroy()
+    ctx = Bd.make_context(pb, params, M0, B)
+    ctx.scale_load(torch.from_numpy(occ).cuda())
+    np.testing.assert_array_equal(ctx.local_energy().cpu().numpy(), e1)
