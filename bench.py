@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--full-samples", type=int, default=128)
     ap.add_argument("--cpu-samples", type=int, default=48)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--lowrank-kernel", default="warp", choices=["warp", "batched"],
+                    help="low-rank local-energy kernel of the timed chain step")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--sweep-steps", type=int, default=64)
     ap.add_argument("--sym-walkers", type=int, default=1024)
@@ -61,7 +63,7 @@ def parse():
 # DRAM traffic of the local-energy kernel per walker, from the ncu capture summarised in
 # this file; used only while the kernel sources still hash to the value recorded there.
 ELOC_PROFILE = os.path.join(ROOT, "profiles", "k_eloc_hubbard16x16.md")
-ELOC_SOURCES = ["lowrank.cu", "move.cuh", "mlp_mma.cuh", "scale_internal.cuh"]
+ELOC_SOURCES = ["lowrank.cu", "eloc_common.cuh", "move.cuh", "mlp_mma.cuh", "scale_internal.cuh"]
 
 
 # The shared header contributes only its device part (geometry, parameter view, activation
@@ -303,6 +305,8 @@ def main():
     Bd.load_library(build=True)
 
     pb = I.workload(args.workload)
+    if args.lowrank_kernel == "batched":
+        pb = pb.replace(lowrank_kernel=I.LOWRANK_BATCHED)
     B, K, W = args.batch, args.steps, args.warmup
     plan = replica_plan(rank, world, B)
     params = I.random_params(pb, plan["param_seed"])
@@ -501,6 +505,9 @@ def main():
         line["grad"] = {"walkers": ng, "ms": a.elapsed_time(b2), "params": ctxg.P}
         del g
         ctxg.close()
+        # per-sample gradients at the gradient workload: 16x4 cylinder, 12 residual 3x3 layers
+        from paper_2604_25775_gb300 import next_bench as NB
+        line["grad_cylinder16x4"] = NB.run_grad(2048)
         # symmetry projection over the lattice translations: |G| fresh amplitudes per walker;
         # ACE (no cached update: every psi(n') of a local energy is a fresh forward + LU)
         from paper_2604_25775_gb300 import next_bench

@@ -135,23 +135,23 @@ __global__ void k_slots(Lattice lat, const int8_t* __restrict__ occ, const int32
   }
 }
 
-// The orbital projection in FP64 (weights, bias and reference orbitals of the FP64 parameter
-// copy): the Slater matrix entries are formed in FP64 from the features of either mode.
-struct Proj64 {
+// The orbital projection's parameters in precision TP.
+template <typename TP>
+struct Proj {
   int h;
-  const double* proj_w;  // [h][2Ne]
-  const double* proj_b;  // [2Ne]
-  const double* M0;      // [2N][Ne]
+  const TP* proj_w;  // [h][2Ne]
+  const TP* proj_b;  // [2Ne]
+  const TP* M0;      // [2N][Ne]
 };
 
 // Slater matrix in ascending orbital order (Sec. II.B "Orbital Projection"):
 //   Phi[a][k] = M0[o_a][k] + proj_b[s*Ne+k] + sum_c H(L)_i[c] proj_w[c][s*Ne+k],
-// o_a = s*N + i the a-th occupied orbital, in FP64 from features H(L) of type TH (mixed mode:
-// the FP32 network output). The full-recompute path divides two such determinants, so an
-// FP32 rounding of the entries would not cancel in the ratio as the low-rank update's
-// differences do.
-template <typename TH>
-__global__ void k_phi(Lattice lat, Proj64 net, const int8_t* __restrict__ occ, const int32_t* __restrict__ list,
+// o_a = s*N + i the a-th occupied orbital, from features H(L) of type TH, computed in TP and
+// stored as FP64. The load and the refresh project in the mode's precision; the
+// full-recompute path projects in FP64 (it divides two determinants, where an FP32 rounding
+// of the entries would not cancel as the low-rank update's differences do).
+template <typename TH, typename TP>
+__global__ void k_phi(Lattice lat, Proj<TP> net, const int8_t* __restrict__ occ, const int32_t* __restrict__ list,
                       const TH* __restrict__ HL, double* __restrict__ phi, int B, const int32_t* __restrict__ count) {
   extern __shared__ int sm[];
   const int nrows = count ? min(*count, B) : B;
@@ -172,11 +172,11 @@ __global__ void k_phi(Lattice lat, Proj64 net, const int8_t* __restrict__ occ, c
   for (int q = threadIdx.x; q < Ne * Ne; q += blockDim.x) {
     const int a = q / Ne, k = q - a * Ne;
     const int o = olist[a], s = o / N, i = o - s * N;
-    double v = net.M0[(size_t)o * Ne + k] + net.proj_b[s * Ne + k];
-    const double* w = net.proj_w + s * Ne + k;
+    TP v = net.M0[(size_t)o * Ne + k] + net.proj_b[s * Ne + k];
+    const TP* w = net.proj_w + s * Ne + k;
     const TH* x = Hb + (size_t)i * h;
-    for (int c = 0; c < h; ++c) v += (double)x[c] * w[(size_t)c * 2 * Ne];
-    P[q] = v;
+    for (int c = 0; c < h; ++c) v += (TP)x[c] * w[(size_t)c * 2 * Ne];
+    P[q] = (double)v;
   }
   }
 }
@@ -368,7 +368,7 @@ template Net<float> make_net<float>(scale_ctx*);
 namespace {
 template <typename T>
 cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, bool keep_cache,
-                      double* phi_out, const int32_t* count) {
+                      double* phi_out, const int32_t* count, bool proj64) {
   const Net<T> net = make_net<T>(c);
   const int N = c->N, h = c->h;
   // with a compacted list (count on the device) the kernels loop over its entries from a
@@ -407,10 +407,15 @@ cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* lis
   const size_t smem = sizeof(int) * (2 * N + 257);
   const int Bphi = count ? std::min(B, 1024) : B;
   if (phi_out) {
-    // FP64 projection parameters: the flat FP64 vector at the offsets of make_net
-    const int64_t off_w = (const T*)net.proj_w - (c->fp64 ? (const T*)c->params64 : (const T*)c->params32);
-    const Proj64 p64{c->h, c->params64 + off_w, c->params64 + off_w + (int64_t)c->h * 2 * c->Ne, c->M0_64};
-    k_phi<T><<<Bphi, 256, smem, c->stream>>>(c->lat, p64, occ, list, in, phi_out, B, count);
+    if (proj64 && !c->fp64) {
+      // FP64 projection parameters: the flat FP64 vector at the offsets of make_net
+      const int64_t off_w = (const T*)net.proj_w - (const T*)c->params32;
+      const Proj<double> p64{c->h, c->params64 + off_w, c->params64 + off_w + (int64_t)c->h * 2 * c->Ne, c->M0_64};
+      k_phi<T, double><<<Bphi, 256, smem, c->stream>>>(c->lat, p64, occ, list, in, phi_out, B, count);
+    } else {
+      const Proj<T> pt{c->h, net.proj_w, net.proj_b, net.M0};
+      k_phi<T, T><<<Bphi, 256, smem, c->stream>>>(c->lat, pt, occ, list, in, phi_out, B, count);
+    }
   }
   return cudaGetLastError();
 }
@@ -423,8 +428,8 @@ cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t
     if (list || count || !phi_out) return cudaErrorInvalidValue;
     return launch_ace_forward(c, occ, B, phi_out, nullptr);
   }
-  if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, count);
-  return forward_t<float>(c, occ, B, list, keep_cache, phi_out, count);
+  if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, count, false);
+  return forward_t<float>(c, occ, B, list, keep_cache, phi_out, count, false);
 }
 
 // Forward for the full-recompute path: FP64 Slater matrices of B packed configurations into
@@ -434,8 +439,8 @@ cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t
 cudaError_t launch_forward_phi(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, const int32_t* vcount,
                                double* phi) {
   if (c->ace) return launch_ace_forward(c, occ, B, phi, vcount);
-  if (c->fp64) return forward_t<double>(c, occ, B, list, false, phi, nullptr);
-  return forward_t<float>(c, occ, B, list, false, phi, nullptr);
+  if (c->fp64) return forward_t<double>(c, occ, B, list, false, phi, nullptr, true);
+  return forward_t<float>(c, occ, B, list, false, phi, nullptr, true);
 }
 
 cudaError_t launch_slots(scale_ctx* c, const int8_t* occ, int B) {

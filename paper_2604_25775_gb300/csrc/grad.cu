@@ -109,7 +109,9 @@ __global__ void k_grad_dz(Lattice lat, Net<T> net, int l, const T* __restrict__ 
   }
 }
 
-// dK[d][ci][co] = sum_i in_{i+d}[ci] dz_i[co]
+// dK[d][ci][co] = sum_i in_{i+d}[ci] dz_i[co], accumulated in the mode's precision (FP32 in
+// mixed precision: an FP64 sum would run on GB300's few FP64 units for no accuracy the FP32
+// activations carry)
 template <typename T>
 __global__ void k_grad_kernel(Lattice lat, Net<T> net, int l, int taps, const int8_t* __restrict__ occ,
                               const T* __restrict__ in, const T* __restrict__ dz, int64_t off_k, int64_t P,
@@ -122,21 +124,33 @@ __global__ void k_grad_kernel(Lattice lat, Net<T> net, int l, int taps, const in
   int dx, dy;
   stencil_tap(net.stencil, k, d, dx, dy);
   const int8_t* ob = occ + (size_t)b * N;
-  double acc = 0.0;
+  T acc = T(0);
   for (int i = 0; i < N; ++i) {
     const int j = site_off(lat, i, dx, dy);
     if (j < 0) continue;
     const T xin = (l == 0) ? net.embed[((size_t)(net.per_site ? j * 4 : 0) + (ob[j] & 3)) * h + ci]
                            : in[((size_t)b * N + j) * h + ci];
-    acc += (double)xin * (double)dz[((size_t)b * N + i) * h + co];
+    acc += xin * dz[((size_t)b * N + i) * h + co];
   }
-  grad[(size_t)b * P + off_k + q] = acc;
+  grad[(size_t)b * P + off_k + q] = (double)acc;
 }
 
-// din_j[ci] = res*dout_j[ci] + sum_d sum_co K[d][ci][co] dz_{j-d}[co]
+// KT[d][co][ci] = K[d][ci][co] of one layer (the loads of k_grad_din are then consecutive
+// across the lanes of a warp).
 template <typename T>
-__global__ void k_grad_din(Lattice lat, Net<T> net, int l, const T* __restrict__ dout, const T* __restrict__ dz,
-                           T* __restrict__ din) {
+__global__ void k_transpose_taps(const T* __restrict__ K, int taps, int h, T* __restrict__ KT) {
+  const int total = taps * h * h;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int d = q / (h * h), rem = q - d * h * h, ci = rem / h, co = rem - ci * h;
+    KT[(size_t)d * h * h + (size_t)co * h + ci] = K[q];
+  }
+}
+
+// din_j[ci] = res*dout_j[ci] + sum_d sum_co K[d][ci][co] dz_{j-d}[co]; KT = the layer's
+// kernel transposed per tap ([d][co][ci]).
+template <typename T>
+__global__ void k_grad_din(Lattice lat, Net<T> net, int l, const T* __restrict__ KT, const T* __restrict__ dout,
+                           const T* __restrict__ dz, T* __restrict__ din) {
   const int b = blockIdx.y;
   const int N = lat.N, h = net.h, k = net.ksize[l], r = (k - 1) / 2;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,9 +164,9 @@ __global__ void k_grad_din(Lattice lat, Net<T> net, int l, const T* __restrict__
       const int t = d++;
       const int i = site_off(lat, j, -(kx - r), -(ky - r));  // site i with i + d = j
       if (i < 0) continue;
-      const T* w = net.kernel[l] + (size_t)t * h * h + (size_t)ci * h;
+      const T* w = KT + (size_t)t * h * h + ci;
       const T* g = dz + ((size_t)b * N + i) * h;
-      for (int co = 0; co < h; ++co) acc += w[co] * g[co];
+      for (int co = 0; co < h; ++co) acc += w[(size_t)co * h] * g[co];
     }
   din[(size_t)b * N * h + q] = acc;
 }
@@ -196,7 +210,9 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
   // slabs: checkpoints (layer inputs 1..L-1 at multiples of stride), segment H and z
   // (stride + 1 and stride), dH ping-pong (2), dz (1)
   const int n_ck = (L + stride - 1) / stride;
-  const size_t need = sizeof(T) * slab * (size_t)(n_ck + (stride + 1) + stride + 3);
+  size_t ktaps = 0;  // transposed kernels of every layer
+  for (int l = 0; l < L; ++l) ktaps += (size_t)stencil_taps(net.stencil, net.ksize[l]) * h * h;
+  const size_t need = sizeof(T) * (slab * (size_t)(n_ck + (stride + 1) + stride + 3) + ktaps);
   if (need > c->grad_scratch_bytes) {
     if (c->grad_scratch) cudaFree(c->grad_scratch);
     c->grad_scratch = nullptr;
@@ -212,8 +228,19 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
   T* dA = segZ + (size_t)stride * slab;
   T* dB = dA + slab;
   T* dZ = dB + slab;
+  T* KT = dZ + slab;  // [sum over layers of taps * h * h]
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)B * c->P, c->stream);
   if (e != cudaSuccess) return e;
+  T* KTl[kMaxLayers];
+  {
+    size_t o = 0;
+    for (int l = 0; l < L; ++l) {
+      const int tl = stencil_taps(net.stencil, net.ksize[l]);
+      KTl[l] = KT + o;
+      k_transpose_taps<T><<<(tl * h * h + 255) / 256, 256, 0, c->stream>>>(net.kernel[l], tl, h, KTl[l]);
+      o += (size_t)tl * h * h;
+    }
+  }
   // offsets
   int64_t off = (int64_t)(c->arch.per_site_embed ? N : 1) * 4 * h;
   int64_t offK[kMaxLayers], offB[kMaxLayers];
@@ -259,7 +286,7 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
       const int kq = taps[l] * h * h;
       k_grad_kernel<T><<<dim3((kq + 127) / 128, B), 128, 0, c->stream>>>(c->lat, net, l, taps[l], c->occ, lin, dZ,
                                                                           offK[l], c->P, grad);
-      k_grad_din<T><<<gridL, 128, 0, c->stream>>>(c->lat, net, l, dcur, dZ, dnext);
+      k_grad_din<T><<<gridL, 128, 0, c->stream>>>(c->lat, net, l, KTl[l], dcur, dZ, dnext);
       std::swap(dcur, dnext);
     }
   }

@@ -15,6 +15,10 @@ their own (one GPU, inputs resident on the device, CUDA events on the context's 
     python -m paper_2604_25775_gb300.next_bench symmetry [walkers]
         The symmetry-projected amplitude (App. "Symmetry Projection") over the 256
         translations of the SCALE 16x16 bench workload.
+    python -m paper_2604_25775_gb300.next_bench grad [walkers]
+        Per-sample d log|psi| / d theta on the gradient workload: the 16x4 cylinder (periodic
+        along 16, open along 4), t' = -0.2, 28 + 28, 12 residual 3x3 layers of 32 channels
+        (123,392 parameters), FP64 and mixed precision, with and without recomputation.
 """
 from __future__ import annotations
 
@@ -133,6 +137,36 @@ def run_wide(walkers: int = 8) -> dict:
     return out
 
 
+def run_grad(walkers: int = 2048) -> dict:
+    """Per-sample gradients on the 16x4 cylinder with the 12-layer residual stack, in FP64 and
+    in mixed precision, with the activations kept and with recomputation."""
+    import torch
+    out = {"workload": "cylinder16x4: 16x4 cylinder, t'=-0.2, U=8, 28+28, 12 residual 3x3 layers, h=32",
+           "walkers": walkers}
+    for prec_name, prec in (("fp64", I.PREC_FP64), ("mixed", I.PREC_MIXED)):
+        pb = I.workload("cylinder16x4").replace(precision=prec)
+        pseed, cseed = I.workload_seeds("cylinder16x4")
+        ctx = Bd.make_context(pb, I.random_params(pb, pseed), I.plane_wave_M0(pb), walkers)
+        ctx.scale_load(torch.from_numpy(I.random_configs(pb, walkers, cseed)).cuda())
+        g = torch.empty((walkers, ctx.P), dtype=torch.float64, device="cuda")
+        a, b = _events()
+        for rec in (0, 1):
+            ctx.scale_grad_logpsi(g, rec)  # warm-up (scratch sized on first use)
+            torch.cuda.synchronize()
+            a.record()
+            ctx.scale_grad_logpsi(g, rec)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            out[f"{prec_name}_{'recompute' if rec else 'stored'}_ms"] = ms
+            out[f"{prec_name}_{'recompute' if rec else 'stored'}_grads_per_s"] = walkers / (ms / 1e3)
+        out["params"] = ctx.P
+        out[f"{prec_name}_finite"] = bool(torch.isfinite(g).all().item())
+        del g
+        ctx.close()
+    return out
+
+
 def run_plus(walkers: int = 8192) -> dict:
     """The SCALE chain step's local energies (cached update) on the bench network with
     SCALE-L's 13-site plus stencil in place of the 3x3 box, 16x16 torus."""
@@ -166,5 +200,7 @@ if __name__ == "__main__":
         print(json.dumps(run_wide(n or 8)))
     elif what == "plus":
         print(json.dumps(run_plus(n or 8192)))
+    elif what == "grad":
+        print(json.dumps(run_grad(n or 2048)))
     else:
         print(json.dumps(run_symmetry(n or 1024)))
