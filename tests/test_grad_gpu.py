@@ -41,6 +41,49 @@ def test_grad_mixed_8x8():
     assert err <= 1e-4
 
 
+@pytest.mark.parametrize("recompute", [False, True])
+def test_grad_mixed_cylinder(recompute):
+    """Mixed mode on the gradient workload (16x4 cylinder, 12 residual 3x3 layers, t' = -0.2):
+    within 1e-4 of the FP64 oracle relative to the sample's largest entry for cond(Phi) <= 1e3.
+    The output is filled with NaN first: every entry must be written by the call."""
+    import torch
+    pb = I.workload("cylinder16x4").replace(precision=I.PREC_MIXED)
+    pseed, cseed = I.workload_seeds("cylinder16x4")
+    ctx, ora, occ, st = setup(pb, 32, pseed, cseed)
+    g_d = torch.full((ctx.B, ctx.P), float("nan"), dtype=torch.float64, device="cuda")
+    ctx.scale_grad_logpsi(g_d, recompute)
+    g = g_d.cpu().numpy()
+    ok = st == 0
+    assert np.isfinite(g[ok]).all()
+    g_o = ora.grad_logpsi(occ)
+    cond = conditioning(ora, occ)
+    good = ok & (cond < 1e3)
+    assert good.sum() >= 4
+    scale = np.maximum(np.abs(g_o[good]).max(axis=1, keepdims=True), 1.0)
+    err = (np.abs(g[good] - g_o[good]) / scale).max()
+    print(f"grad mixed cylinder recompute={recompute}: max rel err {err:.3e} ({good.sum()} samples)")
+    assert err <= 1e-4
+
+
+def test_grad_width_not_multiple_of_four_fp64():
+    """h = 6: the per-element kernels (the tiled ones need h % 4 == 0), FP64, against the oracle;
+    NaN-filled output as above."""
+    import torch
+    pb = I.workload("hubbard4x4").replace(h=6)
+    ctx, ora, occ, st = setup(pb, 16, 11, 12)
+    g_d = torch.full((ctx.B, ctx.P), float("nan"), dtype=torch.float64, device="cuda")
+    ctx.scale_grad_logpsi(g_d, False)
+    g = g_d.cpu().numpy()
+    g_o = ora.grad_logpsi(occ)
+    cond = conditioning(ora, occ)
+    good = (st == 0) & (cond < 1e6)
+    assert good.sum() >= 4
+    scale = np.maximum(np.abs(g_o[good]).max(axis=1, keepdims=True), 1.0)
+    err = (np.abs(g[good] - g_o[good]) / scale).max()
+    print(f"grad h=6 fp64: max rel err {err:.3e}")
+    assert err <= 1e-10
+
+
 def test_grad_central_differences_gpu():
     """Central differences (h = 1e-6, FP64) of the GPU log|psi| on 20 random parameters."""
     import torch
