@@ -515,7 +515,7 @@ def main():
             line["symmetry"] = next_bench.run_symmetry(args.sym_walkers)
         if args.ace_walkers > 0:
             line["ace"] = next_bench.run_ace(args.ace_walkers)
-        if args.wide_walkers > 0:  # Table tab:model SCALE-L / SCALE-XL shapes, full recompute
+        if args.wide_walkers > 0:  # Table tab:model SCALE-L / SCALE-XL shapes: full recompute and cached update
             line["wide"] = next_bench.run_wide(args.wide_walkers)
         # the cached update with SCALE-L's plus stencil (bench network otherwise)
         line["plus_stencil"] = next_bench.run_plus(B)

@@ -81,11 +81,13 @@ enum { SCALE_ACT_TANH = 0, SCALE_ACT_SILU = 1 };
  * stack, so ACE has no cached update: scale_load, scale_log_psi, scale_local_energy with
  * SCALE_PATH_FULL and scale_log_psi_sym run it; the low-rank entry points, the gradient,
  * the server and the allocation-free call return SCALE_EUNSUPPORTED. */
-/* SCALE_FAMILY_WIDE: the SCALE layout (one residual k x k conv, then site-wise layers) at the
- * widths of Table tab:model (conv h up to 1024, site-wise h_mlp up to 2048) and with
- * SCALE-L's plus-shaped stencil; without the cached update (the move path holds one channel
- * vector per lane group and one electron per lane, which these shapes exceed), so the same
- * entry points as ACE apply. */
+/* SCALE_FAMILY_WIDE: the SCALE layout (one k x k conv, then site-wise layers) at the widths of
+ * Table tab:model (conv h up to 1024, site-wise h_mlp up to 2048) and with SCALE-L's
+ * plus-shaped stencil. The entry points of ACE apply, and with layer 0 a 3x3 box or a plus
+ * of at most 13 sites (n_conv = 1, kernel size 1 after it) also the cached local energies:
+ * scale_local_energy with SCALE_PATH_LOWRANK, from a cache (layer-0 pre-activations, the
+ * last layer's features, the FP64 inverse and the projector) that scale_load builds. Ratios,
+ * commits, sweeps and refreshes are not offered at these shapes (SCALE_EUNSUPPORTED). */
 enum { SCALE_FAMILY_SCALE = 0, SCALE_FAMILY_ACE = 1, SCALE_FAMILY_WIDE = 2 };
 /* Stencil of the k x k layers: the whole box, or the box offsets within L2 distance
  * (k - 1) / 2 (k = 5: the 13 sites of SCALE-L, Table tab:model); a kernel holds weights for
@@ -226,12 +228,15 @@ scale_status scale_ratios(scale_ctx *ctx, const int32_t *moves, int32_t M, doubl
 /* E_loc [B] (float64) of the loaded samples.
  * path SCALE_PATH_LOWRANK: connected configurations enumerated on the device, each ratio a
  *   rank-r determinant against the cached Phi^-1 after an incremental receptive-field
- *   update of the network (needs k_l = 1 for l >= 1).
+ *   update of the network (needs k_l = 1 for l >= 1). At the wide shapes the affected rows
+ *   of many moves are gathered and the site-wise layers run on them as row GEMMs (chunks of
+ *   moves sized by the context's activation buffers); the call stays asynchronous.
  * path SCALE_PATH_FULL: psi(n) and every psi(n') by a full network forward in the mode's
  *   precision and a fresh FP64 LU with partial pivoting -- the comparison path of
  *   Sec. III.A, any layer layout; nothing cached by the context enters the result. The
- *   configurations run in chunks sized from memory (up to 4096 per chunk), and the call
- *   stays asynchronous (the counts of connected configurations never reach the host). */
+ *   configurations run in chunks of max(max_batch, a memory-sized count of up to 4096), and
+ *   the call stays asynchronous (the counts of connected configurations never reach the
+ *   host). */
 scale_status scale_local_energy(scale_ctx *ctx, int32_t path, double *eloc);
 
 /* Apply one accepted move per sample (moves [B][4] int32, kind -1 = reject): Woodbury

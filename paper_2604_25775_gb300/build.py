@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libscale.so")
-UNITS = ["api.cu", "forward.cu", "dense_inverse.cu", "lowrank.cu", "eloc_tc.cu", "commit.cu", "full.cu", "grad.cu", "serve.cu", "noalloc.cu", "symmetry.cu", "ace.cu"]
+UNITS = ["api.cu", "forward.cu", "dense_inverse.cu", "lowrank.cu", "eloc_tc.cu", "commit.cu", "full.cu", "grad.cu", "serve.cu", "noalloc.cu", "symmetry.cu", "ace.cu", "wide_lowrank.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -671,13 +671,13 @@ bool tc_wide_width(int h) { return h == 384 || h == 640; }
 // multiple of 128 (tiles of 128 columns, two CTAs per SM).
 bool tc_sitewise(int cin, int cout) { return cin % kTcKC == 0 && cout % 128 == 0; }
 
-cudaError_t launch_conv_tc(const scale_ctx* c, bool ln, int cin, int cout, int res, int ks, const float* bimg,
-                           const float* bias, const float* g, const float* be, int act, float eps,
+cudaError_t launch_conv_tc(const scale_ctx* c, const Lattice& lat, bool ln, int cin, int cout, int res, int ks,
+                           const float* bimg, const float* bias, const float* g, const float* be, int act, float eps,
                            const float* in_hi, const float* in_lo, float* out_hi, float* out_lo, long long rows,
                            const int* vcfg) {
   const int st = c->arch.stencil;
 #define SCALE_TC(NT, LNV) \
-  run_conv_tc<NT, LNV>(c->stream, c->lat, bimg, bias, g, be, act, eps, cin, cout, res, ks, st, in_hi, in_lo, \
+  run_conv_tc<NT, LNV>(c->stream, lat, bimg, bias, g, be, act, eps, cin, cout, res, ks, st, in_hi, in_lo, \
                        out_hi, out_lo, rows, c->ace_err, vcfg)
   if (ln) {
     if (cout == 48) return SCALE_TC(48, true);
@@ -859,8 +859,57 @@ bool tc_layer(const scale_ctx* c, int l) {
   return true;
 }
 
+// Layers [l0, l1) on `rows` rows: a holds the input of layer l0 (as (hi, lo) halves of the
+// buffer when split), b is the other buffer; on return *out points at the buffer holding the
+// output of layer l1 - 1 and *out_split tells whether it is split. Rows are the sites of
+// configurations of lat (rows = configurations x lat.N); the site-wise (1 x 1) layers read
+// row r alone, so they also run on a buffer of gathered rows whose lattice is a stand-in.
 template <typename T>
-cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg) {
+cudaError_t ace_layers_t(scale_ctx* c, const Lattice& lat, int l0, int l1, T* a, T* b, long long rows, bool split,
+                         const int* vcfg, T** out, bool* out_split) {
+  const AceNet<T> net = make_ace_net<T>(c);
+  size_t frag_off = 0;
+  for (int l = 0; l < l0; ++l) frag_off += frag_layer_bytes(c->arch, l);
+  for (int l = l0; l < l1; ++l) {
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (split && tc_layer(c, l)) {  // on tcgen05; split output when the next layer is too
+        const float* bimg = (const float*)((const char*)c->ace_frag + frag_off);
+        const long long tin = rows * net.cin[l], tout = rows * net.cout[l];
+        float* olo = (l + 1 < l1 && tc_layer(c, l + 1)) ? b + tout : nullptr;
+        const cudaError_t e =
+            launch_conv_tc(c, lat, net.ln_g[l] != nullptr, net.cin[l], net.cout[l], c->arch.residual[l], net.ks[l],
+                           bimg, net.bias[l], net.ln_g[l], net.ln_b[l], net.act, (float)net.eps, a, a + tin, b, olo,
+                           rows, vcfg);
+        if (e != cudaSuccess) return e;
+        split = olo != nullptr;
+        done = true;
+      } else if (c->ace_mma) {
+        const MmaPlan p = plan_of(c->arch, l);
+        const WFrag* frag = (const WFrag*)((const char*)c->ace_frag + frag_off);
+        done = launch_mma_layer(c->stream, lat, p, net.ln_g[l] != nullptr, frag, net.bias[l], net.ln_g[l],
+                                net.ln_b[l], net.ks[l], net.stencil, net.cin[l], c->arch.residual[l], net.act,
+                                (float)net.eps, a, b, rows, vcfg);
+      }
+    }
+    if (!done) {
+      const long long blocks = (rows + kAceRowsGeneric - 1) / kAceRowsGeneric;
+      k_ace_layer<T><<<(unsigned)blocks, 32 * kAceRowsGeneric, 0, c->stream>>>(
+          lat, net.kernel[l], net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l], net.stencil, net.cin[l],
+          net.cout[l], c->arch.residual[l], net.act, net.eps, a, b, rows, vcfg);
+    }
+    frag_off += frag_layer_bytes(c->arch, l);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::swap(a, b);
+  }
+  *out = a;
+  *out_split = split;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg, void* hl_out) {
   const AceNet<T> net = make_ace_net<T>(c);
   const int N = c->N;
   const long long rows = (long long)C * N;
@@ -877,47 +926,20 @@ cudaError_t ace_forward_t(scale_ctx* c, const int8_t* occ, int C, double* phi64,
     }
   }
   if (!split) k_ace_embed<T><<<eblocks, 256, 0, c->stream>>>(N, c->h, net.per_site, net.embed, occ, total, a, vcfg);
-  size_t frag_off = 0;
-  for (int l = 0; l < c->L; ++l) {
-    const bool conv = l < net.n_conv;
-    bool done = false;
-    if constexpr (sizeof(T) == 4) {
-      if (split && tc_layer(c, l)) {  // on tcgen05; split output when the next layer is too
-        const float* bimg = (const float*)((const char*)c->ace_frag + frag_off);
-        const long long tin = rows * net.cin[l], tout = rows * net.cout[l];
-        float* olo = (l + 1 < c->L && tc_layer(c, l + 1)) ? b + tout : nullptr;
-        const cudaError_t e =
-            launch_conv_tc(c, net.ln_g[l] != nullptr, net.cin[l], net.cout[l], c->arch.residual[l], net.ks[l], bimg,
-                           net.bias[l], net.ln_g[l], net.ln_b[l], net.act, (float)net.eps, a, a + tin, b, olo, rows,
-                           vcfg);
-        if (e != cudaSuccess) return e;
-        split = olo != nullptr;
-        done = true;
-      } else if (c->ace_mma) {
-        const MmaPlan p = plan_of(c->arch, l);
-        const WFrag* frag = (const WFrag*)((const char*)c->ace_frag + frag_off);
-        done = launch_mma_layer(c->stream, c->lat, p, net.ln_g[l] != nullptr, frag, net.bias[l], net.ln_g[l],
-                                net.ln_b[l], net.ks[l], net.stencil, net.cin[l], c->arch.residual[l], net.act,
-                                (float)net.eps, a, b, rows, vcfg);
-      }
-    }
-    if (!done) {
-      const long long blocks = (rows + kAceRowsGeneric - 1) / kAceRowsGeneric;
-      k_ace_layer<T><<<(unsigned)blocks, 32 * kAceRowsGeneric, 0, c->stream>>>(
-          c->lat, net.kernel[l], net.bias[l], net.ln_g[l], net.ln_b[l], net.ks[l], net.stencil, net.cin[l],
-          net.cout[l], c->arch.residual[l], net.act, net.eps, a, b, rows, vcfg);
-    }
-    frag_off += frag_layer_bytes(c->arch, l);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    std::swap(a, b);
-  }
+  T* hL = nullptr;
+  bool hsplit = false;
+  cudaError_t e = ace_layers_t<T>(c, c->lat, 0, c->L, a, b, rows, split, vcfg, &hL, &hsplit);
+  if (e != cudaSuccess) return e;
   const int hl = net.cout[c->L - 1];
+  if (hl_out) {  // the last layer's features (plain rows: the last layer never writes a split)
+    e = cudaMemcpyAsync(hl_out, hL, sizeof(T) * (size_t)rows * hl, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+  }
   const int Ne = c->Ne;
   const dim3 pgrid((c->sys.n_up + kPhiT - 1) / kPhiT + (c->sys.n_dn + kPhiT - 1) / kPhiT, (Ne + kPhiT - 1) / kPhiT, C);
-  cudaError_t e = cudaFuncSetAttribute(k_ace_phi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * 2 * N));
+  e = cudaFuncSetAttribute(k_ace_phi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * 2 * N));
   if (e != cudaSuccess) return e;
-  k_ace_phi<T><<<pgrid, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, a, c->ace_err, phi64, vcfg);
+  k_ace_phi<T><<<pgrid, 256, sizeof(int) * 2 * N, c->stream>>>(c->lat, net, hl, occ, hL, c->ace_err, phi64, vcfg);
   return cudaGetLastError();
 }
 
@@ -978,10 +1000,22 @@ cudaError_t launch_ace_build(scale_ctx* c) {
 // Slater matrices (FP64) of C configurations occ[C][N] through the ACE network; the
 // activations go to the context's scratch buffers. vcfg (optional, device): only the first
 // *vcfg configurations are evaluated (the rest of the launch returns at once).
-cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg) {
+cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg,
+                               void* hl_out) {
   if (C <= 0) return cudaSuccess;
-  if (c->fp64) return ace_forward_t<double>(c, occ, C, phi64, vcfg);
-  return ace_forward_t<float>(c, occ, C, phi64, vcfg);
+  if (c->fp64) return ace_forward_t<double>(c, occ, C, phi64, vcfg, hl_out);
+  return ace_forward_t<float>(c, occ, C, phi64, vcfg, hl_out);
 }
+
+// Layers [l0, l1) on a buffer of rows (see ace_layers_t); *out receives the buffer of the
+// last output.
+cudaError_t launch_ace_layers(scale_ctx* c, const Lattice& lat, int l0, int l1, void* a, void* b, long long rows,
+                              bool split, const int* vcfg, void** out) {
+  bool os = false;
+  if (c->fp64) return ace_layers_t<double>(c, lat, l0, l1, (double*)a, (double*)b, rows, false, vcfg, (double**)out, &os);
+  return ace_layers_t<float>(c, lat, l0, l1, (float*)a, (float*)b, rows, split, vcfg, (float**)out, &os);
+}
+
+bool ace_tc_layer(const scale_ctx* c, int l) { return tc_layer(c, l); }
 
 }  // namespace scale

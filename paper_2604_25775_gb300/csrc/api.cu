@@ -145,13 +145,17 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   size_t t = 0;
   t += P * 8 + (T == 4 ? P * 4 : 0);
   t += 2 * N * Ne * 8 + (T == 4 ? 2 * N * Ne * 4 : 0) + 2 * N * Ne * T;
-  t += ace ? 16 : (a->per_site_embed ? N : 1) * 4 * stencil_taps(a->stencil, (int)k0) * h * T;  // KE
+  // the cached update: narrow SCALE, or the wide shapes with a layer layout it covers
+  const bool cached = !ace || wide_lowrank_shapes(*a);
+  const size_t hl = ace ? (size_t)ace_width_out(*a, a->n_layers - 1) : h;  // width of H(L)
+  t += cached ? (a->per_site_embed ? N : 1) * 4 * stencil_taps(a->stencil, (int)k0) * h * T : 16;  // KE
   t += (nb_nn + nb_nnn) * 2 * 4;
   t += (size_t)B * (N + Ne * 4 + 2 * N * 4);
-  t += ace ? 32 : (size_t)B * N * h * T * 2;  // z0, HL
-  t += FC * N * hmax * T * 2;                 // act_a, act_b
-  t += ace ? 16 : (size_t)B * Ne * Ne * T;    // Binv
-  t += ace ? 16 : (size_t)B * 2 * Ne * h * T; // Pt
+  t += cached ? (size_t)B * N * (h + hl) * T : 32;  // z0, HL
+  t += FC * N * hmax * T * 2;                       // act_a, act_b
+  t += cached ? (size_t)B * Ne * Ne * T : 16;       // Binv
+  t += cached ? (size_t)B * 2 * Ne * hl * T : 16;   // Pt
+  if (ace && cached) t += (FC * N / (size_t)wide_rows_per_move(*s, *a) + 1) * wide_meta_bytes();  // move records
   t += (size_t)B * (8 + 4 + 4 + 4 + 8 + 4 + 4 + 8 + 4 + 8);
   t += FC * Ne * Ne * 8;                   // Phi64
   t += ace ? 16 : (size_t)B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T;  // commit scratch
@@ -197,7 +201,7 @@ void free_all(scale_ctx* c) {
                   c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_la_all, c->full_sg_all,
                   c->full_list, c->full_vcount, c->full_moves,
                   c->commit_scratch, c->la_tmp, c->sg_tmp, c->full_la, c->full_sg, c->full_diag,
-                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag, c->ace_err, c->et_wimg};
+                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag, c->ace_err, c->et_wimg, c->wl_meta};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -217,8 +221,10 @@ scale_status check_loaded(scale_ctx* c) {
 
 scale_status require_lowrank(scale_ctx* c) {
   if (c->ace) {
-    c->err = "this network family (ACE, or SCALE at the wide shapes) has no cached update: use the "
-             "full-recompute path";
+    c->err = c->wide_lr ? "the wide SCALE shapes offer the cached local energies only (no ratios, commits, "
+                          "sweeps or refreshes): use scale_local_energy"
+                        : "this network family (ACE, or a wide layout without the SCALE layer pattern) has no "
+                          "cached update: use the full-recompute path";
     return SCALE_EUNSUPPORTED;
   }
   if (!c->lowrank_ok) {
@@ -296,9 +302,10 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   c->hmax = c->ace ? std::max(c->h, ace_width_out(*arch, c->L - 1)) : c->h;
   c->ace_mma = c->ace && !c->fp64 && ace_mma_shapes(*arch);
   c->ace_tc = c->ace_mma && ace_tc_shapes(*arch);
+  c->wide_lr = c->ace && wide_lowrank_shapes(*arch);  // the cached local energies at the wide shapes
   std::vector<int32_t> bonds = make_bonds(c->lat, &c->nb_nn, &c->nb_nnn);
   c->max_moves = 2 * (c->nb_nn + c->nb_nnn) + (sys->model == SCALE_MODEL_TJ ? c->nb_nn : 0);
-  c->full_chunk = sz.full_chunk;
+  c->full_chunk = (int)sz.fc;  // the chunk buffers hold FC configurations: use all of them
   const size_t B = max_batch, N = c->N, Ne = c->Ne, h = c->h, T = c->fp64 ? 8 : 4;
   const size_t FC = sz.fc;
   const size_t Ns = arch->per_site_embed ? N : 1;
@@ -313,16 +320,23 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   if (!c->fp64) A(&c->M0_32, 2 * N * Ne * 4);
   A((char**)&c->M0b, 2 * N * Ne * T);
   const bool ace = c->ace;
+  const bool cached = !ace || c->wide_lr;
   const size_t hmax = ace ? (c->fp64 ? 1 : 2) * (size_t)c->hmax : h;  // mixed: (hi, lo) halves
-  A((char**)&c->KE, ace ? 16 : Ns * 4 * stencil_taps(arch->stencil, c->k0) * h * T);
+  const size_t hl = ace ? (size_t)ace_width_out(*arch, c->L - 1) : h;  // width of H(L)
+  A((char**)&c->KE, cached ? Ns * 4 * stencil_taps(arch->stencil, c->k0) * h * T : 16);
   A(&c->bonds, std::max<size_t>(bonds.size(), 2) * 4);
   A(&c->occ, B * N);
   A(&c->orb_of_slot, B * Ne * 4);
   A(&c->slot_of_orb, B * 2 * N * 4);
-  A((char**)&c->z0, ace ? 16 : B * N * h * T);
-  A((char**)&c->HL, ace ? 16 : B * N * h * T);
-  A((char**)&c->Binv, ace ? 16 : B * Ne * Ne * T);
-  A((char**)&c->Pt, ace ? 16 : B * 2 * Ne * h * T);
+  A((char**)&c->z0, cached ? B * N * h * T : 16);
+  A((char**)&c->HL, cached ? B * N * hl * T : 16);
+  A((char**)&c->Binv, cached ? B * Ne * Ne * T : 16);
+  A((char**)&c->Pt, cached ? B * 2 * Ne * hl * T : 16);
+  if (c->wide_lr) {  // moves per chunk: their row slots fill the activation buffers
+    c->wl_rows = wide_rows_per_move(*sys, *arch);
+    c->wl_chunk = (int)std::min<size_t>((FC * N) / (size_t)c->wl_rows, (size_t)1 << 20);
+    A((char**)&c->wl_meta, ((size_t)c->wl_chunk + 1) * wide_meta_bytes());
+  }
   A(&c->logabs, B * 8);
   A(&c->sign_slot, B * 4);
   A(&c->status, B * 4);
@@ -402,8 +416,9 @@ scale_status scale_set_params(scale_ctx* c, const double* params, const double* 
     k_convert<float, double><<<1024, 256, 0, c->stream>>>(c->M0_64, c->M0_32, 2 * N * Ne);
     SCALE_TRY(c, cudaGetLastError());
   }
-  if (c->ace) {  // no cached update (ACE, wide SCALE): only the tensor-core fragments
+  if (c->ace) {  // the tensor-core fragments; the wide shapes' layer-0 table and M0 + proj_b
     SCALE_TRY(c, launch_ace_build(c));
+    if (c->wide_lr) SCALE_TRY(c, launch_wide_params(c));
     c->params_set = true;
     c->B = 0;
     return SCALE_OK;
@@ -439,7 +454,10 @@ scale_status scale_load(scale_ctx* c, const int8_t* occ, int32_t B, int32_t* sam
   SCALE_TRY(c, cudaMemsetAsync(c->drift, 0, (size_t)B * 8, c->stream));
   SCALE_TRY(c, launch_slots(c, c->occ, B));
   SCALE_TRY(c, launch_forward(c, c->occ, B, nullptr, true, c->Phi64));
-  if (c->ace) {  // log|det| and sign only (FP64 LU); nothing is cached for updates
+  if (c->wide_lr) {  // the wide cache: FP64 inverse, z0 from the layer-0 table, Pt = W Phi^-1
+    SCALE_TRY(c, launch_gj(c, c->Phi64, c->Ne, B, nullptr, true, c->fp64, c->Binv, c->logabs, c->sign_slot, c->status));
+    SCALE_TRY(c, launch_wide_cache(c, B));
+  } else if (c->ace) {  // log|det| and sign only (FP64 LU); nothing is cached for updates
     SCALE_TRY(c, launch_gj(c, c->Phi64, c->Ne, B, nullptr, false, true, nullptr, c->logabs, c->sign_slot, c->status));
   } else {
     SCALE_TRY(c, launch_gj(c, c->Phi64, c->Ne, B, nullptr, true, c->fp64, c->Binv, c->logabs, c->sign_slot, c->status));
@@ -480,8 +498,12 @@ scale_status scale_local_energy(scale_ctx* c, int32_t path, double* eloc) {
   if (s != SCALE_OK) return s;
   if (!eloc) return SCALE_EINVAL;
   if (path == SCALE_PATH_LOWRANK) {
-    if ((s = require_lowrank(c)) != SCALE_OK) return s;
-    SCALE_TRY(c, launch_eloc_lowrank(c, eloc));
+    if (c->wide_lr) {
+      SCALE_TRY(c, launch_wide_eloc(c, eloc));
+    } else {
+      if ((s = require_lowrank(c)) != SCALE_OK) return s;
+      SCALE_TRY(c, launch_eloc_lowrank(c, eloc));
+    }
     c->stats.n_eloc += c->B;
   } else if (path == SCALE_PATH_FULL) {
     SCALE_TRY(c, launch_eloc_full(c, eloc));

@@ -377,46 +377,61 @@ __device__ void et_stage(const LowrankArgs& a, const Net<float>& net, const int8
   }
   if (lane == 0) mt.nS = nS;
   __syncwarp();
-  // one round of loads: z0 of the sites of S, the layer-0 table deltas of every (touched site,
-  // tap) pair (KE[t][n'_t][d] - KE[t][n_t][d], added to the row of its site) and the residual
-  // embedding rows; then the rows are assembled in shared memory
-  const int ts_src = net.per_site ? m.src : 0, ts_dst = net.per_site ? m.dst : 0;
-  float z[kSMax], e[kSMax], dv[26];
+  // z0 of the sites of S
+#pragma unroll 1
+  for (int s0 = 0; s0 < nS; s0 += 6) {
+    float z[6];
 #pragma unroll
-  for (int s = 0; s < kSMax; ++s) {
-    const bool on = s < nS;
-    const int site = on ? mt.site[s] : 0;
-    z[s] = on ? __ldg(z0b + (size_t)site * kEtH + c) : 0.f;
-    e[s] = (on && net.resid[0]) ? __ldg(net.embed + ((size_t)(net.per_site ? site * 4 : 0) + mt.nnew[s]) * kEtH + c)
-                                : 0.f;
-  }
-#pragma unroll
-  for (int p = 0; p < 26; ++p) {
-    const int rp = __shfl_sync(0xffffffffu, ps, p);
-    dv[p] = 0.f;
-    if (p < npairs && rp >= 0) {
-      const bool fs = p < kk;
-      const int d = fs ? p : p - kk;
-      const int ts = fs ? ts_src : ts_dst, nn = fs ? n_src_new : n_dst_new, no = fs ? n_src_old : n_dst_old;
-      dv[p] = __ldg(net.KE + (((size_t)ts * 4 + nn) * kk + d) * kEtH + c) -
-              __ldg(net.KE + (((size_t)ts * 4 + no) * kk + d) * kEtH + c);
+    for (int u = 0; u < 6; ++u) {
+      const int s = s0 + u;
+      z[u] = s < nS ? __ldg(z0b + (size_t)mt.site[s] * kEtH + c) : 0.f;
     }
+#pragma unroll
+    for (int u = 0; u < 6; ++u)
+      if (s0 + u < nS) rows[(s0 + u) * kEtLd + c] = z[u];
   }
+  // layer-0 table deltas: pair p adds KE[t][n'_t][d] - KE[t][n_t][d] to the row of its site
+  const int ts_src = net.per_site ? m.src : 0, ts_dst = net.per_site ? m.dst : 0;
+#pragma unroll 1
+  for (int p0 = 0; p0 < npairs; p0 += 9) {
+    float dv[9];
+    int dr[9];
 #pragma unroll
-  for (int s = 0; s < kSMax; ++s)
-    if (s < nS) rows[s * kEtLd + c] = z[s];
+    for (int u = 0; u < 9; ++u) {
+      const int p = p0 + u;
+      const int rp = __shfl_sync(0xffffffffu, ps, p & 31);
+      dr[u] = p < npairs ? rp : -1;
+      dv[u] = 0.f;
+      if (dr[u] >= 0) {
+        const bool fs = p < kk;
+        const int d = fs ? p : p - kk;
+        const int ts = fs ? ts_src : ts_dst, nn = fs ? n_src_new : n_dst_new, no = fs ? n_src_old : n_dst_old;
+        dv[u] = __ldg(net.KE + (((size_t)ts * 4 + nn) * kk + d) * kEtH + c) -
+                __ldg(net.KE + (((size_t)ts * 4 + no) * kk + d) * kEtH + c);
+      }
+    }
 #pragma unroll
-  for (int p = 0; p < 26; ++p) {
-    const int rp = __shfl_sync(0xffffffffu, ps, p);
-    if (p < npairs && rp >= 0) rows[rp * kEtLd + c] += dv[p];
+    for (int u = 0; u < 9; ++u)
+      if (dr[u] >= 0) rows[dr[u] * kEtLd + c] += dv[u];
   }
   // residual embedding + activation
+#pragma unroll 1
+  for (int s0 = 0; s0 < nS; s0 += 6) {
+    float z[6], e[6];
 #pragma unroll
-  for (int s = 0; s < kSMax; ++s) z[s] = s < nS ? rows[s * kEtLd + c] : 0.f;
-  et_act<kSMax>(net.act, z);
+    for (int u = 0; u < 6; ++u) {
+      const int s = s0 + u;
+      const bool on = s < nS;
+      z[u] = on ? rows[s * kEtLd + c] : 0.f;
+      e[u] = (on && net.resid[0])
+                 ? __ldg(net.embed + ((size_t)(net.per_site ? mt.site[s] * 4 : 0) + mt.nnew[s]) * kEtH + c)
+                 : 0.f;
+    }
+    et_act<6>(net.act, z);
 #pragma unroll
-  for (int s = 0; s < kSMax; ++s)
-    if (s < nS) rows[s * kEtLd + c] = e[s] + z[s];
+    for (int u = 0; u < 6; ++u)
+      if (s0 + u < nS) rows[(s0 + u) * kEtLd + c] = e[u] + z[u];
+  }
 }
 
 // Move warp, after the site-wise layers: R of Eq. SMW and det R for one move. rows holds the
@@ -468,77 +483,38 @@ __device__ float et_finish(const LowrankArgs& a, const Net<float>& net, const in
   bad = __any_sync(0xffffffffu, bad);
   __syncwarp();
   if (r > kRMax || bad) return CUDART_NAN_F;
-  // one round of loads: H(L) of the sites of S and, for r <= 16, 16 channels of Pt[up][c_b] and
-  // Pt[down][c_b] for the lane's column b = lane % 16 (half lane / 16)
-  const int bb = lane & 15, hc = lane >> 4;
-  float hl[kSMax], pu[16], pd[16];
+  // H'(L) - H(L) in place
+#pragma unroll 1
+  for (int s0 = 0; s0 < nS; s0 += 6) {
+    float hl[6];
 #pragma unroll
-  for (int s = 0; s < kSMax; ++s) hl[s] = s < nS ? __ldg(HLb + (size_t)mt.site[s] * kEtH + lane) : 0.f;
-  if (r <= 16) {
-    const int sb = sc.slot[bb < r ? bb : 0];
-    const float4* pu4 = reinterpret_cast<const float4*>(Ptb + (size_t)sb * kEtH + 16 * hc);
-    const float4* pd4 = reinterpret_cast<const float4*>(Ptb + ((size_t)Ne + sb) * kEtH + 16 * hc);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float4 x = __ldg(pu4 + u), y = __ldg(pd4 + u);
-      pu[4 * u] = x.x; pu[4 * u + 1] = x.y; pu[4 * u + 2] = x.z; pu[4 * u + 3] = x.w;
-      pd[4 * u] = y.x; pd[4 * u + 1] = y.y; pd[4 * u + 2] = y.z; pd[4 * u + 3] = y.w;
+    for (int u = 0; u < 6; ++u) {
+      const int s = s0 + u;
+      hl[u] = s < nS ? __ldg(HLb + (size_t)mt.site[s] * kEtH + lane) : 0.f;
     }
+#pragma unroll
+    for (int u = 0; u < 6; ++u)
+      if (s0 + u < nS) rows[(s0 + u) * kEtLd + lane] -= hl[u];
   }
-  // H'(L) - H(L) in place (the moved electrons' rows add H(L) back below)
-#pragma unroll
-  for (int s = 0; s < kSMax; ++s)
-    if (s < nS) rows[s * kEtLd + lane] -= hl[s];
   __syncwarp();
-  // electrons that kept their orbital: R[a][b] = delta_ab + (H'(L) - H(L))_{s_a} . Pt[s(a)][c_b].
-  // r <= 16: lane (b, half) runs over the rows a with its Pt registers; the halves meet in one
-  // shuffle. Larger r: one entry (a, b) per lane at a time.
-  if (r <= 16) {
-    for (int aa = 0; aa < r; ++aa) {
-      if (sc.moved[aa]) continue;  // uniform
-      const float4* x4 = reinterpret_cast<const float4*>(rows + sc.sidx[aa] * kEtLd + 16 * hc);
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      if (aa < r_up) {
+  // electrons that kept their orbital: R[a][b] = delta_ab + (H'(L) - H(L))_{s_a} . Pt[s(a)][c_b],
+  // one entry (a, b) per lane at a time
+  const int rr = r * r;
+  for (int q = lane; q < rr; q += 32) {
+    const int aa = q / r, bb = q - aa * r;
+    if (sc.moved[aa]) continue;
+    const float4* x = reinterpret_cast<const float4*>(rows + sc.sidx[aa] * kEtLd);
+    const float4* p = reinterpret_cast<const float4*>(Ptb + ((size_t)(aa >= r_up ? Ne : 0) + sc.slot[bb]) * kEtH);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 xv = x4[u];
-          s0 = fmaf(xv.x, pu[4 * u], s0);
-          s1 = fmaf(xv.y, pu[4 * u + 1], s1);
-          s2 = fmaf(xv.z, pu[4 * u + 2], s2);
-          s3 = fmaf(xv.w, pu[4 * u + 3], s3);
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 xv = x4[u];
-          s0 = fmaf(xv.x, pd[4 * u], s0);
-          s1 = fmaf(xv.y, pd[4 * u + 1], s1);
-          s2 = fmaf(xv.z, pd[4 * u + 2], s2);
-          s3 = fmaf(xv.w, pd[4 * u + 3], s3);
-        }
-      }
-      const float part = (s0 + s1) + (s2 + s3);
-      const float tot = part + __shfl_xor_sync(0xffffffffu, part, 16);
-      if (hc == 0 && bb < r) sc.R[aa][bb] = (aa == bb ? 1.f : 0.f) + tot;
+    for (int u = 0; u < kEtH / 4; ++u) {
+      const float4 xv = x[u], pv = __ldg(p + u);
+      s0 = fmaf(xv.x, pv.x, s0);
+      s1 = fmaf(xv.y, pv.y, s1);
+      s2 = fmaf(xv.z, pv.z, s2);
+      s3 = fmaf(xv.w, pv.w, s3);
     }
-  } else {
-    const int rr = r * r;
-    for (int q = lane; q < rr; q += 32) {
-      const int aa = q / r, bq = q - aa * r;
-      if (sc.moved[aa]) continue;
-      const float4* x = reinterpret_cast<const float4*>(rows + sc.sidx[aa] * kEtLd);
-      const float4* p = reinterpret_cast<const float4*>(Ptb + ((size_t)(aa >= r_up ? Ne : 0) + sc.slot[bq]) * kEtH);
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-      for (int u = 0; u < kEtH / 4; ++u) {
-        const float4 xv = x[u], pv = __ldg(p + u);
-        s0 = fmaf(xv.x, pv.x, s0);
-        s1 = fmaf(xv.y, pv.y, s1);
-        s2 = fmaf(xv.z, pv.z, s2);
-        s3 = fmaf(xv.w, pv.w, s3);
-      }
-      sc.R[aa][bq] = (aa == bq ? 1.f : 0.f) + ((s0 + s1) + (s2 + s3));
-    }
+    sc.R[aa][bb] = (aa == bb ? 1.f : 0.f) + ((s0 + s1) + (s2 + s3));
   }
   // moved electrons: R[a][b] = (M0 + b)[o'_a] . Binv[c_b] + H'(L)_{s_a} . Pt[s(a)][c_b]; lanes over
   // the Ne entries of the first dot and the channels of the second, one warp sum per column

@@ -424,9 +424,9 @@ cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* lis
 // Forward every listed sample of occ; keep_cache writes z0 / HL of the context.
 cudaError_t launch_forward(scale_ctx* c, const int8_t* occ, int B, const int32_t* list, bool keep_cache,
                            double* phi_out, const int32_t* count) {
-  if (c->ace) {  // ACE: no cached features; whole batches only (no list)
+  if (c->ace) {  // ACE / wide: whole batches only (no list); the wide cache keeps H(L)
     if (list || count || !phi_out) return cudaErrorInvalidValue;
-    return launch_ace_forward(c, occ, B, phi_out, nullptr);
+    return launch_ace_forward(c, occ, B, phi_out, nullptr, keep_cache && c->wide_lr ? c->HL : nullptr);
   }
   if (c->fp64) return forward_t<double>(c, occ, B, list, keep_cache, phi_out, count, false);
   return forward_t<float>(c, occ, B, list, keep_cache, phi_out, count, false);

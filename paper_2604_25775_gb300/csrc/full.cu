@@ -101,17 +101,18 @@ __global__ void k_enum(Lattice lat, const int8_t* __restrict__ occ, const int32_
   count[b] = min(n, cap);
 }
 
-// offsets[b] = sum_{b' < b} (count[b'] + 1), offsets[B] = the total: one CTA, each thread
-// scans a contiguous run of samples, then a scan over the threads' sums.
+// offsets[b] = sum_{b' < b} (count[b'] + extra), offsets[B] = the total (extra = 1 here: entry 0
+// of a sample is n itself): one CTA, each thread scans a contiguous run of samples, then a
+// scan over the threads' sums.
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) k_offsets(int B, const int32_t* __restrict__ count,
+__global__ void __launch_bounds__(kScanThreads) k_offsets(int B, const int32_t* __restrict__ count, int extra,
                                                           int64_t* __restrict__ offsets) {
   __shared__ int64_t part[kScanThreads + 1];
   const int tid = threadIdx.x;
   const int per = (B + kScanThreads - 1) / kScanThreads;
   const int b0 = min(B, tid * per), b1 = min(B, b0 + per);
   int64_t s = 0;
-  for (int b = b0; b < b1; ++b) s += (int64_t)count[b] + 1;
+  for (int b = b0; b < b1; ++b) s += (int64_t)count[b] + extra;
   part[tid] = s;
   __syncthreads();
   // Hillis-Steele inclusive scan over the 1024 partial sums
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kScanThreads) k_offsets(int B, const int32_t* 
   int64_t run = part[tid] - s;  // exclusive prefix of this thread's run
   for (int b = b0; b < b1; ++b) {
     offsets[b] = run;
-    run += (int64_t)count[b] + 1;
+    run += (int64_t)count[b] + extra;
   }
   if (tid == kScanThreads - 1) offsets[B] = part[tid];
 }
@@ -222,7 +223,7 @@ cudaError_t launch_eloc_full(scale_ctx* c, double* eloc) {
   k_enum<<<B, 32, 0, c->stream>>>(c->lat, c->occ, c->bonds, c->nb_nn, c->nb_nnn, c->status, cap, c->full_moves,
                                   c->full_coeff, c->move_count, c->full_diag);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_offsets<<<1, kScanThreads, 0, c->stream>>>(B, c->move_count, c->full_offsets);
+  k_offsets<<<1, kScanThreads, 0, c->stream>>>(B, c->move_count, 1, c->full_offsets);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int64_t bound = (int64_t)B * (cap + 1);  // the device-side total is at most this
   const int chunk = c->full_chunk;
@@ -241,6 +242,11 @@ cudaError_t launch_eloc_full(scale_ctx* c, double* eloc) {
   }
   k_reduce_terms<<<(B + 255) / 256, 256, 0, c->stream>>>(B, cap, c->move_count, c->full_diag, c->full_coeff,
                                                          c->full_la_all, c->full_sg_all, eloc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_offsets(scale_ctx* c, int B, const int32_t* count, int extra, int64_t* offsets) {
+  k_offsets<<<1, kScanThreads, 0, c->stream>>>(B, count, extra, offsets);
   return cudaGetLastError();
 }
 

@@ -231,6 +231,13 @@ struct scale_ctx {
   int hmax = 0;             // widest layer (activation buffers are [B][N][hmax])
   void* ace_frag = nullptr; // TF32 hi/lo mma fragments of every ACE layer
 
+  // cached update at the wide SCALE shapes (wide_lowrank.cu): the caches z0 [B][N][h],
+  // HL [B][N][h_last], Binv and Pt [B][2][Ne][h_last] above, and per chunk of moves
+  bool wide_lr = false;
+  int wl_rows = 0;            // row slots per move: the largest affected set of any move
+  int wl_chunk = 0;           // moves per chunk (their rows fill the activation buffers)
+  void* wl_meta = nullptr;    // [wl_chunk] per-move record of the chunk
+
   scale_stats stats{};
 };
 
@@ -261,7 +268,21 @@ size_t ace_frag_bytes(const scale_arch& a);
 bool ace_mma_shapes(const scale_arch& a);
 bool ace_tc_shapes(const scale_arch& a);
 cudaError_t launch_ace_build(scale_ctx* c);
-cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg = nullptr);
+cudaError_t launch_ace_forward(scale_ctx* c, const int8_t* occ, int C, double* phi64, const int* vcfg = nullptr,
+                               void* hl_out = nullptr);
+cudaError_t launch_ace_layers(scale_ctx* c, const Lattice& lat, int l0, int l1, void* a, void* b, long long rows,
+                              bool split, const int* vcfg, void** out);
+bool ace_tc_layer(const scale_ctx* c, int l);
+
+// cached update at the wide SCALE shapes (wide_lowrank.cu)
+bool wide_lowrank_shapes(const scale_arch& a);
+int wide_rows_per_move(const scale_system& s, const scale_arch& a);
+size_t wide_meta_bytes();
+cudaError_t launch_wide_params(scale_ctx* c);
+cudaError_t launch_wide_cache(scale_ctx* c, int B);
+cudaError_t launch_wide_eloc(scale_ctx* c, double* eloc);
+// exclusive prefix sums offsets[b] = sum_{b' < b} (count[b'] + extra), offsets[B] = total
+cudaError_t launch_offsets(scale_ctx* c, int B, const int32_t* count, int extra, int64_t* offsets);
 
 // kernels (launch wrappers), each enqueued on ctx->stream
 // count (optional, device): sample_list is compacted, its first *count entries are used

@@ -93,8 +93,9 @@ def run_symmetry(walkers: int = 1024) -> dict:
 
 
 def run_wide(walkers: int = 8) -> dict:
-    """SCALE-L (plus stencil, conv 384, site-wise 4 x 512) local energies on the 16x16 torus
-    and SCALE-XL (conv 640, site-wise 4 x 1280) amplitudes on the 32x32 torus, full recompute."""
+    """SCALE-L (plus stencil, conv 384, site-wise 4 x 512) local energies on the 16x16 torus by
+    full recompute and by the cached update; SCALE-XL (conv 640, site-wise 4 x 1280) on the
+    32x32 torus: loads (forward, FP64 inverse, cache) and cached-update local energies."""
     import torch
     out = {}
     pl = I.workload("scale_l16x16")
@@ -117,9 +118,24 @@ def run_wide(walkers: int = 8) -> dict:
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
+    # the cached update (low-rank local energies) on the same network and walkers, then on more
+    lw = 256
+    ctx.scale_load(occ[:lw].contiguous())
+    el = torch.empty(lw, dtype=torch.float64, device="cuda")
+    ctx.scale_local_energy(el, Bd.PATH_LOWRANK)
+    torch.cuda.synchronize()
+    a.record()
+    ctx.scale_local_energy(el, Bd.PATH_LOWRANK)
+    b.record()
+    torch.cuda.synchronize()
+    lr_ms = a.elapsed_time(b)
+    diff = ((el[:walkers] - e).abs() / e.abs().clamp(min=1.0)).cpu().numpy()
     out["scale_l16x16"] = {"walkers": walkers, "ms": ms, "eloc_per_s": walkers / (ms / 1e3),
-                           "amplitudes_per_s": 1024 / (load_ms / 1e3),
-                           "finite": bool(torch.isfinite(e).all().item())}
+                           "load_1024_ms": load_ms,
+                           "lowrank_walkers": lw, "lowrank_ms": lr_ms, "lowrank_eloc_per_s": lw / (lr_ms / 1e3),
+                           "speedup_lowrank_vs_full": (lw / lr_ms) / (walkers / ms),
+                           "max_rel_diff_lowrank_vs_full": float(diff.max()),
+                           "finite": bool(torch.isfinite(e).all().item() and torch.isfinite(el).all().item())}
     ctx.close()
     px = I.workload("scale_xl32x32")
     nx = 128
@@ -132,7 +148,19 @@ def run_wide(walkers: int = 8) -> dict:
     b.record()
     torch.cuda.synchronize()
     xl_ms = a.elapsed_time(b)
-    out["scale_xl32x32"] = {"configurations": nx, "ms": xl_ms, "amplitudes_per_s": nx / (xl_ms / 1e3)}
+    xw = 4  # the cached update: low-rank local energies of the first walkers
+    ctx.scale_load(occ[:xw].contiguous())
+    ex = torch.empty(xw, dtype=torch.float64, device="cuda")
+    ctx.scale_local_energy(ex, Bd.PATH_LOWRANK)
+    torch.cuda.synchronize()
+    a.record()
+    ctx.scale_local_energy(ex, Bd.PATH_LOWRANK)
+    b.record()
+    torch.cuda.synchronize()
+    xlr_ms = a.elapsed_time(b)
+    out["scale_xl32x32"] = {"configurations": nx, "load_ms": xl_ms, "loads_per_s": nx / (xl_ms / 1e3),
+                            "lowrank_walkers": xw, "lowrank_ms": xlr_ms, "lowrank_eloc_per_s": xw / (xlr_ms / 1e3),
+                            "finite": bool(torch.isfinite(ex).all().item())}
     ctx.close()
     return out
 

@@ -95,11 +95,18 @@ def test_scale_xl_table_widths():
 
 
 def test_wide_rejects_cached_update_entry_points():
+    """The wide shapes offer the cached local energies (tests/test_wide_lowrank_gpu.py) but no
+    ratios, commits, sweeps or refreshes."""
+    import torch
     pb = I.workload("scale_l5x5")
     ctx, ora, occ, st = setup(pb, 4, 1265, 5715)
-    with pytest.raises(Bd.ScaleError) as e:
-        ctx.local_energy(Bd.PATH_LOWRANK)
-    assert e.value.status == Bd.EUNSUPPORTED
+    moves = torch.zeros((4, 4), dtype=torch.int32, device="cuda")
+    for call in (lambda: ctx.ratios(moves[:, None, :].contiguous()), lambda: ctx.scale_commit(moves),
+                 lambda: ctx.scale_refresh()):
+        with pytest.raises(Bd.ScaleError) as e:
+            call()
+        assert e.value.status == Bd.EUNSUPPORTED
+    assert np.isfinite(ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()).all()
 
 
 def test_wide_open_ragged_single():
