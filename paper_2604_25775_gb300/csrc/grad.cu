@@ -243,6 +243,203 @@ __global__ void k_din_tile(Lattice lat, Net<T> net, int l, const T* __restrict__
   }
 }
 
+// ---- the same three contractions with one sample's slabs staged in shared memory ----------
+// CTA per sample: the layer input rows (the embedding rows for layer 0) and/or dz copied to
+// shared memory once with coalesced loads, and the site table nbr[i][t] (the site reached from
+// i by tap t, or by its opposite for the input gradient; -1 past an open edge). The register
+// tiles and the summation order are those of the kernels above, so the results are the same.
+__device__ __forceinline__ void lds4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x;
+  v[1] = q.y;
+  v[2] = q.z;
+  v[3] = q.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), c = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = c.x;
+  v[3] = c.y;
+}
+
+__device__ __forceinline__ void stage_nbr(const Lattice& lat, int stencil, int k, int taps, int sgn, int* nbr) {
+  for (int q = threadIdx.x; q < lat.N * taps; q += blockDim.x) {
+    const int i = q / taps, t = q - i * taps;
+    int dx, dy;
+    stencil_tap(stencil, k, t, dx, dy);
+    nbr[q] = site_off(lat, i, sgn * dx, sgn * dy);
+  }
+}
+
+// Bytes of shared memory of the staged kernels: [slabs][N][h] rows and the [N][taps] table.
+inline size_t grad_smem_bytes(int N, int h, int taps, int slabs, size_t tsize) {
+  return (size_t)slabs * N * h * tsize + (size_t)N * taps * sizeof(int);
+}
+
+template <typename T, int HC>
+__global__ void k_fwd_smem(Lattice lat, Net<T> net, int l, int taps, const int8_t* __restrict__ occ,
+                           const T* __restrict__ in, T* __restrict__ out, T* __restrict__ zout) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const int h = HC ? HC : net.h, N = lat.N, hq = h >> 2;
+  const int b = blockIdx.x;
+  T* xs = reinterpret_cast<T*>(gsm);
+  int* nbr = reinterpret_cast<int*>(xs + (size_t)N * h);
+  const int8_t* ob = occ + (size_t)b * N;
+  const T* in_b = in + (size_t)b * N * h;
+  for (int q = threadIdx.x; q < N * h; q += blockDim.x) {
+    const int i = q / h, c = q - i * h;
+    xs[q] = layer_in_row(net, l, ob, in_b, i, h)[c];
+  }
+  stage_nbr(lat, net.stencil, net.ksize[l], taps, 1, nbr);
+  __syncthreads();
+  const int tiles = ((N + 3) >> 2) * hq;
+  for (int q = threadIdx.x; q < tiles; q += blockDim.x) {
+    const int sq = q / hq, c0 = (q - sq * hq) * 4;
+    T acc[4][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[s][m] = net.bias[l][c0 + m];
+    for (int t = 0; t < taps; ++t) {
+      int row[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = sq * 4 + s;
+        row[s] = i < N ? nbr[i * taps + t] : -1;
+      }
+      const T* w = net.kernel[l] + (size_t)t * h * h + c0;
+#pragma unroll
+      for (int ci = 0; ci < h; ci += 4) {
+        T wv[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ld4(w + (size_t)(ci + a) * h, wv[a]);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          if (row[s] < 0) continue;
+          T xv[4];
+          lds4(xs + (size_t)row[s] * h + ci, xv);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc[s][m] = fma(xv[a], wv[a][m], acc[s][m]);
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = sq * 4 + s;
+      if (i >= N) break;
+      const size_t o = ((size_t)b * N + i) * h + c0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        out[o + m] = (net.resid[l] ? xs[(size_t)i * h + c0 + m] : T(0)) + act_fn<T>(net.act, acc[s][m]);
+        zout[o + m] = acc[s][m];
+      }
+    }
+  }
+}
+
+template <typename T, int HC>
+__global__ void k_dk_smem(Lattice lat, Net<T> net, int l, int taps, const int8_t* __restrict__ occ,
+                          const T* __restrict__ in, const T* __restrict__ dz, int64_t off_k, int64_t P,
+                          double* __restrict__ grad) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const int N = lat.N, h = HC ? HC : net.h, hq = h >> 2, ho = h >> 3;
+  const int b = blockIdx.x;
+  T* xs = reinterpret_cast<T*>(gsm);
+  T* gs = xs + (size_t)N * h;
+  int* nbr = reinterpret_cast<int*>(gs + (size_t)N * h);
+  const int8_t* ob = occ + (size_t)b * N;
+  const T* in_b = in + (size_t)b * N * h;
+  const T* dz_b = dz + (size_t)b * N * h;
+  for (int q = threadIdx.x; q < N * h; q += blockDim.x) {
+    const int i = q / h, c = q - i * h;
+    xs[q] = layer_in_row(net, l, ob, in_b, i, h)[c];
+    gs[q] = dz_b[q];
+  }
+  stage_nbr(lat, net.stencil, net.ksize[l], taps, 1, nbr);
+  __syncthreads();
+  for (int q = threadIdx.x; q < taps * hq * ho; q += blockDim.x) {
+    const int t = q / (hq * ho), rem = q - t * hq * ho, ci0 = (rem / ho) * 4, co0 = (rem % ho) * 8;
+    T acc[4][8] = {};
+    for (int i = 0; i < N; ++i) {
+      const int j = nbr[i * taps + t];
+      if (j < 0) continue;
+      T xv[4], gv[2][4];
+      lds4(xs + (size_t)j * h + ci0, xv);
+      lds4(gs + (size_t)i * h + co0, gv[0]);
+      lds4(gs + (size_t)i * h + co0 + 4, gv[1]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[a][m] = fma(xv[a], gv[m >> 2][m & 3], acc[a][m]);
+    }
+    double* g = grad + (size_t)b * P + off_k + (size_t)t * h * h + co0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) g[(size_t)(ci0 + a) * h + m] = (double)acc[a][m];
+  }
+}
+
+template <typename T, int HC>
+__global__ void k_din_smem(Lattice lat, Net<T> net, int l, int taps, const T* __restrict__ KT,
+                           const T* __restrict__ dout, const T* __restrict__ dz, T* __restrict__ din) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const int h = HC ? HC : net.h, N = lat.N, hq = h >> 2;
+  const int b = blockIdx.x;
+  T* gs = reinterpret_cast<T*>(gsm);
+  int* nbr = reinterpret_cast<int*>(gs + (size_t)N * h);
+  const size_t base = (size_t)b * N * h;
+  for (int q = threadIdx.x; q < N * h; q += blockDim.x) gs[q] = dz[base + q];
+  stage_nbr(lat, net.stencil, net.ksize[l], taps, -1, nbr);  // site i with i + d = j
+  __syncthreads();
+  const int tiles = ((N + 3) >> 2) * hq;
+  for (int q = threadIdx.x; q < tiles; q += blockDim.x) {
+    const int sq = q / hq, c0 = (q - sq * hq) * 4;
+    T acc[4][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int j = sq * 4 + s;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[s][m] = (net.resid[l] && j < N) ? dout[base + (size_t)j * h + c0 + m] : T(0);
+    }
+    for (int t = 0; t < taps; ++t) {
+      int src[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int j = sq * 4 + s;
+        src[s] = j < N ? nbr[j * taps + t] : -1;
+      }
+      const T* w = KT + (size_t)t * h * h + c0;
+#pragma unroll
+      for (int co = 0; co < h; co += 4) {
+        T wv[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ld4(w + (size_t)(co + a) * h, wv[a]);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          if (src[s] < 0) continue;
+          T gv[4];
+          lds4(gs + (size_t)src[s] * h + co, gv);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc[s][m] = fma(wv[a][m], gv[a], acc[s][m]);
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int j = sq * 4 + s;
+      if (j >= N) break;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) din[base + (size_t)j * h + c0 + m] = acc[s][m];
+    }
+  }
+}
+
 // Projection gradients and dH(L).
 template <typename T>
 __global__ void k_grad_proj(Lattice lat, Net<T> net, const int32_t* __restrict__ orb_of_slot,
@@ -392,12 +589,31 @@ __global__ void k_nan_bad(int B, int64_t P, const int32_t* __restrict__ status, 
   for (int64_t q = threadIdx.x; q < P; q += blockDim.x) grad[(size_t)b * P + q] = CUDART_NAN;
 }
 
+// One CTA per sample with `smem` bytes of staged slabs; the block covers the sample's work
+// (at most 256 threads, each looping over its share).
+template <typename... KA, typename... A>
+cudaError_t staged_launch(void (*kern)(KA...), int B, int work, size_t smem, cudaStream_t st, A... args) {
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int block = std::min(256, std::max(32, (work + 31) / 32 * 32));
+  kern<<<B, block, smem, st>>>(args...);
+  return cudaGetLastError();
+}
+
+constexpr size_t kGradSmemMax = 96 * 1024;  // staged slabs up to this size (a few CTAs per SM)
+
 template <typename T>
 cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
   const Net<T> net = make_net<T>(c);
   const int B = c->B, N = c->N, h = c->h, L = c->L;
   const size_t slab = (size_t)B * N * h;  // elements of one layer slab
   const bool tiled = h % 8 == 0;          // the register-tiled kernels (vector loads of 4)
+  int max_taps = 1;
+  for (int l = 0; l < L; ++l) max_taps = std::max(max_taps, stencil_taps(net.stencil, net.ksize[l]));
+  // the tiled kernels with one sample's slabs staged in shared memory, where they fit
+  const bool staged = tiled && grad_smem_bytes(N, h, max_taps, 2, sizeof(T)) <= kGradSmemMax;
   // stored: every layer's input and pre-activation kept from the one forward pass; recompute:
   // only every stride-th layer input, each segment's forward recomputed during the backward
   const int stride = recompute ? std::max(1, (int)std::ceil(std::sqrt((double)L))) : 1;
@@ -458,8 +674,22 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
     case 64: KERNEL<T, 64><<<GRID, 128, 0, c->stream>>>(__VA_ARGS__); break;               \
     default: KERNEL<T, 0><<<GRID, 128, 0, c->stream>>>(__VA_ARGS__);                       \
   }
+#define SCALE_GRAD_STAGED(KERNEL, WORK, SMEM, ...)                                                            \
+  switch (h) {                                                                                               \
+    case 8: e = staged_launch(KERNEL<T, 8>, B, WORK, SMEM, c->stream, __VA_ARGS__); break;                   \
+    case 16: e = staged_launch(KERNEL<T, 16>, B, WORK, SMEM, c->stream, __VA_ARGS__); break;                 \
+    case 32: e = staged_launch(KERNEL<T, 32>, B, WORK, SMEM, c->stream, __VA_ARGS__); break;                 \
+    case 64: e = staged_launch(KERNEL<T, 64>, B, WORK, SMEM, c->stream, __VA_ARGS__); break;                 \
+    default: e = staged_launch(KERNEL<T, 0>, B, WORK, SMEM, c->stream, __VA_ARGS__);                         \
+  }
+  const int site_tiles = ((N + 3) / 4) * (h / 4);
+  cudaError_t e = cudaSuccess;
   auto fwd = [&](int l, const T* in, T* out, T* z) {
-    if (tiled) {
+    if (staged) {
+      const int tl = stencil_taps(net.stencil, net.ksize[l]);
+      SCALE_GRAD_STAGED(k_fwd_smem, site_tiles, grad_smem_bytes(N, h, tl, 1, sizeof(T)), c->lat, net, l, tl, c->occ,
+                        in, out, z);
+    } else if (tiled) {
       SCALE_GRAD_TILED(k_fwd_tile, gridT, c->lat, net, l, c->occ, in, out, z);
     } else {
       k_fwd_layer<T><<<gridL, 128, 0, c->stream>>>(c->lat, net, l, c->occ, in, out, z);
@@ -475,6 +705,7 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
         out = keep ? ck + (size_t)((l + 1) / stride) * slab : segH + (size_t)((l + 1) % 2) * slab;
       }
       fwd(l, in, out, recompute ? segZ : segZ + (size_t)l * slab);
+      if (e != cudaSuccess) return e;
       in = out;
     }
   }
@@ -489,6 +720,7 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
       for (int l = l0; l < l1; ++l) {
         T* out = segH + (size_t)(l - l0 + 1) * slab;
         fwd(l, in, out, segZ + (size_t)(l - l0) * slab);
+        if (e != cudaSuccess) return e;
         in = out;
       }
     }
@@ -497,7 +729,14 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
       const T* zl = recompute ? segZ + (size_t)(l - l0) * slab : segZ + (size_t)l * slab;
       k_grad_dz<T><<<B, 256, 0, c->stream>>>(c->lat, net, l, dcur, zl, dZ, offB[l], c->P, grad);
       const int kq = tiled ? taps[l] * (h / 4) * (h / 8) : taps[l] * h * h;
-      if (tiled) {
+      if (staged) {
+        SCALE_GRAD_STAGED(k_dk_smem, kq, grad_smem_bytes(N, h, taps[l], 2, sizeof(T)), c->lat, net, l, taps[l], c->occ,
+                          lin, dZ, offK[l], c->P, grad);
+        if (e != cudaSuccess) return e;
+        SCALE_GRAD_STAGED(k_din_smem, site_tiles, grad_smem_bytes(N, h, taps[l], 1, sizeof(T)), c->lat, net, l,
+                          taps[l], KTl[l], dcur, dZ, dnext);
+        if (e != cudaSuccess) return e;
+      } else if (tiled) {
         const dim3 gridK((kq + 127) / 128, B);
         SCALE_GRAD_TILED(k_dk_tile, gridK, c->lat, net, l, taps[l], c->occ, lin, dZ, offK[l], c->P, grad);
         SCALE_GRAD_TILED(k_din_tile, gridT, c->lat, net, l, KTl[l], dcur, dZ, dnext);
@@ -510,6 +749,7 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
     }
   }
 #undef SCALE_GRAD_TILED
+#undef SCALE_GRAD_STAGED
   k_grad_embed<T><<<B, 256, 0, c->stream>>>(c->lat, net, c->occ, dcur, c->P, grad);
   k_nan_bad<<<B, 256, 0, c->stream>>>(B, c->P, c->status, grad);
   return cudaGetLastError();

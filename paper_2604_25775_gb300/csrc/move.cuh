@@ -391,6 +391,33 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   // each electron of that spin dotted against its feature row (H' if it moved, Delta H if
   // not); identity for the electrons that kept their orbital
   if constexpr (H <= 32) {
+    if (r <= 16) {
+      // two half-warps per column b = lane % 16, each with half of the Pt row in registers;
+      // the halves meet in one shuffle (twice the active lanes of one column per lane)
+      constexpr int HH = H / 2;
+      const int bb = lane & 15, hc = lane >> 4;
+      const int cbb = ms.slot[bb < r ? bb : 0];
+      for (int sp = 0; sp < 2; ++sp) {
+        const int a0 = sp ? r_up : 0, a1 = sp ? r : r_up;
+        if (a0 == a1) continue;
+        const T* pt = sv.Pt + ((size_t)sp * Ne + cbb) * h + hc * HH;
+        T pv[HH];
+#pragma unroll
+        for (int u = 0; u < HH; ++u) pv[u] = (hc * HH + u < h) ? pt[u] : T(0);
+        for (int a = a0; a < a1; ++a) {
+          const T* row = (ms.moved[a] ? ms.feat[ms.sidx[a]] : ms.hl[ms.sidx[a]]) + hc * HH;
+          T v[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+          for (int u = 0; u < HH; ++u)
+            if (hc * HH + u < h) v[u & 3] += row[u] * pv[u];
+          const T part = (v[0] + v[1]) + (v[2] + v[3]);
+          const T tot = part + __shfl_xor_sync(0xffffffffu, part, 16);
+          const T init = (!ms.moved[a] && a == bb) ? T(1) : T(0);
+          if (hc == 0 && bb < r) ms.R[a][bb] = init + tot;
+        }
+      }
+      __syncwarp();
+    } else {
     // the whole Pt row of the lane's column in registers; every row of R written once
     for (int sp = 0; sp < 2; ++sp) {
       const int a0 = sp ? r_up : 0, a1 = sp ? r : r_up;
@@ -410,6 +437,7 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
       }
     }
     __syncwarp();
+    }
   } else {
   if (lane < r)
     for (int a = 0; a < r; ++a) ms.R[a][lane] = (!ms.moved[a] && a == lane) ? T(1) : T(0);
