@@ -243,11 +243,11 @@ __global__ void k_din_tile(Lattice lat, Net<T> net, int l, const T* __restrict__
   }
 }
 
-// ---- the same three contractions with one sample's slabs staged in shared memory ----------
-// CTA per sample: the layer input rows (the embedding rows for layer 0) and/or dz copied to
-// shared memory once with coalesced loads, and the site table nbr[i][t] (the site reached from
-// i by tap t, or by its opposite for the input gradient; -1 past an open edge). The register
-// tiles and the summation order are those of the kernels above, so the results are the same.
+// ---- the forward and dK with one sample's slabs staged in shared memory --------------------
+// CTA per sample: the layer input rows (the embedding rows for layer 0) and, for dK, dz copied
+// to shared memory once with coalesced loads, and the site table nbr[i][t] (the site reached
+// from i by tap t; -1 past an open edge). The register tiles and the summation order are those
+// of the kernels above, so the results are the same.
 __device__ __forceinline__ void lds4(const float* p, float (&v)[4]) {
   const float4 q = *reinterpret_cast<const float4*>(p);
   v[0] = q.x;
@@ -380,63 +380,6 @@ __global__ void k_dk_smem(Lattice lat, Net<T> net, int l, int taps, const int8_t
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int m = 0; m < 8; ++m) g[(size_t)(ci0 + a) * h + m] = (double)acc[a][m];
-  }
-}
-
-template <typename T, int HC>
-__global__ void k_din_smem(Lattice lat, Net<T> net, int l, int taps, const T* __restrict__ KT,
-                           const T* __restrict__ dout, const T* __restrict__ dz, T* __restrict__ din) {
-  extern __shared__ __align__(16) unsigned char gsm[];
-  const int h = HC ? HC : net.h, N = lat.N, hq = h >> 2;
-  const int b = blockIdx.x;
-  T* gs = reinterpret_cast<T*>(gsm);
-  int* nbr = reinterpret_cast<int*>(gs + (size_t)N * h);
-  const size_t base = (size_t)b * N * h;
-  for (int q = threadIdx.x; q < N * h; q += blockDim.x) gs[q] = dz[base + q];
-  stage_nbr(lat, net.stencil, net.ksize[l], taps, -1, nbr);  // site i with i + d = j
-  __syncthreads();
-  const int tiles = ((N + 3) >> 2) * hq;
-  for (int q = threadIdx.x; q < tiles; q += blockDim.x) {
-    const int sq = q / hq, c0 = (q - sq * hq) * 4;
-    T acc[4][4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int j = sq * 4 + s;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) acc[s][m] = (net.resid[l] && j < N) ? dout[base + (size_t)j * h + c0 + m] : T(0);
-    }
-    for (int t = 0; t < taps; ++t) {
-      int src[4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int j = sq * 4 + s;
-        src[s] = j < N ? nbr[j * taps + t] : -1;
-      }
-      const T* w = KT + (size_t)t * h * h + c0;
-#pragma unroll
-      for (int co = 0; co < h; co += 4) {
-        T wv[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) ld4(w + (size_t)(co + a) * h, wv[a]);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          if (src[s] < 0) continue;
-          T gv[4];
-          lds4(gs + (size_t)src[s] * h + co, gv);
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int m = 0; m < 4; ++m) acc[s][m] = fma(wv[a][m], gv[a], acc[s][m]);
-        }
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int j = sq * 4 + s;
-      if (j >= N) break;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) din[base + (size_t)j * h + c0 + m] = acc[s][m];
-    }
   }
 }
 
@@ -733,9 +676,8 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
         SCALE_GRAD_STAGED(k_dk_smem, kq, grad_smem_bytes(N, h, taps[l], 2, sizeof(T)), c->lat, net, l, taps[l], c->occ,
                           lin, dZ, offK[l], c->P, grad);
         if (e != cudaSuccess) return e;
-        SCALE_GRAD_STAGED(k_din_smem, site_tiles, grad_smem_bytes(N, h, taps[l], 1, sizeof(T)), c->lat, net, l,
-                          taps[l], KTl[l], dcur, dZ, dnext);
-        if (e != cudaSuccess) return e;
+        // the input gradient reads dz through L1 as fast as from a staged copy (measured)
+        SCALE_GRAD_TILED(k_din_tile, gridT, c->lat, net, l, KTl[l], dcur, dZ, dnext);
       } else if (tiled) {
         const dim3 gridK((kq + 127) / 128, B);
         SCALE_GRAD_TILED(k_dk_tile, gridK, c->lat, net, l, taps[l], c->occ, lin, dZ, offK[l], c->P, grad);
