@@ -552,10 +552,14 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
       }
     }
   }
-  // this thread's half of the tile's residual row (independent of the MMAs: loaded under them)
+  // this thread's half of the tile's residual row (independent of the MMAs: loaded under them);
+  // the 256-column tiles (site-wise layers, no residual) stream their epilogue instead
+  constexpr bool kStream = N == 256;
   const int c0 = part * H2;
-  float u[H2];
-  if (LN || res) {  // the normalised conv blocks are residual
+  float u[kStream ? 1 : H2];
+  if constexpr (kStream) {
+    u[0] = 0.f;
+  } else if (LN || res) {  // the normalised conv blocks are residual
     const float* xh = in_hi + (size_t)(valid ? R : 0) * C + cb + c0;
     const float* xl = in_lo + (size_t)(valid ? R : 0) * C + cb + c0;
 #pragma unroll
@@ -571,6 +575,7 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
 #pragma unroll
     for (int c = 0; c < H2; ++c) u[c] = 0.f;
   }
+  (void)u;
   if (!s_abort && tid == 0) {
     const int sl = STEPS - 1;
     if (!tc::mbar_wait(&done[sl % kTcStages], (uint32_t)(sl / kTcStages) & 1u, kTcWaitPolls)) s_abort = 1;
@@ -579,6 +584,43 @@ __global__ void __launch_bounds__(kTcThreads, (N > 144 ? 1 : 2)) k_ace_conv_tc(
   __syncthreads();
   tc::fence_after_sync();
   const bool run = !s_abort;
+  if constexpr (kStream) {  // 8 columns at a time: TMEM -> bias, activation -> (split) store
+    if (run) {
+      const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + c0;
+#pragma unroll 1
+      for (int cc = 0; cc < H2 / 8; ++cc) {
+        float z[8];
+        tc::tmem_ld8(trow + cc * 8, z);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) z[q] = act_tc(act, z[q] + __ldg(bias + cb + c0 + cc * 8 + q));
+        if (valid) {
+          const size_t o = (size_t)R * CO + cb + c0 + cc * 8;
+          if (out_lo) {
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) split_tf32(z[e], hi[e], lo[e]);
+#pragma unroll
+            for (int e = 0; e < 8; e += 4) {
+              *reinterpret_cast<float4*>(out_hi + o + e) = make_float4(
+                  __uint_as_float(hi[e]), __uint_as_float(hi[e + 1]), __uint_as_float(hi[e + 2]), __uint_as_float(hi[e + 3]));
+              *reinterpret_cast<float4*>(out_lo + o + e) = make_float4(
+                  __uint_as_float(lo[e]), __uint_as_float(lo[e + 1]), __uint_as_float(lo[e + 2]), __uint_as_float(lo[e + 3]));
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; e += 4)
+              *reinterpret_cast<float4*>(out_hi + o + e) = make_float4(z[e], z[e + 1], z[e + 2], z[e + 3]);
+          }
+        }
+      }
+    } else if (tid == 0) {
+      atomicExch(err, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, S::TCOLS);
+    return;
+  }
   if (run) {
     const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + c0;
 #pragma unroll
@@ -686,6 +728,9 @@ cudaError_t launch_conv_tc(const scale_ctx* c, const Lattice& lat, bool ln, int 
   }
   if (ks > 1 && cout == 384) return SCALE_TC(192, false);
   if (ks > 1 && cout == 640) return SCALE_TC(160, false);
+  // site-wise layers without residual: 256-column tiles where the width allows (twice the
+  // MMA work per pipeline stage, the rows read half as often); else 128
+  if (ks == 1 && !res && cout % 256 == 0) return SCALE_TC(256, false);
   return SCALE_TC(128, false);
 #undef SCALE_TC
 }
