@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(32 * kWlWarps) k_wl_stage(WideView<T> v, int64
 template <typename T>
 __global__ void __launch_bounds__(32 * kWlWarps) k_wl_finish(WideView<T> v, int64_t g0, int MC,
                                                              const T* __restrict__ feat, double* __restrict__ terms) {
+  extern __shared__ __align__(16) unsigned char wsm[];  // [kWlWarps][hl]: the row a's vector
   __shared__ T Rs[kWlWarps][kRMax][kRMax + 1];
   __shared__ int sl_slot[kWlWarps][kRMax], sl_sidx[kWlWarps][kRMax], sl_moved[kWlWarps][kRMax], sl_orb[kWlWarps][kRMax];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -339,30 +340,49 @@ __global__ void __launch_bounds__(32 * kWlWarps) k_wl_finish(WideView<T> v, int6
     if (lane == 0) terms[g] = CUDART_NAN;
     return;
   }
-  // R, one row a at a time: its feature row (H'(L) - H(L) if the orbital is kept) against the
-  // Pt rows of its spin for every column, lanes over channels, a warp sum per entry
+  // R, one row a at a time: its feature row (H'(L) - H(L) if the orbital is kept) staged in
+  // shared memory once, then dotted against the Pt rows of its spin four columns per pass
+  // (lanes over channels, one reduction round per pass)
   const T* Ptb = v.Pt + (size_t)b * 2 * Ne * hl;
   const T* HLb = v.HL + (size_t)b * N * hl;
   const T* Bb = v.Binv + (size_t)b * Ne * Ne;
+  T* dh = reinterpret_cast<T*>(wsm) + (size_t)warp * hl;
   for (int a = 0; a < r; ++a) {
     const int sp = a >= r_up;
     const int s = sidx[a];
     const bool kept = !moved[a];
     const T* x = feat + ((size_t)j * v.rpm + s) * hl;
     const T* hrow = HLb + (size_t)m.site[s] * hl;
-    for (int bq = 0; bq < r; ++bq) {
-      const T* p = Ptb + ((size_t)sp * Ne + slot[bq]) * hl;
-      T acc = T(0);
-      for (int c = lane; c < hl; c += 32) acc += (kept ? x[c] - hrow[c] : x[c]) * p[c];
+    for (int c = lane; c < hl; c += 32) dh[c] = kept ? x[c] - hrow[c] : x[c];
+    __syncwarp();
+    for (int b0 = 0; b0 < r; b0 += 4) {
+      const T* p[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) p[u] = Ptb + ((size_t)sp * Ne + slot[min(b0 + u, r - 1)]) * hl;
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      for (int c = lane; c < hl; c += 32) {
+        const T d = dh[c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += d * p[u][c];
+      }
       if (!kept) {  // + (M0 + proj_b)[o'_a] . Binv[c_b]
         const T* mb = v.M0b + (size_t)orb[a] * Ne;
-        const T* bc = Bb + (size_t)slot[bq] * Ne;
-        for (int k = lane; k < Ne; k += 32) acc += mb[k] * bc[k];
+        for (int k = lane; k < Ne; k += 32) {
+          const T mk = mb[k];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] += mk * Bb[(size_t)slot[min(b0 + u, r - 1)] * Ne + k];
+        }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) R[a][bq] = (kept && a == bq ? T(1) : T(0)) + acc;
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+      if (lane == 0)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (b0 + u < r) R[a][b0 + u] = (kept && a == b0 + u ? T(1) : T(0)) + acc[u];
     }
+    __syncwarp();
   }
   __syncwarp();
   const T det = warp_det_R<T>(R, r);
@@ -476,6 +496,10 @@ cudaError_t wide_eloc_t(scale_ctx* c, double* eloc) {
   const bool split = !c->fp64 && ace_tc_layer(c, 1);
   const int64_t bound = (int64_t)B * (int64_t)cap;  // the device-side total is at most this
   T* ra = (T*)c->act_a;
+  const size_t fsm = (size_t)kWlWarps * v.hl * sizeof(T);  // the finishing warps' row vectors
+  if (fsm > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(k_wl_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm)) != cudaSuccess)
+    return e;
   for (int64_t g0 = 0; g0 < bound; g0 += MC) {
     const unsigned grid = (unsigned)((MC + kWlWarps - 1) / kWlWarps);
     if (split)
@@ -486,7 +510,7 @@ cudaError_t wide_eloc_t(scale_ctx* c, double* eloc) {
     void* out = nullptr;
     if ((e = launch_ace_layers(c, rl, 1, c->L, c->act_a, c->act_b, rows, split, c->full_vcount, &out)) != cudaSuccess)
       return e;
-    k_wl_finish<T><<<grid, 32 * kWlWarps, 0, c->stream>>>(v, g0, MC, (const T*)out, c->full_coeff);
+    k_wl_finish<T><<<grid, 32 * kWlWarps, fsm, c->stream>>>(v, g0, MC, (const T*)out, c->full_coeff);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   k_wl_reduce<<<(B + 127) / 128, 128, 0, c->stream>>>(B, c->full_offsets, c->full_diag, c->full_coeff, c->status,
