@@ -533,14 +533,14 @@ __global__ void k_nan_bad(int B, int64_t P, const int32_t* __restrict__ status, 
 }
 
 // One CTA per sample with `smem` bytes of staged slabs; the block covers the sample's work
-// (at most 256 threads, each looping over its share).
+// (one tile per thread up to 1024 tiles, beyond that each thread loops over its share).
 template <typename... KA, typename... A>
 cudaError_t staged_launch(void (*kern)(KA...), int B, int work, size_t smem, cudaStream_t st, A... args) {
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const int block = std::min(256, std::max(32, (work + 31) / 32 * 32));
+  const int block = std::min(1024, std::max(32, (work + 31) / 32 * 32));  // one tile per thread
   kern<<<B, block, smem, st>>>(args...);
   return cudaGetLastError();
 }
@@ -555,8 +555,10 @@ cudaError_t grad_t(scale_ctx* c, double* grad, int recompute) {
   const bool tiled = h % 8 == 0;          // the register-tiled kernels (vector loads of 4)
   int max_taps = 1;
   for (int l = 0; l < L; ++l) max_taps = std::max(max_taps, stencil_taps(net.stencil, net.ksize[l]));
-  // the tiled kernels with one sample's slabs staged in shared memory, where they fit
-  const bool staged = tiled && grad_smem_bytes(N, h, max_taps, 2, sizeof(T)) <= kGradSmemMax;
+  // the tiled kernels with one sample's slabs staged in shared memory: small lattices (the
+  // 16x4 cylinder: forward 109 -> 96 us, dK 216 -> 140 us per 2048 walkers); at 256 sites the
+  // 73 KB of staged slabs per sample cost more than the L1-served kernels (measured)
+  const bool staged = tiled && N <= 128 && grad_smem_bytes(N, h, max_taps, 2, sizeof(T)) <= kGradSmemMax;
   // stored: every layer's input and pre-activation kept from the one forward pass; recompute:
   // only every stride-th layer input, each segment's forward recomputed during the backward
   const int stride = recompute ? std::max(1, (int)std::ceil(std::sqrt((double)L))) : 1;
