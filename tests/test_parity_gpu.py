@@ -158,21 +158,32 @@ def test_local_energy_mixed_8x8(name, prec):
 @pytest.fixture(scope="module")
 def mixed16():
     """The 16x16 workload at its full batch (8192 walkers) in the bench's launch configuration
-    (TF32x3 site-wise layers); 32 sampled walkers recomputed by the oracle."""
+    (TF32x3 site-wise layers); 64 sampled walkers recomputed by the oracle."""
     pb = I.workload("hubbard16x16")
     pseed, cseed = I.workload_seeds("hubbard16x16")
     ctx, ora, occ, st = setup(pb, 8192, pseed, cseed)
     rng = np.random.default_rng(0)
-    pick = np.sort(rng.choice(8192, 32, replace=False))
+    pick = np.sort(rng.choice(8192, 64, replace=False))
     cond = conditioning(ora, occ[pick])
     e_o, _ = ora.local_energy(occ[pick])
     return pb, ctx, ora, occ, pick, cond, e_o
 
 
+def _by_band(name, err, cond):
+    """The error distribution per conditioning band, over every sampled walker."""
+    edges = [0.0, 1e3, 1e4, 1e5, 1e6, np.inf]
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        m = (cond >= lo) & (cond < hi)
+        if m.any():
+            print(f"{name} cond in [{lo:.0e}, {hi:.0e}): n={m.sum()} median {np.median(err[m]):.2e} "
+                  f"max {err[m].max():.2e} within 1e-4: {np.mean(err[m] <= 1e-4):.2f}")
+
+
 def test_local_energy_mixed_16x16_full_batch_sampled(mixed16):
-    """Low-rank path, 16x16 at the full batch, 32 sampled outputs against the oracle."""
+    """Low-rank path, 16x16 at the full batch, 64 sampled outputs against the oracle."""
     pb, ctx, ora, occ, pick, cond, e_o = mixed16
     e = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    _by_band("16x16 mixed lowrank", rel_err(e[pick], e_o), cond)
     la, sg = ctx.log_psi()
     # uniformly random 16x16 configurations have cond(Phi) >= 1e3; the strict band is
     # cond < 1e4 here, every sample still within cond * 8 * 2^-24
@@ -185,11 +196,12 @@ def test_local_energy_mixed_16x16_full_batch_sampled(mixed16):
 
 def test_full_path_mixed_16x16_full_batch_sampled(mixed16):
     """Full-recompute path (every psi(n) and psi(n') a fresh mixed-precision forward and FP64
-    LU) on the same 8192 walkers: the 32 sampled outputs against the oracle in the same band,
+    LU) on the same 8192 walkers: the 64 sampled outputs against the oracle in the same band,
     and the whole batch against the low-rank path."""
     pb, ctx, ora, occ, pick, cond, e_o = mixed16
     ef = ctx.local_energy(Bd.PATH_FULL).cpu().numpy()
     el = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    _by_band("16x16 mixed full", rel_err(ef[pick], e_o), cond)
     _check("16x16 mixed full (sampled)", ef[pick], e_o, cond, MIXED_TOL, 1e4, min_good=5)
     assert np.isfinite(ef).all()
     d = rel_err(el, ef)
