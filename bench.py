@@ -225,9 +225,11 @@ def move_schedule(pb, occ, n_steps, seed):
 def lowrank_flops_per_sample(pb, occ, n=32):
     """Algorithmic FLOPs of one low-rank E_loc per walker, counted from the configurations:
     per connected move, |S| sites x (L-1) site-wise layers x 2h^2, the moved electron's
-    G row (2 r Ne + 2 r h), the Delta H . P block (2 r^2 h) and the r x r LU (2/3 r^3);
-    r = electrons on the affected sites after the move, S = union of the 3x3 stencils."""
-    N, h, L, Ne = pb.N, pb.h, pb.n_layers, pb.Ne
+    features against the projector (2 r h; its (M0 + proj_b) . Phi^-1 part is read from the
+    cache that every commit keeps current), the Delta H . P block (2 r^2 h) and the r x r LU
+    (2/3 r^3); r = electrons on the affected sites after the move, S = union of the 3x3
+    stencils."""
+    N, h, L = pb.N, pb.h, pb.n_layers
     r0 = (pb.ksize[0] - 1) // 2
     tot = 0.0
     for b in range(min(n, occ.shape[0])):
@@ -250,7 +252,7 @@ def lowrank_flops_per_sample(pb, occ, n=32):
                     y[src] &= ~(1 << s)
                     y[dst] |= 1 << s
                     r = int(sum(((y[q] & 1) + ((y[q] >> 1) & 1)) for q in S))
-                    tot += len(S) * (L - 1) * 2 * h * h + 2 * r * Ne + 2 * r * h + 2 * r * r * h + 2 * r ** 3 / 3
+                    tot += len(S) * (L - 1) * 2 * h * h + 2 * r * h + 2 * r * r * h + 2 * r ** 3 / 3
     return tot / min(n, occ.shape[0])
 
 

@@ -158,7 +158,8 @@ Sizes sizes_of(const scale_system* s, const scale_arch* a, int B) {
   if (ace && cached) t += (FC * N / (size_t)wide_rows_per_move(*s, *a) + 1) * wide_meta_bytes();  // move records
   t += (size_t)B * (8 + 4 + 4 + 4 + 8 + 4 + 4 + 8 + 4 + 8);
   t += FC * Ne * Ne * 8;                   // Phi64
-  t += ace ? 16 : (size_t)B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T;  // commit scratch
+  t += ace ? 16 : (size_t)B * commit_scratch_elems((int)Ne, (int)N) * T;  // commit scratch
+  t += ace ? 16 : (size_t)B * Ne * 2 * N * T;                            // G0t
   if (ace && T == 4) t += ace_frag_bytes(*a);
   if (a->lowrank_kernel == SCALE_LOWRANK_BATCHED) t += (size_t)(a->n_layers - 1) * 2 * h * h * 4;  // weight image
   t += FC * (N + 4 + 8 + 4 + 4);          // full-path chunk: occupations, owner, log|psi|, sign, list
@@ -201,7 +202,7 @@ void free_all(scale_ctx* c) {
                   c->move_count, c->full_occ, c->full_owner, c->full_coeff, c->full_la_all, c->full_sg_all,
                   c->full_list, c->full_vcount, c->full_moves,
                   c->commit_scratch, c->la_tmp, c->sg_tmp, c->full_la, c->full_sg, c->full_diag,
-                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag, c->ace_err, c->et_wimg, c->wl_meta};
+                  c->full_offsets, c->grad_scratch, c->wfrag, c->ace_frag, c->ace_err, c->et_wimg, c->wl_meta, c->G0t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -349,7 +350,8 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A(&c->list_count, 16);
   A(&c->stat_dev, 4 * 8);
   A(&c->move_count, B * 4);
-  A((char**)&c->commit_scratch, ace ? 16 : B * (3 * 32 * Ne + 2 * 32 * kMaxH) * T);
+  A((char**)&c->commit_scratch, ace ? 16 : B * commit_scratch_elems((int)Ne, (int)N) * T);
+  A((char**)&c->G0t, ace ? 16 : B * Ne * 2 * N * T);
   A(&c->la_tmp, B * 8);
   A(&c->sg_tmp, B * 4);
   A(&c->full_occ, FC * N);

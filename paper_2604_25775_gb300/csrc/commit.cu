@@ -26,6 +26,7 @@ struct CommitArgs {
   void* HL;
   void* Binv;
   void* Pt;
+  void* G0t;
   double* logabs;
   int32_t* sign_slot;
   int32_t* status;
@@ -33,7 +34,7 @@ struct CommitArgs {
   double* drift;
   double drift_tol;
   const int32_t* moves;
-  void* scratch;          // [B][3*kRMax*Ne + 2*kRMax*kMaxH] T : X, D, saved Binv rows, saved Pt rows
+  void* scratch;          // [B][commit_scratch_elems] T: D, saved Binv rows, saved G0t rows
   unsigned long long* drift_max_bits;
   int32_t* n_commits;
   MlpFrags mf;
@@ -258,9 +259,12 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
   T* hb = (T*)a.HL + (size_t)b * N * h;
   T* Bb = (T*)a.Binv + (size_t)b * Ne * Ne;
   T* Pb = (T*)a.Pt + (size_t)b * 2 * Ne * h;
-  T* scr = (T*)a.scratch + (size_t)b * (3 * kRMax * Ne + 2 * kRMax * kMaxH);
+  const int No = 2 * N;
+  T* Gb = (T*)a.G0t + (size_t)b * Ne * No;
+  T* scr = (T*)a.scratch + (size_t)b * commit_scratch_elems(Ne, N);
   T* D = d_in_smem ? reinterpret_cast<T*>(smem + L.d) : scr;                         // [kRMax][NeP]
   T* Bc = bc_in_smem ? reinterpret_cast<T*>(smem + L.bc) : scr + (size_t)kRMax * NeP;  // [kRMax][NeP]
+  T* Gc = scr + (size_t)2 * kRMax * NeP;                                               // [kRMax][2N]
 
   SampleView<T> sv;
   sv.occ = occ_s;
@@ -269,6 +273,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
   sv.HL = hb;
   sv.Binv = Bb;
   sv.Pt = Pb;
+  sv.G0t = Gb;
   if (warp == 0) {
     if (lane == 0) {
       ms.kind = kind;
@@ -300,36 +305,10 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
       s_drift_bits = 0ull;
     }
   } else if (!singular) {
-    // four slots j per pass, lanes along k, every load of a pass in flight before the first
-    // use (this pass reads all of Binv; the later phases then find it in L2)
-    constexpr int KU = 32 / sizeof(T);  // k values per lane per pass
-    for (int m = 0; m < n_moved; ++m) {
-      const T* m0b = net.M0b + (size_t)(m ? om1 : om0) * Ne;
-      for (int j0 = 4 * (warp - 1); j0 < Ne; j0 += 4 * (kCommitWarps - 1)) {
-        T v[4] = {T(0), T(0), T(0), T(0)};
-        for (int k0 = 0; k0 < Ne; k0 += 32 * KU) {
-          T x[KU], y[4][KU];
-#pragma unroll
-          for (int u = 0; u < KU; ++u) {
-            const int k = k0 + lane + 32 * u;
-            const bool on = k < Ne;
-            x[u] = on ? m0b[k] : T(0);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) y[i][u] = (on && j0 + i < Ne) ? Bb[(size_t)(j0 + i) * Ne + k] : T(0);
-          }
-#pragma unroll
-          for (int u = 0; u < KU; ++u)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] += x[u] * y[i][u];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          T s = v[i];
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-          if (lane == 0 && j0 + i < Ne) g[m * NeP + j0 + i] = s;
-        }
-      }
+    // g_m[j] = (M0[o'_m] + proj_b) . Binv[j] for the moved orbitals: the cached G0t column
+    for (int q = tid - 32; q < n_moved * Ne; q += kCommitThreads - 32) {
+      const int m = q / Ne, j = q - m * Ne;
+      g[m * NeP + j] = Gb[(size_t)j * No + (m ? om1 : om0)];
     }
   }
   __syncthreads();
@@ -367,6 +346,10 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
     } else {
       for (int k = lane; k < Ne; k += 32) dst_row[k] = src_row[k];
     }
+  }
+  for (int q = tid; q < r * No; q += kCommitThreads) {  // old G0t rows of the slots c_b
+    const int bi = q / No, o = q - bi * No;
+    Gc[q] = Gb[(size_t)ms.slot[bi] * No + o];
   }
   for (int q = tid; q < 2 * kRMax * H; q += kCommitThreads) {
     const int sp = q / (kRMax * H), rem = q - sp * kRMax * H, bi = rem / H, c = rem - bi * H;
@@ -541,6 +524,54 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
         if (j0 + i < Ne) prow[(size_t)(j0 + i) * h + c] = acc[i];
     }
   }
+  // (C3) G0t[j][o] -= sum_b D[b][j] Gc[b][o]: G0t[j] = (M0 + proj_b) Binv[j] is linear in
+  // Binv[j], so it takes the same rank-r step; a 4-row x V-column tile per thread
+  if (No % V == 0) {
+    const int nov = No / V;
+    for (int q = tid; q < nquad * nov; q += kCommitThreads) {
+      const int ov = q % nov, j0 = 4 * (q / nov);
+      T acc[4][V];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (j0 + i < Ne) {
+          vld(Gb + (size_t)(j0 + i) * No + ov * V, acc[i]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[i][v] = T(0);
+        }
+      }
+#pragma unroll 2
+      for (int bi = 0; bi < r; ++bi) {
+        T gc[V], d[4];
+        vld(Gc + (size_t)bi * No + ov * V, gc);
+        load4(D + (size_t)bi * NeP + j0, d);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[i][v] -= d[i] * gc[v];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (j0 + i < Ne) vst(Gb + (size_t)(j0 + i) * No + ov * V, acc[i]);
+    }
+  } else {
+    for (int q = tid; q < nquad * No; q += kCommitThreads) {
+      const int o = q % No, j0 = 4 * (q / No);
+      T acc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = (j0 + i < Ne) ? Gb[(size_t)(j0 + i) * No + o] : T(0);
+      for (int bi = 0; bi < r; ++bi) {
+        const T gc = Gc[(size_t)bi * No + o];
+        T d[4];
+        load4(D + (size_t)bi * NeP + j0, d);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] -= d[i] * gc;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (j0 + i < Ne) Gb[(size_t)(j0 + i) * No + o] = acc[i];
+    }
+  }
   // (D) features on S: z0 <- z0', H(L) <- H'(L)
   for (int q = tid; q < ms.nS * h; q += kCommitThreads) {
     const int s = q / h, c = q - s * h;
@@ -710,6 +741,7 @@ cudaError_t commit_t(scale_ctx* c, const int32_t* moves, const int32_t* pick, co
   a.HL = c->HL;
   a.Binv = c->Binv;
   a.Pt = c->Pt;
+  a.G0t = c->G0t;
   a.logabs = c->logabs;
   a.sign_slot = c->sign_slot;
   a.status = c->status;

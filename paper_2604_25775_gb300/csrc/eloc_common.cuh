@@ -25,6 +25,7 @@ struct LowrankArgs {
   const void* HL;
   const void* Binv;
   const void* Pt;
+  const void* G0t;
   const int32_t* bonds;
   int nb_nn, nb_nnn;
   const int32_t* status;
@@ -163,6 +164,7 @@ inline LowrankArgs make_args(scale_ctx* c) {
   a.HL = c->HL;
   a.Binv = c->Binv;
   a.Pt = c->Pt;
+  a.G0t = c->G0t;
   a.bonds = c->bonds;
   a.nb_nn = c->nb_nn;
   a.nb_nnn = c->nb_nnn;

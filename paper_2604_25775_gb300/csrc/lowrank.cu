@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net) 
   sv.HL = (const T*)a.HL + (size_t)b * N * h;
   sv.Binv = (const T*)a.Binv + (size_t)b * Ne * Ne;
   sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
+  sv.G0t = (const T*)a.G0t + (size_t)b * Ne * 2 * N;
   MoveScratch<T, H>& ms = ms_all[warp];
 
   const int ncand = candidate_count(a);
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_ratios(LowrankArgs a, Net<T> ne
   sv.HL = (const T*)a.HL + (size_t)b * N * h;
   sv.Binv = (const T*)a.Binv + (size_t)b * Ne * Ne;
   sv.Pt = (const T*)a.Pt + (size_t)b * 2 * Ne * h;
+  sv.G0t = (const T*)a.G0t + (size_t)b * Ne * 2 * N;
   MoveScratch<T, H>& ms = ms_all[warp];
   for (int mi = warp; mi < a.M; mi += kWarps) {
     const int32_t* mv = a.moves + ((size_t)b * a.M + mi) * 4;
@@ -285,11 +287,73 @@ cudaError_t ratios_t(scale_ctx* c, const int32_t* moves, int M, double* ratio) {
   return cudaGetLastError();
 }
 
+// G0t[b][j][o] = (M0[o] + proj_b[s(o)]) . Binv[b][j]: the part of every Slater row's
+// product with the inverse that does not depend on the network features (the moved rows of
+// R need it for the target orbital). A GEMM per sample: CTA tiles of 64 slots x 64 orbitals,
+// 4 x 4 per thread, K staged 32 at a time through shared memory; the listed samples only
+// (their first *count entries when count is given).
+template <typename T>
+__global__ void __launch_bounds__(256) k_build_g0(int Ne, int No, const T* __restrict__ Binv,
+                                                  const T* __restrict__ M0b, T* __restrict__ G0t,
+                                                  const int32_t* __restrict__ list, int B,
+                                                  const int32_t* __restrict__ count) {
+  __shared__ T As[32][65];  // As[k][j] = Binv[j][k]
+  __shared__ T Ms[32][65];  // Ms[k][o] = M0b[o][k]
+  const int nrows = count ? min(*count, B) : B;
+  const int j0 = blockIdx.x * 64, o0 = blockIdx.y * 64;
+  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+  for (int lrow = blockIdx.z; lrow < nrows; lrow += gridDim.z) {
+    const int b = list ? list[lrow] : lrow;
+    if (b < 0) continue;
+    const T* Bb = Binv + (size_t)b * Ne * Ne;
+    T acc[4][4] = {};
+    for (int k0 = 0; k0 < Ne; k0 += 32) {
+      __syncthreads();  // the previous tiles are consumed
+      for (int q = tid; q < 64 * 32; q += 256) {
+        const int rr = q >> 5, kk = q & 31, k = k0 + kk;
+        As[kk][rr] = (j0 + rr < Ne && k < Ne) ? Bb[(size_t)(j0 + rr) * Ne + k] : T(0);
+        Ms[kk][rr] = (o0 + rr < No && k < Ne) ? M0b[(size_t)(o0 + rr) * Ne + k] : T(0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < 32; ++kk) {
+        T x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[u] = As[kk][tr + 16 * u];
+          y[u] = Ms[kk][tc + 16 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += x[u] * y[v];
+      }
+    }
+    T* out = G0t + (size_t)b * Ne * No;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + tr + 16 * u;
+      if (j >= Ne) continue;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int o = o0 + tc + 16 * v;
+        if (o < No) out[(size_t)j * No + o] = acc[u][v];
+      }
+    }
+  }
+}
+
 template <typename T>
 cudaError_t project_t(scale_ctx* c, int B, const int32_t* list, const int32_t* count) {
   dim3 grid((c->Ne + 31) / 32, count ? std::min(B, 1024) : B);
   k_project<T><<<grid, 256, 0, c->stream>>>(c->Ne, c->h, make_net<T>(c).proj_w, (const T*)c->Binv, (T*)c->Pt, list,
                                             B, count);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int No = 2 * c->N;
+  const dim3 g0grid((c->Ne + 63) / 64, (No + 63) / 64, count ? std::min(B, 256) : std::min(B, 65535));
+  k_build_g0<T><<<g0grid, 256, 0, c->stream>>>(c->Ne, No, (const T*)c->Binv, (const T*)c->M0b, (T*)c->G0t, list, B,
+                                               count);
   return cudaGetLastError();
 }
 

@@ -37,6 +37,12 @@ struct Lattice {
   double t, tp, U, J;
 };
 
+// Elements of one sample's commit scratch: the matrix D and the saved Binv rows ([32][NeP]
+// each, NeP = Ne rounded up to 4; 32 = the largest rank r) and the saved G0t rows ([32][2N]).
+__host__ __device__ inline size_t commit_scratch_elems(int Ne, int N) {
+  return (size_t)2 * 32 * ((Ne + 3) & ~3) + (size_t)32 * 2 * N;
+}
+
 // Offset (dx, dy) of tap d of a k x k layer: taps run over the box in row-major order; the
 // disk stencil keeps the offsets within L2 distance (k-1)/2 (k = 5: the 13 sites of SCALE-L).
 __host__ __device__ __forceinline__ void stencil_tap(int stencil, int k, int d, int& dx, int& dy) {
@@ -187,6 +193,7 @@ struct scale_ctx {
   void* HL = nullptr;
   void* Binv = nullptr;
   void* Pt = nullptr;
+  void* G0t = nullptr;  // [B][Ne][2N] T: G0t[j][o] = (M0[o] + proj_b[s(o)]) . Binv[j]
   double* logabs = nullptr;
   int32_t* sign_slot = nullptr;
   int32_t* status = nullptr;
