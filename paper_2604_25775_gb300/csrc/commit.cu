@@ -527,32 +527,50 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
   // (C3) G0t[j][o] -= sum_b D[b][j] Gc[b][o]: G0t[j] = (M0 + proj_b) Binv[j] is linear in
   // Binv[j], so it takes the same rank-r step; a 4-row x V-column tile per thread
   if (No % V == 0) {
-    const int nov = No / V;
-    for (int q = tid; q < nquad * nov; q += kCommitThreads) {
+    // two tiles per thread (rows j0.. and j0 + 4..), both loaded before the updates: twice the
+    // bytes in flight per thread of this streaming step
+    const int nov = No / V, ntile = nquad * nov;
+    for (int q = tid; q < ntile; q += 2 * kCommitThreads) {
+      const int q2 = q + kCommitThreads;
+      const bool two = q2 < ntile;
       const int ov = q % nov, j0 = 4 * (q / nov);
-      T acc[4][V];
+      const int ov2 = two ? q2 % nov : ov, j02 = two ? 4 * (q2 / nov) : j0;
+      T acc[2][4][V];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (j0 + i < Ne) {
-          vld(Gb + (size_t)(j0 + i) * No + ov * V, acc[i]);
-        } else {
+      for (int t = 0; t < 2; ++t) {
+        const int jj = t ? j02 : j0, oo = t ? ov2 : ov;
 #pragma unroll
-          for (int v = 0; v < V; ++v) acc[i][v] = T(0);
+        for (int i = 0; i < 4; ++i) {
+          if (jj + i < Ne && (t == 0 || two)) {
+            vld(Gb + (size_t)(jj + i) * No + oo * V, acc[t][i]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[t][i][v] = T(0);
+          }
         }
       }
 #pragma unroll 2
       for (int bi = 0; bi < r; ++bi) {
-        T gc[V], d[4];
-        vld(Gc + (size_t)bi * No + ov * V, gc);
-        load4(D + (size_t)bi * NeP + j0, d);
+        T gc[2][V], d[2][4];
+        vld(Gc + (size_t)bi * No + ov * V, gc[0]);
+        load4(D + (size_t)bi * NeP + j0, d[0]);
+        vld(Gc + (size_t)bi * No + ov2 * V, gc[1]);
+        load4(D + (size_t)bi * NeP + j02, d[1]);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int t = 0; t < 2; ++t)
 #pragma unroll
-          for (int v = 0; v < V; ++v) acc[i][v] -= d[i] * gc[v];
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[t][i][v] -= d[t][i] * gc[t][v];
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        if (j0 + i < Ne) vst(Gb + (size_t)(j0 + i) * No + ov * V, acc[i]);
+        if (j0 + i < Ne) vst(Gb + (size_t)(j0 + i) * No + ov * V, acc[0][i]);
+      if (two) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (j02 + i < Ne) vst(Gb + (size_t)(j02 + i) * No + ov2 * V, acc[1][i]);
+      }
     }
   } else {
     for (int q = tid; q < nquad * No; q += kCommitThreads) {
