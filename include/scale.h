@@ -35,7 +35,7 @@
  * Memory, streams, errors
  *   - Pointer arguments are DEVICE pointers unless the name ends in _host. The caller owns
  *     every pointer it passes; the context owns its cache (features, Phi^-1, projector,
- *     slot maps), allocated once at scale_create within the HBM budget.
+ *     (M0 + proj_b) Phi^-1, slot maps), allocated once at scale_create within the HBM budget.
  *   - Every call is asynchronous on the stream given at creation, except the stated
  *     host-reading calls (scale_get_stats, scale_footprint_bytes). A context is not
  *     re-entrant: one host thread at a time.
@@ -208,7 +208,9 @@ scale_status scale_set_params(scale_ctx *ctx, const double *params, const double
 
 /* Load B <= max_batch configurations occ[B][N] (int8) and build their cache: network
  * forward, Phi, FP64 Gauss-Jordan inverse with partial pivoting and log|det| (Sec. II.C,
- * "single LU"), projector P_s = W_s Phi^-1. sample_status[B] (int32, may be NULL)
+ * "single LU"), projector P_s = W_s Phi^-1 and G0 = (M0 + proj_b) Phi^-1 (the part of every
+ * Slater row's product with the inverse that does not depend on the network features).
+ * sample_status[B] (int32, may be NULL)
  * receives SCALE_SAMPLE_* bits. */
 scale_status scale_load(scale_ctx *ctx, const int8_t *occ, int32_t B, int32_t *sample_status);
 
@@ -240,7 +242,7 @@ scale_status scale_ratios(scale_ctx *ctx, const int32_t *moves, int32_t M, doubl
 scale_status scale_local_energy(scale_ctx *ctx, int32_t path, double *eloc);
 
 /* Apply one accepted move per sample (moves [B][4] int32, kind -1 = reject): Woodbury
- * update of Phi^-1 (Eq. SMW, second line), rank-r update of the projector, incremental
+ * update of Phi^-1 (Eq. SMW, second line), rank-r update of the projector and of G0, incremental
  * update of the cached features, occupations and slot maps, running log|det|. Samples
  * whose commit counter reaches refresh_every, or whose drift check fired, are
  * re-factorised in FP64 within the same call. Moves must be allowed (the library checks

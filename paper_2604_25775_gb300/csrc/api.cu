@@ -545,6 +545,9 @@ scale_status scale_sweep(scale_ctx* c, int32_t n_steps, const int32_t* pick, con
     const bool due = (k % kSweepRefreshStride) == kSweepRefreshStride - 1 || k == n_steps - 1;
     SCALE_TRY(c, refresh_samples(c, false, due));
   }
+  // The Metropolis commits leave the cached G0t rows behind the inverse (keeping them current
+  // per accepted move costs more than the sweep's ratios save); one GEMM per sample restores them.
+  if (n_steps > 0) SCALE_TRY(c, launch_build_g0(c, c->B, nullptr, nullptr));
   return SCALE_OK;
 }
 

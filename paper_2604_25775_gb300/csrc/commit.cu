@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
   sv.HL = hb;
   sv.Binv = Bb;
   sv.Pt = Pb;
-  sv.G0t = Gb;
+  sv.G0t = metropolis ? nullptr : Gb;  // a sweep does not keep G0t current
   if (warp == 0) {
     if (lane == 0) {
       ms.kind = kind;
@@ -304,11 +304,44 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
       s_det = (double)det;
       s_drift_bits = 0ull;
     }
-  } else if (!singular) {
+  } else if (!singular && !metropolis) {
     // g_m[j] = (M0[o'_m] + proj_b) . Binv[j] for the moved orbitals: the cached G0t column
     for (int q = tid - 32; q < n_moved * Ne; q += kCommitThreads - 32) {
       const int m = q / Ne, j = q - m * Ne;
       g[m * NeP + j] = Gb[(size_t)j * No + (m ? om1 : om0)];
+    }
+  } else if (!singular) {
+    // a Metropolis sweep does not keep G0t current (scale_sweep rebuilds it at the end): the
+    // dot products against the inverse, four slots j per pass, lanes along k, every load of a
+    // pass in flight before the first use
+    constexpr int KU = 32 / sizeof(T);  // k values per lane per pass
+    for (int m = 0; m < n_moved; ++m) {
+      const T* m0b = net.M0b + (size_t)(m ? om1 : om0) * Ne;
+      for (int j0 = 4 * (warp - 1); j0 < Ne; j0 += 4 * (kCommitWarps - 1)) {
+        T v[4] = {T(0), T(0), T(0), T(0)};
+        for (int k0 = 0; k0 < Ne; k0 += 32 * KU) {
+          T x[KU], y[4][KU];
+#pragma unroll
+          for (int u = 0; u < KU; ++u) {
+            const int k = k0 + lane + 32 * u;
+            const bool on = k < Ne;
+            x[u] = on ? m0b[k] : T(0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) y[i][u] = (on && j0 + i < Ne) ? Bb[(size_t)(j0 + i) * Ne + k] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < KU; ++u)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] += x[u] * y[i][u];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          T sum = v[i];
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+          if (lane == 0 && j0 + i < Ne) g[m * NeP + j0 + i] = sum;
+        }
+      }
     }
   }
   __syncthreads();
@@ -347,10 +380,11 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
       for (int k = lane; k < Ne; k += 32) dst_row[k] = src_row[k];
     }
   }
-  for (int q = tid; q < r * No; q += kCommitThreads) {  // old G0t rows of the slots c_b
-    const int bi = q / No, o = q - bi * No;
-    Gc[q] = Gb[(size_t)ms.slot[bi] * No + o];
-  }
+  if (!metropolis)
+    for (int q = tid; q < r * No; q += kCommitThreads) {  // old G0t rows of the slots c_b
+      const int bi = q / No, o = q - bi * No;
+      Gc[q] = Gb[(size_t)ms.slot[bi] * No + o];
+    }
   for (int q = tid; q < 2 * kRMax * H; q += kCommitThreads) {
     const int sp = q / (kRMax * H), rem = q - sp * kRMax * H, bi = rem / H, c = rem - bi * H;
     T pc = T(0), y = T(0);
@@ -525,8 +559,10 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
     }
   }
   // (C3) G0t[j][o] -= sum_b D[b][j] Gc[b][o]: G0t[j] = (M0 + proj_b) Binv[j] is linear in
-  // Binv[j], so it takes the same rank-r step; a 4-row x V-column tile per thread
-  if (No % V == 0) {
+  // Binv[j], so it takes the same rank-r step; a 4-row x V-column tile per thread (not in a
+  // Metropolis sweep, which rebuilds G0t once at its end)
+  if (metropolis) {
+  } else if (No % V == 0) {
     // two tiles per thread (rows j0.. and j0 + 4..), both loaded before the updates: twice the
     // bytes in flight per thread of this streaming step
     const int nov = No / V, ntile = nquad * nov;

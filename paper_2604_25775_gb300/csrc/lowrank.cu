@@ -344,17 +344,22 @@ __global__ void __launch_bounds__(256) k_build_g0(int Ne, int No, const T* __res
 }
 
 template <typename T>
+cudaError_t build_g0_t(scale_ctx* c, int B, const int32_t* list, const int32_t* count) {
+  const int No = 2 * c->N;
+  const dim3 g0grid((c->Ne + 63) / 64, (No + 63) / 64, count ? std::min(B, 256) : std::min(B, 65535));
+  k_build_g0<T><<<g0grid, 256, 0, c->stream>>>(c->Ne, No, (const T*)c->Binv, (const T*)c->M0b, (T*)c->G0t, list, B,
+                                               count);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t project_t(scale_ctx* c, int B, const int32_t* list, const int32_t* count) {
   dim3 grid((c->Ne + 31) / 32, count ? std::min(B, 1024) : B);
   k_project<T><<<grid, 256, 0, c->stream>>>(c->Ne, c->h, make_net<T>(c).proj_w, (const T*)c->Binv, (T*)c->Pt, list,
                                             B, count);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int No = 2 * c->N;
-  const dim3 g0grid((c->Ne + 63) / 64, (No + 63) / 64, count ? std::min(B, 256) : std::min(B, 65535));
-  k_build_g0<T><<<g0grid, 256, 0, c->stream>>>(c->Ne, No, (const T*)c->Binv, (const T*)c->M0b, (T*)c->G0t, list, B,
-                                               count);
-  return cudaGetLastError();
+  return build_g0_t<T>(c, B, list, count);
 }
 
 }  // namespace
@@ -383,6 +388,10 @@ cudaError_t launch_ratios(scale_ctx* c, const int32_t* moves, int M, double* rat
 
 cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list, const int32_t* count) {
   return c->fp64 ? project_t<double>(c, B, list, count) : project_t<float>(c, B, list, count);
+}
+
+cudaError_t launch_build_g0(scale_ctx* c, int B, const int32_t* list, const int32_t* count) {
+  return c->fp64 ? build_g0_t<double>(c, B, list, count) : build_g0_t<float>(c, B, list, count);
 }
 
 }  // namespace scale

@@ -56,7 +56,7 @@ struct SampleView {
   const T* HL;                 // [N][h]
   const T* Binv;               // [Ne][Ne]
   const T* Pt;                 // [2][Ne][h]
-  const T* G0t;                // [Ne][2N]: (M0[o] + proj_b[s(o)]) . Binv[j], kept by every commit
+  const T* G0t;                // [Ne][2N]: (M0[o] + proj_b[s(o)]) . Binv[j]; null: not current
 };
 
 // Site-wise layer weights as hi/lo mma fragments, TF32 or BF16 by `kind` (mixed mode); null
@@ -466,10 +466,47 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   }
   __syncwarp();
   }
-  // moved rows: + (M0[o'] + proj_b[s]) . Binv[c_b] = G0t[c_b][o'], one cached entry per lane
-  for (int a = 0; a < r; ++a) {
-    if (!ms.moved[a]) continue;
-    if (lane < r) ms.R[a][lane] += sv.G0t[(size_t)ms.slot[lane] * 2 * N + ms.orb[a]];
+  // moved rows: + (M0[o'] + proj_b[s]) . Binv[c_b] = G0t[c_b][o'], one cached entry per lane;
+  // without the cache (a Metropolis sweep, which does not keep it current) the dot products
+  // against the inverse, lanes split k, one warp reduction per b
+  if (sv.G0t) {
+    for (int a = 0; a < r; ++a) {
+      if (!ms.moved[a]) continue;
+      if (lane < r) ms.R[a][lane] += sv.G0t[(size_t)ms.slot[lane] * 2 * N + ms.orb[a]];
+    }
+  } else {
+    for (int a = 0; a < r; ++a) {
+      if (!ms.moved[a]) continue;
+      const T* m0b = net.M0b + (size_t)ms.orb[a] * Ne;
+      constexpr int KK = 7;  // k values per lane per pass (224 per warp: one pass at 16x16)
+      for (int b0 = 0; b0 < r; b0 += 4) {
+        T g[4] = {T(0), T(0), T(0), T(0)};
+        const T* br[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) br[q] = sv.Binv + (size_t)ms.slot[min(b0 + q, r - 1)] * Ne;
+        for (int k0 = 0; k0 < Ne; k0 += 32 * KK) {
+          T v[KK], bv[4][KK];
+#pragma unroll
+          for (int u = 0; u < KK; ++u) {
+            const int k = k0 + lane + 32 * u;
+            const bool on = k < Ne;
+            v[u] = on ? m0b[k] : T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bv[q][u] = on ? br[q][k] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < KK; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g[q] += v[u] * bv[q][u];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) g[q] += __shfl_xor_sync(0xffffffffu, g[q], off);
+          if (lane == b0 + q && b0 + q < r) ms.R[a][lane] += g[q];
+        }
+      }
+    }
   }
   __syncwarp();
   return r;

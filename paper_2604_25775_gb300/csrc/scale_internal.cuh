@@ -300,6 +300,8 @@ cudaError_t launch_gj(scale_ctx* c, const double* Phi, int n, int B, const int32
                       bool inverse, bool out_fp64, void* Binv, double* logabs, int32_t* sign,
                       int32_t* status);
 cudaError_t launch_projector(scale_ctx* c, int B, const int32_t* list, const int32_t* count = nullptr);
+// G0t = (M0 + proj_b) Binv^T of the listed samples (all B when list is null).
+cudaError_t launch_build_g0(scale_ctx* c, int B, const int32_t* list, const int32_t* count = nullptr);
 cudaError_t launch_build_ke(scale_ctx* c);
 cudaError_t launch_build_wfrag(scale_ctx* c);
 cudaError_t launch_eloc_lowrank_list(scale_ctx* c, const int32_t* list, int n, double* eloc);
