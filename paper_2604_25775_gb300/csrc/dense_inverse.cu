@@ -61,12 +61,55 @@ __device__ __forceinline__ void key_merge(K& k, int& i, K k2, int i2) {
   }
 }
 
-template <typename TW>
-__device__ __forceinline__ void argmax_merge(TW& v, int& i, TW v2, int i2) {
-  if (v2 > v || (v2 == v && i2 < i)) {
-    v = v2;
-    i = i2;
+// Largest key over the warp (ties to the lowest row); the result is valid on lane 0.
+template <typename K>
+__device__ __forceinline__ void warp_key_max(K& k, int& i) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const K k2 = __shfl_down_sync(0xffffffffu, k, off);
+    const int i2 = __shfl_down_sync(0xffffffffu, i, off);
+    key_merge(k, i, k2, i2);
   }
+}
+
+// Pivot row of panel column jj: the largest |value| among the rows not yet pivoted, ties to
+// the lowest row. Each thread scans its rows, each warp merges its lanes, and warp 0 merges
+// the warps' winners; the row (n if none) is returned on thread 0 only.
+template <typename TW, int NT>
+__device__ __forceinline__ int pivot_search(const TW* panel, int ldp, int jj, int n, const unsigned char* used,
+                                            typename AbsKey<TW>::T* red_k, int* red_i) {
+  using KeyT = typename AbsKey<TW>::T;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  KeyT bk = 0;
+  int bi = n;
+  for (int i = tid; i < n; i += NT) {
+    if (used[i]) continue;
+    key_merge(bk, bi, AbsKey<TW>::of(panel[i * ldp + jj]), i);
+  }
+  warp_key_max(bk, bi);
+  if (lane == 0) {
+    red_k[warp] = bk;
+    red_i[warp] = bi;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    bk = lane < NT / 32 ? red_k[lane] : KeyT(0);
+    bi = lane < NT / 32 ? red_i[lane] : n;
+    warp_key_max(bk, bi);
+  }
+  return bi;
+}
+
+// log|det| = sum_k log|pivot_k| by warp 0: one log per lane at a time, then a warp tree
+// (the result is valid on thread 0).
+__device__ __forceinline__ double sum_log_pivots(const double* pabs, int n, bool skip) {
+  const int lane = threadIdx.x & 31;
+  double part = 0.0;
+  if (!skip)
+    for (int k = lane; k < n; k += 32) part += log(pabs[k]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+  return part;
 }
 
 // TW: working precision; TOUT: inverse output precision.
@@ -74,16 +117,18 @@ __device__ __forceinline__ void argmax_merge(TW& v, int& i, TW v2, int i2) {
 // determinant-only path runs 256-thread CTAs with 8-column panels, several per SM, so that
 // one matrix's serial pivot steps overlap the trailing updates of the others (measured on
 // 1024 matrices of 224: W 8 / 256 threads 1.8x faster than W 16 / 1024 threads).
+//
+// The FP64 pipe of sm_103a issues one warp-wide DFMA per SM sub-partition about every 64
+// cycles, so the serial part of a pivot step (search, reciprocal, log) is kept off it: the
+// search compares integer keys, one thread takes the reciprocal and shares it, and the logs
+// of the pivots are summed by all threads at the end.
 template <typename TW, typename TOUT, bool kInverse, int W, int TH = kThreads>
 __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const int32_t* __restrict__ list,
                                                  TOUT* __restrict__ binv, double* __restrict__ logabs_out,
                                                  int32_t* __restrict__ sign_out, int32_t* __restrict__ status) {
+  static_assert((W & (W - 1)) == 0, "the panel width is a power of two");
   extern __shared__ unsigned char smem_raw[];
   using KeyT = typename AbsKey<TW>::T;
-  // small determinant-only CTAs (several matrices per SM): integer-key pivot search, log|pivot|
-  // summed by all threads at the end, one column per lane; the 1024-thread kernels keep FP
-  // compares, the running log and two columns per lane (their registers stay unspilled)
-  constexpr bool kLean = !kInverse && TH <= 512;
   double* pabs = reinterpret_cast<double*>(smem_raw);  // [n] |pivot| of column k (log taken at the end)
   TW* panel = reinterpret_cast<TW*>(pabs + n);         // [n][W]
   TW* prow = panel + (size_t)n * W;              // [W][n]
@@ -93,9 +138,8 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
   int* qinv = piv + n;                           // [n] column whose pivot row is r
   unsigned char* used = reinterpret_cast<unsigned char*>(qinv + n);  // [n]
   __shared__ KeyT red_k[TH / 32];
-  __shared__ TW red_v[TH / 32];
   __shared__ int red_i[TH / 32];
-  __shared__ double red_l[TH / 32];
+  __shared__ TW s_inv;
   __shared__ int s_p;
   __shared__ int s_singular;
 
@@ -106,89 +150,50 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
 
   for (int i = tid; i < n; i += TH) used[i] = 0;
   if (tid == 0) s_singular = 0;
-  double logdet = 0.0;  // inverse mode: kept by thread 0
-  int sgn = 1;          // kept by thread 0
+  int sgn = 1;  // kept by thread 0
   __syncthreads();
 
   for (int K0 = 0; K0 < n; K0 += W) {
     const int w = min(W, n - K0);
     // panel <- columns [K0, K0+w)
-    for (int q = tid; q < n * w; q += TH) {
-      const int i = q / w, j = q - i * w;
-      panel[i * W + j] = A[(size_t)i * n + K0 + j];
+    for (int q = tid; q < n * W; q += TH) {
+      const int i = q / W, j = q % W;
+      if (j < w) panel[q] = A[(size_t)i * n + K0 + j];
     }
     __syncthreads();
     for (int jj = 0; jj < w; ++jj) {
       const int k = K0 + jj;
-      // pivot search over unpivoted rows (largest |value|, ties to the lowest row); the
-      // determinant-only kernels compare integer keys, the inverse kernels FP values
-      int bi = n;
-      if constexpr (kLean) {
-        KeyT bk = 0;
-        for (int i = tid; i < n; i += TH) {
-          if (used[i]) continue;
-          key_merge(bk, bi, AbsKey<TW>::of(panel[i * W + jj]), i);
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          const KeyT k2 = __shfl_down_sync(0xffffffffu, bk, off);
-          const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
-          key_merge(bk, bi, k2, i2);
-        }
-        if (lane == 0) red_k[warp] = bk;
-      } else {
-        TW bv = TW(-1);
-        for (int i = tid; i < n; i += TH) {
-          if (used[i]) continue;
-          argmax_merge(bv, bi, TW(fabs(panel[i * W + jj])), i);
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          const TW v2 = __shfl_down_sync(0xffffffffu, bv, off);
-          const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
-          argmax_merge(bv, bi, v2, i2);
-        }
-        if (lane == 0) red_v[warp] = bv;
-      }
-      if (lane == 0) red_i[warp] = bi;
-      __syncthreads();
+      const int bi = pivot_search<TW, TH>(panel, W, jj, n, used, red_k, red_i);
       if (tid == 0) {
-        int i = red_i[0];
-        if constexpr (kLean) {
-          KeyT kk = red_k[0];
-          for (int q = 1; q < TH / 32; ++q) key_merge(kk, i, red_k[q], red_i[q]);
-        } else {
-          TW v = red_v[0];
-          for (int q = 1; q < TH / 32; ++q) argmax_merge(v, i, red_v[q], red_i[q]);
-        }
-        if (i >= n || !(fabs(panel[i * W + jj]) > TW(0))) {
+        if (bi >= n || !(fabs(panel[bi * W + jj]) > TW(0))) {
           s_singular = 1;
-          i = 0;
+        } else {
+          const TW pv = panel[bi * W + jj];
+          s_inv = TW(1) / pv;
+          s_p = bi;
+          piv[k] = bi;
+          used[bi] = 1;
+          pabs[k] = fabs((double)pv);
+          if (pv < TW(0)) sgn = -sgn;
         }
-        s_p = i;
       }
       __syncthreads();
       if (s_singular) break;
       const int p = s_p;
-      const TW pv = panel[p * W + jj];
-      const TW inv = TW(1) / pv;
+      const TW inv = s_inv;
       // snapshot the pivot row (panel part) and column jj before updating
       for (int j = tid; j < w; j += TH) rowp[j] = (j == jj) ? inv : panel[p * W + j] * inv;
       for (int i = tid; i < n; i += TH) colk[i] = panel[i * W + jj];
-      if (tid == 0) {
-        piv[k] = p;
-        used[p] = 1;
-        if constexpr (!kLean) logdet += log(fabs((double)pv));
-        else pabs[k] = fabs((double)pv);
-        if (pv < TW(0)) sgn = -sgn;
-      }
       __syncthreads();
-      for (int q = tid; q < n * w; q += TH) {
-        const int i = q / w, j = q - i * w;
+      for (int q = tid; q < n * W; q += TH) {
+        const int i = q / W, j = q % W;
+        if (j >= w) continue;
         if (i == p) {
-          panel[i * W + j] = rowp[j];
+          panel[q] = rowp[j];
         } else if (kInverse || !used[i]) {
           const TW f = colk[i];
-          const TW base = (j == jj) ? TW(0) : panel[i * W + j];
-          panel[i * W + j] = base - f * rowp[j];
+          const TW base = (j == jj) ? TW(0) : panel[q];
+          panel[q] = base - f * rowp[j];
         }
       }
       __syncthreads();
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
     }
     __syncthreads();
     // rank-w update of the columns outside the panel: warp per row, lanes over columns,
-    // the row's multipliers u_j = U[i][j] in registers, two columns per lane in flight
+    // the row's multipliers u_j = U[i][j] in registers
     const int c_lo = kInverse ? 0 : K0 + w;
     for (int i = warp; i < n; i += TH / 32) {
       if (!kInverse && used[i]) continue;
@@ -209,10 +214,9 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
 #pragma unroll
       for (int j = 0; j < W; ++j) u[j] = (j < w) ? panel[i * W + j] - ((piv[K0 + j] == i) ? TW(1) : TW(0)) : TW(0);
       TW* Ai = A + (size_t)i * n;
-      if constexpr (kLean) {
+      if constexpr (!kInverse) {
         // determinant only: every column from c_lo on lies right of the panel; one column
-        // per lane (several matrices per SM supply the parallelism), so a strip wastes at most
-        // 31 lanes instead of 63
+        // per lane, so a strip wastes at most 31 lanes
         for (int c = c_lo + lane; c < n; c += 32) {
           TW a1 = Ai[c];
 #pragma unroll
@@ -222,42 +226,43 @@ __global__ void __launch_bounds__(TH) k_gj(TW* __restrict__ mats, int n, const i
         }
         continue;
       }
-      for (int c = c_lo + lane; c < n; c += 64) {
+      // inverse: every column; two columns per lane in flight while both lie inside the
+      // row, then the odd strip alone (no strip runs with its lanes idle); the panel
+      // columns are written back from the panel below
+      int c = lane;
+      for (; c + 32 < n; c += 64) {
         const int c2 = c + 32;
         const bool in1 = !(c >= K0 && c < K0 + w);
-        const bool in2 = c2 < n && !(c2 >= K0 && c2 < K0 + w);
+        const bool in2 = !(c2 >= K0 && c2 < K0 + w);
         TW a1 = in1 ? Ai[c] : TW(0);
         TW a2 = in2 ? Ai[c2] : TW(0);
 #pragma unroll
         for (int j = 0; j < W; ++j) {
           if (j < w) {
             a1 += u[j] * prow[j * n + c];
-            if (c2 < n) a2 += u[j] * prow[j * n + c2];
+            a2 += u[j] * prow[j * n + c2];
           }
         }
         if (in1) Ai[c] = a1;
         if (in2) Ai[c2] = a2;
       }
+      if (c < n && !(c >= K0 && c < K0 + w)) {
+        TW a1 = Ai[c];
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w) a1 += u[j] * prow[j * n + c];
+        Ai[c] = a1;
+      }
     }
     // write the swept panel back
-    for (int q = tid; q < n * w; q += TH) {
-      const int i = q / w, j = q - i * w;
-      A[(size_t)i * n + K0 + j] = panel[i * W + j];
+    for (int q = tid; q < n * W; q += TH) {
+      const int i = q / W, j = q % W;
+      if (j < w) A[(size_t)i * n + K0 + j] = panel[q];
     }
     __syncthreads();
   }
 
-  // determinant only: log|det| = sum of log|pivot|, one log per thread
-  if constexpr (kLean) {
-    double part = 0.0;
-    if (!s_singular)
-      for (int k = tid; k < n; k += TH) part += log(pabs[k]);
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-    if (lane == 0) red_l[warp] = part;
-    __syncthreads();
-    if (tid == 0)
-      for (int q = 0; q < TH / 32; ++q) logdet += red_l[q];
-  }
+  const double logdet = warp == 0 ? sum_log_pivots(pabs, n, s_singular != 0) : 0.0;  // on thread 0
   if (tid == 0) {
     int st = 0;
     double la = logdet;
@@ -329,25 +334,25 @@ __global__ void __launch_bounds__(kThreads) k_gj_cluster(double* __restrict__ ma
   const int bpc = (nblocks + C - 1) / C;  // blocks per CTA
   const int c_lo = min(n, q * bpc * W), c_hi = min(n, (q + 1) * bpc * W);
   const int ncol = c_hi - c_lo, ldp = bpc * W;
-  double* panels = reinterpret_cast<double*>(smem_raw);  // [2][n][W]
+  double* pabs = reinterpret_cast<double*>(smem_raw);    // [n] |pivot| of the columns this CTA owns
+  double* panels = pabs + n;                             // [2][n][W]
   double* prow = panels + (size_t)2 * n * W;             // [W][ldp]
   double* colk = prow + (size_t)W * ldp;                 // [n]
   double* rowp = colk + n;                               // [W]
   int* piv = reinterpret_cast<int*>(rowp + W);           // [n]
   int* qinv = piv + n;                                   // [n]
   unsigned char* used = reinterpret_cast<unsigned char*>(qinv + n);  // [n]
-  __shared__ double red_v[kThreads / 32];
+  __shared__ unsigned long long red_k[kThreads / 32];
   __shared__ int red_i[kThreads / 32];
+  __shared__ double s_inv;
   __shared__ int s_p;
   __shared__ int s_singular;
-  __shared__ double s_logdet;
   __shared__ int s_sgn;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < n; i += kThreads) used[i] = 0;
   if (tid == 0) {
     s_singular = 0;
-    s_logdet = 0.0;
     s_sgn = 1;
   }
   __syncthreads();
@@ -359,64 +364,43 @@ __global__ void __launch_bounds__(kThreads) k_gj_cluster(double* __restrict__ ma
     const int owner = blk / bpc;
     double* panel = panels + (size_t)(blk & 1) * n * W;
     if (q == owner) {
-      // log|det| continues from the previous block's owner, so the pivots are summed in
-      // order exactly as in k_gj (that owner no longer changes its total)
-      if (tid == 0 && blk > 0 && (blk - 1) / bpc != q) s_logdet = *cluster.map_shared_rank(&s_logdet, (blk - 1) / bpc);
-      for (int e = tid; e < n * w; e += kThreads) {
-        const int i = e / w, j = e - i * w;
-        panel[i * W + j] = A[(size_t)i * n + K0 + j];
+      for (int e = tid; e < n * W; e += kThreads) {
+        const int i = e / W, j = e % W;
+        if (j < w) panel[e] = A[(size_t)i * n + K0 + j];
       }
       __syncthreads();
       for (int jj = 0; jj < w; ++jj) {
         const int k = K0 + jj;
-        double bv = -1.0;
-        int bi = n;
-        for (int i = tid; i < n; i += kThreads) {
-          if (used[i]) continue;
-          argmax_merge(bv, bi, fabs(panel[i * W + jj]), i);
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          const double v2 = __shfl_down_sync(0xffffffffu, bv, off);
-          const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
-          argmax_merge(bv, bi, v2, i2);
-        }
-        if (lane == 0) {
-          red_v[warp] = bv;
-          red_i[warp] = bi;
-        }
-        __syncthreads();
+        const int bi = pivot_search<double, kThreads>(panel, W, jj, n, used, red_k, red_i);
         if (tid == 0) {
-          double v = red_v[0];
-          int i = red_i[0];
-          for (int r = 1; r < kThreads / 32; ++r) argmax_merge(v, i, red_v[r], red_i[r]);
-          if (!(v > 0.0) || i >= n) {
+          if (bi >= n || !(fabs(panel[bi * W + jj]) > 0.0)) {
             s_singular = 1;
-            i = 0;
+          } else {
+            const double pv = panel[bi * W + jj];
+            s_inv = 1.0 / pv;
+            s_p = bi;
+            piv[k] = bi;
+            used[bi] = 1;
+            pabs[k] = fabs(pv);
+            if (pv < 0.0) s_sgn = -s_sgn;
           }
-          s_p = i;
         }
         __syncthreads();
         if (s_singular) break;
         const int p = s_p;
-        const double pv = panel[p * W + jj];
-        const double inv = 1.0 / pv;
+        const double inv = s_inv;
         for (int j = tid; j < w; j += kThreads) rowp[j] = (j == jj) ? inv : panel[p * W + j] * inv;
         for (int i = tid; i < n; i += kThreads) colk[i] = panel[i * W + jj];
-        if (tid == 0) {
-          piv[k] = p;
-          used[p] = 1;
-          s_logdet += log(fabs(pv));
-          if (pv < 0.0) s_sgn = -s_sgn;
-        }
         __syncthreads();
-        for (int e = tid; e < n * w; e += kThreads) {
-          const int i = e / w, j = e - i * w;
+        for (int e = tid; e < n * W; e += kThreads) {
+          const int i = e / W, j = e % W;
+          if (j >= w) continue;
           if (i == p) {
-            panel[i * W + j] = rowp[j];
+            panel[e] = rowp[j];
           } else {
             const double f = colk[i];
-            const double base = (j == jj) ? 0.0 : panel[i * W + j];
-            panel[i * W + j] = base - f * rowp[j];
+            const double base = (j == jj) ? 0.0 : panel[e];
+            panel[e] = base - f * rowp[j];
           }
         }
         __syncthreads();
@@ -431,10 +415,8 @@ __global__ void __launch_bounds__(kThreads) k_gj_cluster(double* __restrict__ ma
     if (q != owner) {
       const double* o_panel = cluster.map_shared_rank(panel, owner);
       const int* o_piv = cluster.map_shared_rank(piv, owner);
-      for (int e = tid; e < n * w; e += kThreads) {
-        const int i = e / w, j = e - i * w;
-        panel[i * W + j] = o_panel[i * W + j];
-      }
+      for (int e = tid; e < n * W; e += kThreads)
+        if (e % W < w) panel[e] = o_panel[e];
       for (int j = tid; j < w; j += kThreads) piv[K0 + j] = o_piv[K0 + j];
       __syncthreads();
       for (int j = tid; j < w; j += kThreads) used[piv[K0 + j]] = 1;
@@ -451,57 +433,72 @@ __global__ void __launch_bounds__(kThreads) k_gj_cluster(double* __restrict__ ma
 #pragma unroll
       for (int j = 0; j < W; ++j) u[j] = (j < w) ? panel[i * W + j] - ((piv[K0 + j] == i) ? 1.0 : 0.0) : 0.0;
       double* Ai = A + (size_t)i * n;
-      for (int c = c_lo + lane; c < c_hi; c += 64) {
+      int c = c_lo + lane;
+      for (; c + 32 < c_hi; c += 64) {
         const int c2 = c + 32;
         const bool in1 = !(c >= K0 && c < K0 + w);
-        const bool in2 = c2 < c_hi && !(c2 >= K0 && c2 < K0 + w);
+        const bool in2 = !(c2 >= K0 && c2 < K0 + w);
         double a1 = in1 ? Ai[c] : 0.0;
         double a2 = in2 ? Ai[c2] : 0.0;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
           if (j < w) {
             a1 += u[j] * prow[j * ldp + (c - c_lo)];
-            if (c2 < c_hi) a2 += u[j] * prow[j * ldp + (c2 - c_lo)];
+            a2 += u[j] * prow[j * ldp + (c2 - c_lo)];
           }
         }
         if (in1) Ai[c] = a1;
         if (in2) Ai[c2] = a2;
       }
+      if (c < c_hi && !(c >= K0 && c < K0 + w)) {
+        double a1 = Ai[c];
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w) a1 += u[j] * prow[j * ldp + (c - c_lo)];
+        Ai[c] = a1;
+      }
     }
     if (q == owner) {
-      for (int e = tid; e < n * w; e += kThreads) {
-        const int i = e / w, j = e - i * w;
-        A[(size_t)i * n + K0 + j] = panel[i * W + j];
+      for (int e = tid; e < n * W; e += kThreads) {
+        const int i = e / W, j = e % W;
+        if (j < w) A[(size_t)i * n + K0 + j] = panel[e];
       }
     }
     __syncthreads();
   }
-  cluster.sync();  // all pivots, determinants and flags final; no CTA reads another after this
-  if (q == 0 && tid == 0) {
-    double la = *cluster.map_shared_rank(&s_logdet, (nblocks - 1) / bpc);  // the running total
-    int sg = 1;
-    for (int r = 0; r < C; ++r) sg *= *cluster.map_shared_rank(&s_sgn, r);
-    if (singular) {
-      la = -INFINITY;
-      sg = 0;
-      if (status) status[b] |= SCALE_SAMPLE_SINGULAR;
-    } else {
-      for (int k = 0; k < n; ++k) qinv[k] = 0;
-      int parity = 0;
-      for (int k = 0; k < n; ++k) {
-        if (qinv[k]) continue;
-        int j = k, len = 0;
-        while (!qinv[j]) {
-          qinv[j] = 1;
-          j = piv[j];
-          ++len;
+  cluster.sync();  // all pivots and flags final: rank 0 gathers the pivots of every block
+  if (q == 0) {
+    // each column's pivot from the CTA that owns its block, summed as in k_gj
+    if (!singular)
+      for (int k = tid; k < n; k += kThreads) pabs[k] = cluster.map_shared_rank(pabs, (k / W) / bpc)[k];
+    __syncthreads();
+    const double logdet = warp == 0 ? sum_log_pivots(pabs, n, singular) : 0.0;
+    if (tid == 0) {
+      double la = logdet;
+      int sg = 1;
+      for (int r = 0; r < C; ++r) sg *= *cluster.map_shared_rank(&s_sgn, r);
+      if (singular) {
+        la = -INFINITY;
+        sg = 0;
+        if (status) status[b] |= SCALE_SAMPLE_SINGULAR;
+      } else {
+        for (int k = 0; k < n; ++k) qinv[k] = 0;
+        int parity = 0;
+        for (int k = 0; k < n; ++k) {
+          if (qinv[k]) continue;
+          int j = k, len = 0;
+          while (!qinv[j]) {
+            qinv[j] = 1;
+            j = piv[j];
+            ++len;
+          }
+          parity += len - 1;
         }
-        parity += len - 1;
+        if (parity & 1) sg = -sg;
       }
-      if (parity & 1) sg = -sg;
+      if (logabs_out) logabs_out[b] = la;
+      if (sign_out) sign_out[b] = sg;
     }
-    if (logabs_out) logabs_out[b] = la;
-    if (sign_out) sign_out[b] = sg;
   }
   if (singular) {
     // zero this CTA's share of the rows of Binv
@@ -514,14 +511,15 @@ __global__ void __launch_bounds__(kThreads) k_gj_cluster(double* __restrict__ ma
       binv[(size_t)b * n * n + (size_t)piv[col] * n + cf] = (TOUT)A[(size_t)piv[cf] * n + col];
     }
   }
-  cluster.sync();  // rank 0 read the others' determinants
+  cluster.sync();  // rank 0 read the others' pivots and signs
 }
 
 template <typename TOUT, int W, int C>
 cudaError_t run_gj_cluster(cudaStream_t st, double* mats, int n, int B, const int32_t* list, TOUT* binv, double* la,
                            int32_t* sg, int32_t* status) {
   const int nblocks = (n + W - 1) / W, bpc = (nblocks + C - 1) / C;
-  const size_t smem = sizeof(double) * ((size_t)2 * n * W + (size_t)W * bpc * W + n + W) + sizeof(int) * 2 * n + n + 16;
+  const size_t smem =
+      sizeof(double) * ((size_t)n + 2 * n * W + (size_t)W * bpc * W + n + W) + sizeof(int) * 2 * n + n + 16;
   auto kern = k_gj_cluster<TOUT, W, C>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
