@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_commit(CommitArgs a, Net<
     }
     __syncwarp();
     move_features<T, H>(a.lat, net, a.k0, sv, a.mf, ms, z0n);
-    const int r = move_matrix<T, H>(a.lat, net, sv, ms);
+    const int r = move_matrix<T, H, true>(a.lat, net, sv, ms);
     T det = T(0);
     if (r > 0 && !singular) det = warp_inverse<T>(ms.R, Ri, r);
     if (lane == 0) {

@@ -335,7 +335,9 @@ __device__ void move_features(const Lattice& lat, const Net<T>& net, int k0, con
 
 // Step 4: the electron list on S after the move and the r x r matrix R. Returns r (valid in
 // all lanes), or -1 when r exceeds kRMax or a slot map is inconsistent.
-template <typename T, int H>
+// kDotFallback: sv.G0t may be null (a Metropolis commit), so the dot-product path is compiled
+// in; the local-energy and ratio kernels always have the cache and leave it out.
+template <typename T, int H, bool kDotFallback = false>
 __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleView<T>& sv, MoveScratch<T, H>& ms) {
   const int lane = threadIdx.x & 31;
   const int N = lat.N, Ne = lat.Ne, h = net.h;
@@ -469,12 +471,12 @@ __device__ int move_matrix(const Lattice& lat, const Net<T>& net, const SampleVi
   // moved rows: + (M0[o'] + proj_b[s]) . Binv[c_b] = G0t[c_b][o'], one cached entry per lane;
   // without the cache (a Metropolis sweep, which does not keep it current) the dot products
   // against the inverse, lanes split k, one warp reduction per b
-  if (sv.G0t) {
+  if (!kDotFallback || sv.G0t) {
     for (int a = 0; a < r; ++a) {
       if (!ms.moved[a]) continue;
       if (lane < r) ms.R[a][lane] += sv.G0t[(size_t)ms.slot[lane] * 2 * N + ms.orb[a]];
     }
-  } else {
+  } else if constexpr (kDotFallback) {
     for (int a = 0; a < r; ++a) {
       if (!ms.moved[a]) continue;
       const T* m0b = net.M0b + (size_t)ms.orb[a] * Ne;

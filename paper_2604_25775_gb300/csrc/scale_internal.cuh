@@ -103,20 +103,17 @@ struct Net {
   const T* KE;                   // [Ns][4][taps0][h]
 };
 
-// FP32 tanh for the tensor-core layers, from the odd Taylor series
-//   tanh z = z - z^3/3 + 2z^5/15 - 17z^7/315 + 62z^9/2835 - 1382z^11/155925
-//            + 21844z^13/6081075 - 929569z^15/638512875 + ...
-// for |z| < 0.5 (the first omitted term is below 1e-8 relative there), and from
-// tanh|z| = (1 - e^{-2|z|}) / (1 + e^{-2|z|}) above (no cancellation once |z| >= 0.5).
-__device__ __forceinline__ float tanh_f32_small(float z) {  // the series branch, |z| < 0.5
+// FP32 tanh for the tensor-core layers. For |z| < 1/2, tanh z = z + z s q(s) with s = z^2 and
+// q the cubic that minimises the largest relative error on (0, 1/2] (1.5e-8, below the FP32
+// rounding; fitted by fit_tanh_poly.py beside this file: tanh z = z - z^3/3 + 2z^5/15 - ...,
+// so q(0) = -1/3); above, tanh|z| = (1 - e^{-2|z|}) / (1 + e^{-2|z|}) (no cancellation once
+// |z| >= 1/2).
+__device__ __forceinline__ float tanh_f32_small(float z) {  // |z| < 1/2
   const float s = z * z;
-  float p = -929569.f / 638512875.f;
-  p = fmaf(p, s, 21844.f / 6081075.f);
-  p = fmaf(p, s, -1382.f / 155925.f);
-  p = fmaf(p, s, 62.f / 2835.f);
-  p = fmaf(p, s, -17.f / 315.f);
-  p = fmaf(p, s, 2.f / 15.f);
-  p = fmaf(p, s, -1.f / 3.f);
+  float p = 1.724151708e-02f;
+  p = fmaf(p, s, -5.304550752e-02f);
+  p = fmaf(p, s, 1.332587898e-01f);
+  p = fmaf(p, s, -3.333314359e-01f);
   return fmaf(z * s, p, z);
 }
 __device__ __forceinline__ float tanh_f32(float z) {
