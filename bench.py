@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--full-samples", type=int, default=128)
     ap.add_argument("--cpu-samples", type=int, default=48)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--precision", default=None, choices=list(PRECISIONS),
+                    help="site-wise layers as three TF32 (mixed), FP16 (mixed_fp16) or BF16 (mixed_bf16) "
+                         "tensor-core products; default: the workload's mode (hubbard16x16: mixed_fp16)")
     ap.add_argument("--lowrank-kernel", default="warp", choices=["warp", "batched"],
                     help="low-rank local-energy kernel of the timed chain step")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -256,6 +259,10 @@ def lowrank_flops_per_sample(pb, occ, n=32):
     return tot / min(n, occ.shape[0])
 
 
+# --precision: the mode of the site-wise tensor-core layers (everything else as in mixed mode)
+PRECISIONS = {"mixed": I.PREC_MIXED, "mixed_fp16": I.PREC_MIXED_FP16, "mixed_bf16": I.PREC_MIXED_BF16}
+
+
 def run_reference(args, world, rank):
     """The oracle (FP64 CPU, full recompute), as it stands, on the host cores: each step a
     bounded sample of walkers of the same workload."""
@@ -307,6 +314,8 @@ def main():
     Bd.load_library(build=True)
 
     pb = I.workload(args.workload)
+    if args.precision:
+        pb = pb.replace(precision=PRECISIONS[args.precision])
     if args.lowrank_kernel == "batched":
         pb = pb.replace(lowrank_kernel=I.LOWRANK_BATCHED)
     B, K, W = args.batch, args.steps, args.warmup
@@ -382,7 +391,7 @@ def main():
         "dtype": "f32 (rank-r, network) + f64 (LU refresh, accumulation)", "data": "synthetic",
         "config": workload_config(pb, args.workload, B, world),
         "step": "E_loc (low-rank) + 1 Woodbury commit per walker + staggered FP64 refresh",
-        "precision": "mixed",
+        "precision": {v: k for k, v in PRECISIONS.items()}.get(pb.precision, "fp64"),
         "e2e": {"value": e2e_val, "unit": "E_loc/s", "h2d_bytes_per_step": B * 4 * 4,
                 "d2h_bytes_per_step": B * 8},
         "stage_ms": {"eloc_lowrank": eloc_ms, "commit_and_refresh": commit_ms},
@@ -418,21 +427,30 @@ def main():
                         "eloc_per_s": B / ((load_ms + cold_eloc_ms) / 1e3)}
         ctx2.close()
         # the same local energies with the batched tensor-core kernel (site-wise layers of all
-        # moves on tcgen05; arch.lowrank_kernel = SCALE_LOWRANK_BATCHED)
-        ctxb = Bd.make_context(pb.replace(lowrank_kernel=I.LOWRANK_BATCHED), params, M0, B)
-        ctxb.scale_load(occ_d)
-        eb = torch.empty(B, dtype=torch.float64, device="cuda")
-        ctxb.scale_local_energy(eb)
-        torch.cuda.synchronize()
-        a.record()
-        ctxb.scale_local_energy(eb)
-        b2.record()
-        torch.cuda.synchronize()
-        bt_ms = a.elapsed_time(b2)
-        ctxb.close()
+        # moves on tcgen05; arch.lowrank_kernel = SCALE_LOWRANK_BATCHED), which runs the TF32x3
+        # products of SCALE_PREC_MIXED, beside the per-warp kernel in that mode
+        pb_t = pb.replace(precision=I.PREC_MIXED)
+        alt_ms = {}
+        for key, pbx in (("batched", pb_t.replace(lowrank_kernel=I.LOWRANK_BATCHED)), ("warp_tf32x3", pb_t)):
+            ctxb = Bd.make_context(pbx, params, M0, B)
+            ctxb.scale_load(occ_d)
+            eb = torch.empty(B, dtype=torch.float64, device="cuda")
+            ctxb.scale_local_energy(eb)
+            torch.cuda.synchronize()
+            a.record()
+            ctxb.scale_local_energy(eb)
+            b2.record()
+            torch.cuda.synchronize()
+            alt_ms[key] = a.elapsed_time(b2)
+            ctxb.close()
+        bt_ms = alt_ms["batched"]
         line["lowrank_batched_kernel"] = {"eloc_ms": bt_ms, "eloc_per_s": B / (bt_ms / 1e3),
+                                          "warp_kernel_tf32x3_eloc_ms": alt_ms["warp_tf32x3"],
                                           "warp_kernel_eloc_ms": eloc_ms,
-                                          "note": "same walkers as the cold load; the per-warp kernel is the default"}
+                                          "note": "same walkers as the cold load; the batched kernel runs the TF32x3 "
+                                                  "products (SCALE_PREC_MIXED), compare it with the per-warp kernel in "
+                                                  "that mode; the default is the per-warp kernel with the workload's "
+                                                  "products"}
         # Metropolis sweep on the same walkers: hop proposal, rank-r ratio, accept, Woodbury
         # commit of the accepted moves (random numbers generated on the host beforehand). The
         # first --sweep-steps are timed; the sweep then continues untimed to 2.5 N steps per

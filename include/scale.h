@@ -93,7 +93,7 @@ enum { SCALE_FAMILY_SCALE = 0, SCALE_FAMILY_ACE = 1, SCALE_FAMILY_WIDE = 2 };
  * (k - 1) / 2 (k = 5: the 13 sites of SCALE-L, Table tab:model); a kernel holds weights for
  * its taps only, [taps][c_in][c_out], taps in row-major box order. */
 enum { SCALE_STENCIL_BOX = 0, SCALE_STENCIL_DISK = 1 };
-enum { SCALE_PREC_FP64 = 0, SCALE_PREC_MIXED = 1, SCALE_PREC_MIXED_BF16 = 2 };
+enum { SCALE_PREC_FP64 = 0, SCALE_PREC_MIXED = 1, SCALE_PREC_MIXED_BF16 = 2, SCALE_PREC_MIXED_FP16 = 3 };
 enum { SCALE_PATH_LOWRANK = 0, SCALE_PATH_FULL = 1 };
 
 /* per-sample status bits */
@@ -128,6 +128,14 @@ typedef struct {
                              three TF32 products of a hi/lo split (FP32 accumulation),
                              other layers, rank-r algebra and cached Phi^-1 in FP32,
                              LU / log|det| / drift check / E_loc sums in FP64.
+                             SCALE_PREC_MIXED_FP16: as MIXED with three FP16 products
+                             (m16n8k16: half the MMA instructions of TF32), the
+                             activations scaled by 2^4 and each layer's weights by
+                             the power of two that puts max|W| in [1/2, 1) so that the
+                             lo parts stay normal, the accumulator scaled back exactly:
+                             about 2^-21 per layer like MIXED; the site-wise
+                             activations must stay below 4096 in magnitude. ACE and
+                             wide shapes run it as MIXED.
                              SCALE_PREC_MIXED_BF16: as MIXED with three BF16 products
                              (about 2^-16 per layer instead of 2^-21).
                              The tensor-core path needs the SCALE layout and h in

@@ -61,7 +61,8 @@ bool validate(const scale_system* s, const scale_arch* a, std::string* why) {
     if (a->h < 1 || a->h > kMaxH) return fail("h must be in [1, 64]");
   }
   if (a->act != SCALE_ACT_TANH && a->act != SCALE_ACT_SILU) return fail("unknown activation");
-  if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED && a->precision != SCALE_PREC_MIXED_BF16)
+  if (a->precision != SCALE_PREC_FP64 && a->precision != SCALE_PREC_MIXED && a->precision != SCALE_PREC_MIXED_BF16 &&
+      a->precision != SCALE_PREC_MIXED_FP16)
     return fail("unknown precision");
   if (a->refresh_every < 1) return fail("refresh_every must be >= 1");
   if (a->lowrank_kernel != SCALE_LOWRANK_WARP && a->lowrank_kernel != SCALE_LOWRANK_BATCHED)

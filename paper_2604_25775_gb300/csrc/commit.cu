@@ -807,7 +807,8 @@ cudaError_t commit_t(scale_ctx* c, const int32_t* moves, const int32_t* pick, co
   a.drift_max_bits = reinterpret_cast<unsigned long long*>(c->stat_dev);
   a.n_commits = reinterpret_cast<int32_t*>(c->stat_dev + 1);
   a.mf.wf = c->use_mma ? (const WFrag*)c->wfrag : nullptr;
-  a.mf.kind = c->arch.precision == SCALE_PREC_MIXED_BF16 ? kBF16 : kTF32;
+  a.mf.kind = mma_kind_of(c->arch.precision);
+  a.mf.oscale = c->use_mma && a.mf.kind == kFP16 ? fp16_scales(c) + kMaxLayers : nullptr;
   a.pick = pick;
   a.dir = dir;
   a.u = u;

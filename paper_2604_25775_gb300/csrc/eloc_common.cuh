@@ -170,7 +170,8 @@ inline LowrankArgs make_args(scale_ctx* c) {
   a.nb_nnn = c->nb_nnn;
   a.status = c->status;
   a.mf.wf = c->use_mma ? (const WFrag*)c->wfrag : nullptr;
-  a.mf.kind = c->arch.precision == SCALE_PREC_MIXED_BF16 ? kBF16 : kTF32;
+  a.mf.kind = mma_kind_of(c->arch.precision);
+  a.mf.oscale = c->use_mma && a.mf.kind == kFP16 ? fp16_scales(c) + kMaxLayers : nullptr;
   return a;
 }
 

@@ -231,7 +231,8 @@ __global__ void k_logpsi_out(int Ne, const int32_t* __restrict__ orb_of_slot, co
 template <int H, int KIND>
 __global__ void __launch_bounds__(256) k_mlp_fwd(Net<float> net, const WFrag* __restrict__ wf, int N, int B,
                                                  const int32_t* __restrict__ list, const float* __restrict__ in,
-                                                 float* __restrict__ out, const int32_t* __restrict__ count) {
+                                                 float* __restrict__ out, const int32_t* __restrict__ count,
+                                                 const float* __restrict__ oscale) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long row0 = (long long)warp * 16;
   // entries of the launch: B, or the first *count entries of a compacted list
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(256) k_mlp_fwd(Net<float> net, const WFrag* __
       x[j][2 * hh + 1] = keep[hh] ? in[drow[hh] * H + c + 1] : 0.f;
     }
   }
-  mlp_tile<H, KIND>(x, wf, net.bias, net.resid, net.L, net.act);
+  mlp_tile<H, KIND>(x, wf, net.bias, net.resid, net.L, net.act, oscale);
 #pragma unroll
   for (int j = 0; j < H / 8; ++j) {
     const int c = 8 * j + 2 * t;
@@ -278,11 +279,36 @@ __global__ void __launch_bounds__(256) k_mlp_fwd(Net<float> net, const WFrag* __
   }
 }
 
+// kFP16 scaling of the site-wise layers (l >= 1): with max|W_l| = f 2^e_l, f in [1/2, 1), the
+// fragments hold W_l 2^-e_l and the layer's accumulator is multiplied back by 2^e_l / 2^4
+// (both exact). One block per layer.
+__global__ void k_fp16_scales(Net<float> net, float* __restrict__ sc) {
+  const int l = blockIdx.x;
+  __shared__ float red[32];
+  float m = 0.f;
+  if (l >= 1 && net.ksize[l] == 1) {
+    const float* W = net.kernel[l];
+    for (int q = threadIdx.x; q < net.h * net.h; q += blockDim.x) m = fmaxf(m, fabsf(W[q]));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    int e = 0;
+    if (m > 0.f && isfinite(m)) frexpf(m, &e);
+    sc[l] = ldexpf(1.f, -e);
+    sc[kMaxLayers + l] = ldexpf(1.f, e) / kFp16InScale;
+  }
+}
+
 // hi/lo fragments of the site-wise weights W_l[c_in][c_out] (layers l >= 1):
-//   BF16: b0 = (W[16kk + 2t][8j + g], W[16kk + 2t + 1][8j + g]), b1 = the same at rows + 8;
+//   BF16 / FP16: b0 = (W[16kk + 2t][8j + g], W[16kk + 2t + 1][8j + g]), b1 = the same at rows + 8
+//                (FP16: W scaled by wsc[l]);
 //   TF32: b0 = W[8kk + 2t][8j + g], b1 = W[8kk + 2t + 1][8j + g] (permuted k, see mlp_mma.cuh).
 template <int H, int KIND>
-__global__ void k_build_wfrag(Net<float> net, WFrag* __restrict__ wf) {
+__global__ void k_build_wfrag(Net<float> net, WFrag* __restrict__ wf, const float* __restrict__ wsc) {
   constexpr int NT = MmaShape<H, KIND>::NT, KT = MmaShape<H, KIND>::KT;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int total = net.L * KT * NT * 32;
@@ -297,6 +323,11 @@ __global__ void k_build_wfrag(Net<float> net, WFrag* __restrict__ wf) {
       const int k0 = 8 * kk + 2 * t;
       split_tf32(W[(size_t)k0 * H + n], f.v[0], f.v[2]);
       split_tf32(W[(size_t)(k0 + 1) * H + n], f.v[1], f.v[3]);
+    } else if constexpr (KIND == kFP16) {
+      const int k0 = 16 * kk + 2 * t;
+      const float sw = wsc[l];
+      split2h(sw * W[(size_t)k0 * H + n], sw * W[(size_t)(k0 + 1) * H + n], f.v[0], f.v[2]);
+      split2h(sw * W[(size_t)(k0 + 8) * H + n], sw * W[(size_t)(k0 + 9) * H + n], f.v[1], f.v[3]);
     } else {
       const int k0 = 16 * kk + 2 * t;
       split2(W[(size_t)k0 * H + n], W[(size_t)(k0 + 1) * H + n], f.v[0], f.v[2]);
@@ -320,14 +351,22 @@ void build_wfrag_k(scale_ctx* c) {
   const Net<float> net = make_net<float>(c);
   const int total = c->L * (KIND == kTF32 ? c->hpad / 8 : c->hpad / 16) * (c->hpad / 8) * 32;
   const int blocks = (total + 255) / 256;
-  if (c->hpad == 16) k_build_wfrag<16, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag);
-  else if (c->hpad == 32) k_build_wfrag<32, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag);
-  else k_build_wfrag<64, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag);
+  const float* wsc = nullptr;
+  if constexpr (KIND == kFP16) {
+    float* sc = fp16_scales(c);
+    k_fp16_scales<<<c->L, 256, 0, c->stream>>>(net, sc);
+    wsc = sc;
+  }
+  if (c->hpad == 16) k_build_wfrag<16, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag, wsc);
+  else if (c->hpad == 32) k_build_wfrag<32, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag, wsc);
+  else k_build_wfrag<64, KIND><<<blocks, 256, 0, c->stream>>>(net, (WFrag*)c->wfrag, wsc);
 }
 
 cudaError_t launch_build_wfrag(scale_ctx* c) {
   if (!c->use_mma) return cudaSuccess;
-  if (c->arch.precision == SCALE_PREC_MIXED_BF16) build_wfrag_k<kBF16>(c);
+  const int kind = mma_kind_of(c->arch.precision);
+  if (kind == kBF16) build_wfrag_k<kBF16>(c);
+  else if (kind == kFP16) build_wfrag_k<kFP16>(c);
   else build_wfrag_k<kTF32>(c);
   return cudaGetLastError();
 }
@@ -392,15 +431,18 @@ cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* lis
       const Net<float> nf = make_net<float>(c);
       const WFrag* wf = (const WFrag*)c->wfrag;
       const float* fin = (const float*)in;
-      if (c->arch.precision == SCALE_PREC_MIXED_BF16) {
-        if (c->hpad == 16) k_mlp_fwd<16, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
-        else if (c->hpad == 32) k_mlp_fwd<32, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
-        else k_mlp_fwd<64, kBF16><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
-      } else {
-        if (c->hpad == 16) k_mlp_fwd<16, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
-        else if (c->hpad == 32) k_mlp_fwd<32, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
-        else k_mlp_fwd<64, kTF32><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count);
-      }
+      const int kind = mma_kind_of(c->arch.precision);
+      const float* osc = kind == kFP16 ? fp16_scales(c) + kMaxLayers : nullptr;
+#define SCALE_MLP_FWD(KIND)                                                                                     \
+  do {                                                                                                          \
+    if (c->hpad == 16) k_mlp_fwd<16, KIND><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count, osc); \
+    else if (c->hpad == 32) k_mlp_fwd<32, KIND><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count, osc); \
+    else k_mlp_fwd<64, KIND><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count, osc); \
+  } while (0)
+      if (kind == kBF16) SCALE_MLP_FWD(kBF16);
+      else if (kind == kFP16) SCALE_MLP_FWD(kFP16);
+      else SCALE_MLP_FWD(kTF32);
+#undef SCALE_MLP_FWD
       in = (const T*)out;
     }
   }

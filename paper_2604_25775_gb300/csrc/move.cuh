@@ -63,7 +63,8 @@ struct SampleView {
 // in FP64 mode.
 struct MlpFrags {
   const WFrag* wf;
-  int kind;  // kTF32 or kBF16
+  int kind;             // kTF32, kFP16 or kBF16
+  const float* oscale;  // kFP16: per-layer output factors (fp16_scales + kMaxLayers)
 };
 
 __device__ __forceinline__ int move_new_state(int kind, int spin, bool is_src, int n_src, int n_dst) {
@@ -320,6 +321,8 @@ __device__ void move_features(const Lattice& lat, const Net<T>& net, int k0, con
           tile_load<H>(x, &ms.feat[r0t][0], H, nS - r0t);
           if (mf.kind == kTF32)
             mlp_tile<H, kTF32>(x, mf.wf, net.bias, net.resid, net.L, net.act);
+          else if (mf.kind == kFP16)
+            mlp_tile<H, kFP16>(x, mf.wf, net.bias, net.resid, net.L, net.act, mf.oscale);
           else
             mlp_tile<H, kBF16>(x, mf.wf, net.bias, net.resid, net.L, net.act);
           __syncwarp();

@@ -44,6 +44,7 @@ STENCIL_DISK = 1  # offsets of the k x k box within L2 distance (k-1)/2 (k = 5: 
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_MIXED_BF16 = 2
+PREC_MIXED_FP16 = 3
 
 LOWRANK_WARP = 0     # low-rank local-energy kernels of the library (same results)
 LOWRANK_BATCHED = 1
@@ -376,10 +377,10 @@ def workload(name: str) -> Problem:
         ks, rs = scale_layout(4)
         return Problem(8, 8, 1, 1, 28, 28, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 4, 16, ks, rs,
                        ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
-    if name == "hubbard16x16":  # 16x16 torus, 112+112, 6 layers, 32 channels, mixed
+    if name == "hubbard16x16":  # 16x16 torus, 112+112, 6 layers, 32 channels, mixed (FP16x3 site-wise)
         ks, rs = scale_layout(6)
         return Problem(16, 16, 1, 1, 112, 112, MODEL_HUBBARD, 1.0, 0.0, 8.0, 0.0, 6, 32, ks, rs,
-                       ACT_TANH, 1, PREC_MIXED, 64, 1e-4)
+                       ACT_TANH, 1, PREC_MIXED_FP16, 64, 1e-4)
     if name == "cylinder16x4":  # periodic along 16, open along 4, t'=-0.2, 12 residual 3x3
         return Problem(16, 4, 1, 0, 28, 28, MODEL_HUBBARD, 1.0, -0.2, 8.0, 0.0, 12, 32,
                        [3] * 12, [1] * 12, ACT_TANH, 1, PREC_FP64, 64, 1e-10)

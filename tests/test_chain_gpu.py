@@ -11,7 +11,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("prec,tol,refresh", [(I.PREC_FP64, 1e-9, 1000), (I.PREC_FP64, 1e-9, 7),
-                                               (I.PREC_MIXED, 1e-4, 16), (I.PREC_MIXED_BF16, 5e-4, 16)])
+                                               (I.PREC_MIXED, 1e-4, 16), (I.PREC_MIXED_FP16, 1e-4, 16),
+                                               (I.PREC_MIXED_BF16, 5e-4, 16)])
 def test_commits_match_oracle(prec, tol, refresh):
     import torch
     pb = I.workload("hubbard8x8").replace(precision=prec, refresh_every=refresh, tp=-0.2,

@@ -5,8 +5,9 @@ Tolerances (relative error |x_gpu - x_ora| / max(|x_ora|, 1)):
   FP64 mode   E_loc, ratios, gradients <= 1e-10 and log|psi| absolute <= 1e-10 on samples
               with cond(Phi) <= 1e6; signs exact.
   mixed mode  E_loc, ratios, log|psi| <= 1e-4 on samples with cond(Phi) <= 1e3 (1e4 at 16x16,
-              where uniformly random configurations have cond >= 1e3) (TF32x3 layers);
-              the BF16x3 option <= 5e-4. On |psi|^2-distributed 16x16 walkers (after a
+              where uniformly random configurations have cond >= 1e3) with the site-wise layers
+              as TF32x3 or FP16x3 products (the 16x16 workload's mode); the BF16x3 option
+              <= 5e-4. On |psi|^2-distributed 16x16 walkers (after a
               Metropolis sweep) at least 90% within 1e-4 with no conditioning filter.
 Beyond those condition numbers every sample must still satisfy err <= cond * c * u with
 u = 2^-53 (FP64) or 2^-24 (mixed) and c = 1e3 (FP64) / 8 (mixed): an FP32-stored Phi^-1
@@ -138,7 +139,7 @@ def test_ratios_fp64():
     assert (rb[:, 0] == 0).all() and (rb[:, 1] == 1).all()
 
 
-@pytest.mark.parametrize("prec", [I.PREC_MIXED, I.PREC_MIXED_BF16])
+@pytest.mark.parametrize("prec", [I.PREC_MIXED, I.PREC_MIXED_FP16, I.PREC_MIXED_BF16])
 @pytest.mark.parametrize("name", ["hubbard8x8", "tj8x8", "hubbard_ph8x8"])
 def test_local_energy_mixed_8x8(name, prec):
     pb = I.workload(name).replace(precision=prec)
@@ -158,7 +159,7 @@ def test_local_energy_mixed_8x8(name, prec):
 @pytest.fixture(scope="module")
 def mixed16():
     """The 16x16 workload at its full batch (8192 walkers) in the bench's launch configuration
-    (TF32x3 site-wise layers); 64 sampled walkers recomputed by the oracle."""
+    (FP16x3 site-wise layers); 64 sampled walkers recomputed by the oracle."""
     pb = I.workload("hubbard16x16")
     pseed, cseed = I.workload_seeds("hubbard16x16")
     ctx, ora, occ, st = setup(pb, 8192, pseed, cseed)
@@ -183,11 +184,11 @@ def test_local_energy_mixed_16x16_full_batch_sampled(mixed16):
     """Low-rank path, 16x16 at the full batch, 64 sampled outputs against the oracle."""
     pb, ctx, ora, occ, pick, cond, e_o = mixed16
     e = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
-    _by_band("16x16 mixed lowrank", rel_err(e[pick], e_o), cond)
+    _by_band("16x16 mixed FP16x3 lowrank", rel_err(e[pick], e_o), cond)
     la, sg = ctx.log_psi()
     # uniformly random 16x16 configurations have cond(Phi) >= 1e3; the strict band is
     # cond < 1e4 here, every sample still within cond * 8 * 2^-24
-    _check("16x16 mixed lowrank (sampled)", e[pick], e_o, cond, MIXED_TOL, 1e4, min_good=5)
+    _check("16x16 mixed FP16x3 lowrank (sampled)", e[pick], e_o, cond, MIXED_TOL, 1e4, min_good=5)
     la_o, sg_o = ora.log_psi(occ[pick])
     good = cond < 1e4
     assert rel_err(la.cpu().numpy()[pick][good], la_o[good]).max() <= MIXED_TOL
@@ -224,17 +225,65 @@ def test_local_energy_mixed_16x16_bf16x3_sampled():
     assert np.isfinite(e).all()
 
 
+@pytest.mark.parametrize("scale", [0.002, 0.05, 0.5])
+def test_local_energy_mixed_fp16_weight_scales(scale):
+    """FP16x3 site-wise layers keep the lo parts of the split in FP16's normal range by
+    scaling the activations by 2^4 and each layer's weights by a power of two. For networks
+    whose weights are 25x smaller or 10x larger than the workloads', FP16x3 meets the mixed
+    bar where TF32x3 does (cond < 1e3), and over the walkers with cond < 1e4 its largest and
+    median errors stay within a factor 2 of TF32x3's on the same network and walkers (beyond
+    that both are bounded only by the conditioning)."""
+    errs = {}
+    for prec in (I.PREC_MIXED, I.PREC_MIXED_FP16):
+        pb = I.workload("hubbard8x8").replace(precision=prec)
+        ctx, ora, occ, st = setup(pb, 128, 1237, 5681, scale=scale)
+        cond = conditioning(ora, occ)
+        e = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+        e_o, _ = ora.local_energy(occ)
+        err = rel_err(e, e_o)
+        band = cond < 1e4
+        print(f"hubbard8x8 weights N(0, {scale}^2), precision {prec}: cond < 1e4: {band.sum()} walkers, "
+              f"max err {err[band].max():.2e}, median {np.median(err[band]):.2e}")
+        assert band.sum() >= 8
+        assert err[cond < 1e3].max(initial=0.0) <= MIXED_TOL
+        errs[prec] = err[band]
+        ctx.close()
+    # the same walkers (same seeds): the error distribution of FP16x3 no wider than TF32x3's
+    # (per walker the two roundings differ at random, so the maxima and medians are compared)
+    e16, e32 = errs[I.PREC_MIXED_FP16], errs[I.PREC_MIXED]
+    assert e16.max() <= max(2 * e32.max(), 2e-5)
+    assert np.median(e16) <= 2 * np.median(e32) + 1e-7
+
+
+def test_local_energy_mixed_16x16_tf32x3_sampled():
+    """The TF32x3 site-wise layers (SCALE_PREC_MIXED) at the full 16x16 batch: 64 sampled
+    walkers against the oracle in the same band as the bench's FP16x3 (1e-4 for cond < 1e4,
+    cond * 8 * 2^-24 above)."""
+    pb = I.workload("hubbard16x16").replace(precision=I.PREC_MIXED)
+    pseed, cseed = I.workload_seeds("hubbard16x16")
+    ctx, ora, occ, st = setup(pb, 8192, pseed, cseed)
+    e = ctx.local_energy(Bd.PATH_LOWRANK).cpu().numpy()
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(8192, 64, replace=False))
+    cond = conditioning(ora, occ[pick])
+    e_o, _ = ora.local_energy(occ[pick])
+    _by_band("16x16 mixed TF32x3 lowrank", rel_err(e[pick], e_o), cond)
+    _check("16x16 mixed TF32x3 lowrank (sampled)", e[pick], e_o, cond, MIXED_TOL, 1e4, min_good=5)
+    assert np.isfinite(e).all()
+
+
 EQ_FLOOR = 0.9  # fraction of |psi|^2-distributed 16x16 walkers within 1e-4 of the oracle
 
 
-def test_local_energy_mixed_16x16_equilibrated():
+@pytest.mark.parametrize("prec", [I.PREC_MIXED_FP16, I.PREC_MIXED])
+def test_local_energy_mixed_16x16_equilibrated(prec):
     """Walkers drawn from |psi|^2, as VMC evaluates them: the bench's 8192 walkers after
     2.5 N Metropolis steps each (scale_sweep; Woodbury-updated inverses with the staggered FP64
     refresh, as a chain holds them). 64 of them against the oracle with no conditioning
     filter: at least EQ_FLOOR of them within 1e-4 and every one within cond * 8 * 2^-24; the
     full-recompute path on the same 64 walkers in the same way."""
     import torch
-    pb = I.workload("hubbard16x16")
+    pb = I.workload("hubbard16x16").replace(precision=prec)
     pseed, cseed = I.workload_seeds("hubbard16x16")
     ctx, ora, occ, st = setup(pb, 8192, pseed, cseed)
     S = int(2.5 * pb.N)
@@ -249,7 +298,7 @@ def test_local_energy_mixed_16x16_equilibrated():
     e_o, _ = ora.local_energy(occ_eq[pick])
     err = rel_err(e[pick], e_o)
     frac = float(np.mean(err <= MIXED_TOL))
-    print(f"equilibrated 16x16: cond median {np.median(cond):.2e} max {cond.max():.2e}; "
+    print(f"equilibrated 16x16 (precision {prec}): cond median {np.median(cond):.2e} max {cond.max():.2e}; "
           f"E_loc err median {np.median(err):.2e} max {err.max():.2e}; within 1e-4: {frac:.3f}")
     assert frac >= EQ_FLOOR
     assert np.all(err <= np.maximum(MIXED_TOL, cond * 8 * 2.0 ** -24))
@@ -318,9 +367,10 @@ def test_local_energy_tensor_core_batched_8x8(variant):
 
 
 def test_batched_kernel_16x16_sampled():
-    """The batched tensor-core kernel on the 16x16 workload (1024 walkers): 16 sampled outputs
-    against the oracle in the strict band, and the whole batch against the per-warp kernel."""
-    pb = I.workload("hubbard16x16")
+    """The batched tensor-core kernel (TF32x3 products, SCALE_PREC_MIXED) on the 16x16 workload
+    (1024 walkers): 16 sampled outputs against the oracle in the strict band, and the whole
+    batch against the per-warp kernel in the same mode."""
+    pb = I.workload("hubbard16x16").replace(precision=I.PREC_MIXED)
     pseed, cseed = I.workload_seeds("hubbard16x16")
     ctx_w, ora, occ, st = setup(pb, 1024, pseed, cseed)
     ctx_b, _, _, _ = setup(pb.replace(lowrank_kernel=I.LOWRANK_BATCHED), 1024, pseed, cseed)
