@@ -261,6 +261,9 @@ def lowrank_flops_per_sample(pb, occ, n=32):
 
 # --precision: the mode of the site-wise tensor-core layers (everything else as in mixed mode)
 PRECISIONS = {"mixed": I.PREC_MIXED, "mixed_fp16": I.PREC_MIXED_FP16, "mixed_bf16": I.PREC_MIXED_BF16}
+DTYPES = {I.PREC_MIXED: "f32 (rank-r, network; site-wise layers as 3 tf32 tensor-core products) + f64 (LU refresh, accumulation)",
+          I.PREC_MIXED_FP16: "f32 (rank-r, network; site-wise layers as 3 f16 tensor-core products) + f64 (LU refresh, accumulation)",
+          I.PREC_MIXED_BF16: "f32 (rank-r, network; site-wise layers as 3 bf16 tensor-core products) + f64 (LU refresh, accumulation)"}
 
 
 def run_reference(args, world, rank):
@@ -388,7 +391,7 @@ def main():
         "metric": METRIC,
         "value": value, "unit": "E_loc/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (rank-r, network) + f64 (LU refresh, accumulation)", "data": "synthetic",
+        "dtype": DTYPES.get(pb.precision, "f64"), "data": "synthetic",
         "config": workload_config(pb, args.workload, B, world),
         "step": "E_loc (low-rank) + 1 Woodbury commit per walker + staggered FP64 refresh",
         "precision": {v: k for k, v in PRECISIONS.items()}.get(pb.precision, "fp64"),
