@@ -97,27 +97,27 @@ __device__ __forceinline__ double move_coeff(const Lattice& lat, uint32_t pm) {
 
 // Diagonal matrix element of configuration occ (shared-memory copy): Hubbard U * (doubly
 // occupied sites); particle-hole Hubbard U * (sites with an up particle and no transformed
-// down particle); t-J J sum_<ij> Sz_i Sz_j over the NN bonds. One thread.
+// down particle); t-J J sum_<ij> Sz_i Sz_j over the NN bonds, as (J/4) sum s_i s_j with the
+// integer s = n_up - n_dn. Called by a whole warp: integer counts over the lanes, a warp sum,
+// one FP64 multiply (FP64 instructions are scarce on this GPU: one thread looping over the
+// bonds in FP64 kept the CTA waiting for about 0.2M cycles); the value is returned to every lane.
 __device__ __forceinline__ double diag_energy(const LowrankArgs& a, const int8_t* occ_s) {
+  const int lane = threadIdx.x & 31;
   const int N = a.lat.N;
-  double d = 0.0;
+  int cnt = 0;
   if (a.lat.model == SCALE_MODEL_HUBBARD) {
-    int nd = 0;
-    for (int i = 0; i < N; ++i) nd += occ_s[i] == 3;
-    d = a.lat.U * nd;
+    for (int i = lane; i < N; i += 32) cnt += occ_s[i] == 3;
   } else if (a.lat.model == SCALE_MODEL_HUBBARD_PH) {
-    int nu = 0;
-    for (int i = 0; i < N; ++i) nu += occ_s[i] == 1;
-    d = a.lat.U * nu;
+    for (int i = lane; i < N; i += 32) cnt += occ_s[i] == 1;
   } else {
-    for (int q = 0; q < a.nb_nn; ++q) {
-      const int i = a.bonds[2 * q], j = a.bonds[2 * q + 1];
-      const double szi = 0.5 * ((occ_s[i] & 1) - ((occ_s[i] >> 1) & 1));
-      const double szj = 0.5 * ((occ_s[j] & 1) - ((occ_s[j] >> 1) & 1));
-      d += a.lat.J * szi * szj;
+    for (int q = lane; q < a.nb_nn; q += 32) {
+      const int oi = occ_s[a.bonds[2 * q]], oj = occ_s[a.bonds[2 * q + 1]];
+      cnt += ((oi & 1) - ((oi >> 1) & 1)) * ((oj & 1) - ((oj >> 1) & 1));
     }
   }
-  return d;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+  return a.lat.model == SCALE_MODEL_TJ ? (0.25 * a.lat.J) * cnt : a.lat.U * cnt;
 }
 
 // Number of candidate ids of a sample: 2 (NN + NNN bonds) hops, then NN exchanges (t-J).
