@@ -5,6 +5,7 @@
 #include <cstring>
 #include <vector>
 
+#include "mlp_mma.cuh"
 #include "scale_internal.cuh"
 
 using namespace scale;
@@ -367,7 +368,7 @@ scale_status scale_create(const scale_system* sys, const scale_arch* arch, int32
   A(&c->full_moves, B * cap * 16);
   A(&c->full_la_all, B * (cap + 1) * 8);
   A(&c->full_sg_all, B * (cap + 1) * 4);
-  if (c->use_mma) A((char**)&c->wfrag, (size_t)c->L * (c->hpad / 8) * (c->hpad / 8) * 32 * 16);
+  if (c->use_mma) A((char**)&c->wfrag, wfrag_bytes(c->L, c->hpad));
   if (c->ace_mma) A((char**)&c->ace_frag, ace_frag_bytes(*arch));
   A(&c->ace_err, 16);  // error word of the tensor-core kernels (bounded waits)
   {

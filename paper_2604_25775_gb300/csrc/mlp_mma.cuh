@@ -111,12 +111,20 @@ __host__ __device__ inline int mma_kind_of(int precision) {
   return precision == SCALE_PREC_MIXED_BF16 ? kBF16 : precision == SCALE_PREC_MIXED_FP16 ? kFP16 : kTF32;
 }
 
+// Bytes of the fragment buffer of a context: sized for TF32 (L x hpad/8 k-steps x hpad/8
+// n-tiles x 32 lanes).
+__host__ __device__ inline size_t wfrag_bytes(int L, int hpad) {
+  return (size_t)L * (hpad / 8) * (hpad / 8) * 32 * sizeof(WFrag);
+}
+
 // kFP16: the per-layer weight factors 2^-e_l ([kMaxLayers]) and output factors 2^e_l / 2^4
-// ([kMaxLayers]) sit behind the fragments in the fragment buffer, which is sized for TF32
-// (FP16 fragments take half of it).
+// ([kMaxLayers]) sit behind the fragments in the fragment buffer (FP16 fragments take half of
+// it; the other half, at least 1 KB, holds the 2 x kMaxLayers factors).
 __host__ __device__ inline size_t fp16_scale_offset(int L, int hpad) {
   return (size_t)L * (hpad / 16) * (hpad / 8) * 32 * sizeof(WFrag);
 }
+static_assert(2 * kMaxLayers * sizeof(float) <= 1 * (16 / 8) * (16 / 16) * 32 * sizeof(WFrag),
+              "the FP16 scale factors fit behind the fragments of the smallest buffer");
 
 inline float* fp16_scales(scale_ctx* c) {
   return reinterpret_cast<float*>(static_cast<char*>(c->wfrag) + fp16_scale_offset(c->L, c->hpad));

@@ -27,6 +27,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "mlp_mma.cuh"
 #include "scale_internal.cuh"
 
 using namespace scale;
@@ -138,7 +139,7 @@ extern "C" scale_status scale_log_psi_noalloc(const scale_system* sys, const sca
   }
   if (c.use_mma) {
     c.wfrag = base + off;
-    off = align256(off + (size_t)c.L * (c.hpad / 8) * (c.hpad / 8) * 32 * 16);
+    off = align256(off + wfrag_bytes(c.L, c.hpad));
   }
   // per-sample part
   const size_t per = align256(N * h * T) * 2 + align256(Ne * Ne * 8) + align256(Ne * 4) + align256(2 * N * 4) +
