@@ -98,25 +98,22 @@ __device__ __forceinline__ double move_coeff(const Lattice& lat, uint32_t pm) {
 // Diagonal matrix element of configuration occ (shared-memory copy): Hubbard U * (doubly
 // occupied sites); particle-hole Hubbard U * (sites with an up particle and no transformed
 // down particle); t-J J sum_<ij> Sz_i Sz_j over the NN bonds, as (J/4) sum s_i s_j with the
-// integer s = n_up - n_dn. Called by a whole warp: integer counts over the lanes, a warp sum,
-// one FP64 multiply (FP64 instructions are scarce on this GPU: one thread looping over the
-// bonds in FP64 kept the CTA waiting for about 0.2M cycles); the value is returned to every lane.
+// integer s = n_up - n_dn. One thread: integer counts, one FP64 multiply (FP64 instructions
+// are scarce on this GPU: the same loop over the bonds in FP64 kept the CTA waiting for about
+// 0.2M cycles; a warp-wide version took the kernel's registers from 80 to 96).
 __device__ __forceinline__ double diag_energy(const LowrankArgs& a, const int8_t* occ_s) {
-  const int lane = threadIdx.x & 31;
   const int N = a.lat.N;
   int cnt = 0;
   if (a.lat.model == SCALE_MODEL_HUBBARD) {
-    for (int i = lane; i < N; i += 32) cnt += occ_s[i] == 3;
+    for (int i = 0; i < N; ++i) cnt += occ_s[i] == 3;
   } else if (a.lat.model == SCALE_MODEL_HUBBARD_PH) {
-    for (int i = lane; i < N; i += 32) cnt += occ_s[i] == 1;
+    for (int i = 0; i < N; ++i) cnt += occ_s[i] == 1;
   } else {
-    for (int q = lane; q < a.nb_nn; q += 32) {
+    for (int q = 0; q < a.nb_nn; ++q) {
       const int oi = occ_s[a.bonds[2 * q]], oj = occ_s[a.bonds[2 * q + 1]];
       cnt += ((oi & 1) - ((oi >> 1) & 1)) * ((oj & 1) - ((oj >> 1) & 1));
     }
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
   return a.lat.model == SCALE_MODEL_TJ ? (0.25 * a.lat.J) * cnt : a.lat.U * cnt;
 }
 

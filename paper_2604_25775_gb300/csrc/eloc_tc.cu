@@ -653,10 +653,7 @@ __global__ void __launch_bounds__(kEtThreads, 1) k_eloc_tc(LowrankArgs a, Net<fl
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
-  if (warp == 0) {
-    const double d = diag_energy(a, occ_s);
-    if (lane == 0) s_diag = d;
-  }
+  if (tid == 0) s_diag = diag_energy(a, occ_s);
 
   const float* z0b = (const float*)a.z0 + (size_t)b * N * kEtH;
   const float* HLb = (const float*)a.HL + (size_t)b * N * kEtH;

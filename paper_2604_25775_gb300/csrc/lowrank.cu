@@ -52,10 +52,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_eloc(LowrankArgs a, Net<T> net) 
   for (int i = tid; i < N; i += blockDim.x) occ_s[i] = a.occ[(size_t)b * N + i];
   for (int o = tid; o < 2 * N; o += blockDim.x) slot_s[o] = a.slot_of_orb[(size_t)b * 2 * N + o];
   __syncthreads();
-  if (warp == 0) {
-    const double d = diag_energy(a, occ_s);
-    if (lane == 0) s_diag = d;
-  }
+  if (tid == 0) s_diag = diag_energy(a, occ_s);
   SampleView<T> sv;
   sv.occ = occ_s;
   sv.slot_of_orb = slot_s;

@@ -172,12 +172,9 @@ __global__ void __launch_bounds__(32 * NW) k_wl_enum(LowrankArgs a, const int64_
     nm += n;
     __syncthreads();
   }
-  if (!off && tid < 32) {
-    const double d = diag_energy(a, occ_s);
-    if (tid == 0) {
-      count[b] = nm;
-      diag[b] = d;
-    }
+  if (!off && tid == 0) {
+    count[b] = nm;
+    diag[b] = diag_energy(a, occ_s);
   }
 }
 
