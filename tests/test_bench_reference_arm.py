@@ -37,3 +37,17 @@ def test_workload_config_names_the_sizes():
     assert c["workload"] == "hubbard16x16: 16x16 torus, U=8, 112+112, SCALE 1 conv 3x3 + 5 site-wise, h=32"
     assert c["walkers"] == 8192 and c["parallelism"] == "replicas x2"
     assert c["l2"] == "inputs larger than L2 (cached inverses 1.6 GB)"
+
+
+def test_precision_modes_of_the_bench():
+    """The bench's --precision names map onto the library's mixed modes, each with a dtype
+    description naming its site-wise tensor-core products; without the option the workload's
+    own mode runs (FP16x3 for the 16x16 workload)."""
+    import bench
+    from paper_2604_25775_gb300 import inputs as I
+    assert bench.PRECISIONS == {"mixed": I.PREC_MIXED, "mixed_fp16": I.PREC_MIXED_FP16,
+                                "mixed_bf16": I.PREC_MIXED_BF16}
+    for name, mode in bench.PRECISIONS.items():
+        word = {"mixed": "tf32", "mixed_fp16": "f16", "mixed_bf16": "bf16"}[name]
+        assert f"3 {word} tensor-core products" in bench.DTYPES[mode]
+    assert I.workload("hubbard16x16").precision == I.PREC_MIXED_FP16
