@@ -337,6 +337,27 @@ __global__ void k_build_wfrag(Net<float> net, WFrag* __restrict__ wf, const floa
   wf[q] = f;
 }
 
+// Arguments of k_mlp_fwd, and its launch at the context's channel capacity.
+struct MlpFwdArgs {
+  Net<float> net;
+  const WFrag* wf;
+  int N, B;
+  const int32_t* list;
+  const float* in;
+  float* out;
+  const int32_t* count;
+  const float* oscale;
+};
+template <int KIND>
+void launch_mlp_fwd(const scale_ctx* c, int blocks, const MlpFwdArgs& f) {
+  if (c->hpad == 16)
+    k_mlp_fwd<16, KIND><<<blocks, 256, 0, c->stream>>>(f.net, f.wf, f.N, f.B, f.list, f.in, f.out, f.count, f.oscale);
+  else if (c->hpad == 32)
+    k_mlp_fwd<32, KIND><<<blocks, 256, 0, c->stream>>>(f.net, f.wf, f.N, f.B, f.list, f.in, f.out, f.count, f.oscale);
+  else
+    k_mlp_fwd<64, KIND><<<blocks, 256, 0, c->stream>>>(f.net, f.wf, f.N, f.B, f.list, f.in, f.out, f.count, f.oscale);
+}
+
 // occ rows of a packed batch into the listed samples' rows.
 __global__ void k_scatter_occ(int N, const int8_t* __restrict__ src, const int32_t* __restrict__ list,
                               int8_t* __restrict__ dst) {
@@ -433,16 +454,10 @@ cudaError_t forward_t(scale_ctx* c, const int8_t* occ, int B, const int32_t* lis
       const float* fin = (const float*)in;
       const int kind = mma_kind_of(c->arch.precision);
       const float* osc = kind == kFP16 ? fp16_scales(c) + kMaxLayers : nullptr;
-#define SCALE_MLP_FWD(KIND)                                                                                     \
-  do {                                                                                                          \
-    if (c->hpad == 16) k_mlp_fwd<16, KIND><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count, osc); \
-    else if (c->hpad == 32) k_mlp_fwd<32, KIND><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count, osc); \
-    else k_mlp_fwd<64, KIND><<<blocks, 256, 0, c->stream>>>(nf, wf, N, B, list, fin, out, count, osc); \
-  } while (0)
-      if (kind == kBF16) SCALE_MLP_FWD(kBF16);
-      else if (kind == kFP16) SCALE_MLP_FWD(kFP16);
-      else SCALE_MLP_FWD(kTF32);
-#undef SCALE_MLP_FWD
+      const MlpFwdArgs fa{nf, wf, N, B, list, fin, out, count, osc};
+      if (kind == kBF16) launch_mlp_fwd<kBF16>(c, blocks, fa);
+      else if (kind == kFP16) launch_mlp_fwd<kFP16>(c, blocks, fa);
+      else launch_mlp_fwd<kTF32>(c, blocks, fa);
       in = (const T*)out;
     }
   }
